@@ -1,0 +1,212 @@
+"""Exact small-system solver for the shaken dynamics (numpy, fp64).
+
+TEST INFRASTRUCTURE (see ``oracle/__init__.py``).
+
+Everything here is a direct transcription of a definition of arXiv:1904.06257
+on the full configuration space {-1,+1}^V (|V| <= ~12):
+
+* ``hamiltonian``       -- H(sigma), Eq. (ham1): -sum_{e} J_e s_x s_y - 2 sum_x lambda_x s_x.
+* ``pair_hamiltonian``  -- H(sigma1, sigma2), Eq. (ham21).
+* ``half_matrix``       -- P^{1->2} / P^{2->1} as products of single-site heat-bath
+                           factors e^{beta h tau} / 2cosh(beta h), Sec. 2 (and the
+                           lattice P^{dl}, P^{ur} of Sec. 3).
+* ``z_forward``         -- Z->_sigma = sum_tau e^{-beta H(sigma, tau)}, Thm 2.1.
+* ``stationary``        -- pi(sigma) = Z->_sigma / Z, Thm 2.1.
+* ``alt_matrix``        -- P^{alt} on pairs, Eq. (Palt), and ``pair_gibbs`` pi^b, Eq. (pi2).
+* ``gibbs``             -- pi^G(sigma) ~ e^{-beta H(sigma)}, Eq. (piG).
+
+A graph is given by its oriented edge list E^o (tail -> head) and couplings;
+the doubling graph of Def. 2.1 joins tail^(1) to head^(2).  Frozen sites
+(Sec. 3, the set B) restrict the configuration space to sigma_x = +1 on B.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+
+def states(n: int) -> np.ndarray:
+    """All configurations of n spins, shape (2^n, n); state i has sigma_x = +1 iff bit x of i."""
+    idx = np.arange(1 << n, dtype=np.int64)
+    bits = (idx[:, None] >> np.arange(n)[None, :]) & 1
+    return (2 * bits - 1).astype(np.int64)
+
+
+def state_index(sig: np.ndarray) -> np.ndarray:
+    """Inverse of ``states``: configurations (..., n) -> integer index."""
+    sig = np.asarray(sig)
+    bits = (sig > 0).astype(np.int64)
+    return (bits << np.arange(sig.shape[-1])).sum(axis=-1)
+
+
+def lattice_edges(L: int):
+    """Oriented lattice edges (x -> x_up), (x -> x_right) on the L x L torus (Sec. 3,
+    Eq. (ham2)); x = (i, j) -> i*L + j, up = row i+1, right = column j+1."""
+    tails, heads = [], []
+    for i in range(L):
+        for j in range(L):
+            x = i * L + j
+            tails += [x, x]
+            heads += [((i + 1) % L) * L + j, i * L + (j + 1) % L]
+    return np.array(tails), np.array(heads)
+
+
+def oriented_matrix(n, tails, heads, J):
+    """J^o with J^o[tail, head] = J_e (duplicate edges add), Sec. 2 (matrix form)."""
+    Jo = np.zeros((n, n))
+    np.add.at(Jo, (np.asarray(tails), np.asarray(heads)), np.broadcast_to(J, np.shape(tails)))
+    return Jo
+
+
+def fields(S, Jo, lam, q, half):
+    """Local fields for every configuration (rows of S).
+    half 0: h^{1->2}(sigma) = J^{oT} sigma + q sigma + lambda;
+    half 1: h^{2->1}(sigma) = J^o sigma + q sigma + lambda   (Sec. 2)."""
+    lam = np.broadcast_to(np.asarray(lam, dtype=float), (S.shape[1],))
+    if half == 0:
+        coup = S @ Jo  # (J^{oT} sigma)_x = sum_y Jo[y, x] sigma_y
+    else:
+        coup = S @ Jo.T  # (J^o sigma)_x = sum_y Jo[x, y] sigma_y
+    return coup + q * S + lam[None, :]
+
+
+def allowed(S, frozen):
+    if frozen is None:
+        return np.ones(S.shape[0], dtype=bool)
+    f = np.asarray(frozen, dtype=bool)
+    return np.all(S[:, f] > 0, axis=1)
+
+
+def half_matrix(S, Jo, lam, q, beta, half, frozen=None):
+    """P[sigma, tau] = prod_{x not in B} e^{beta h_x(sigma) tau_x} / 2cosh(beta h_x(sigma)),
+    restricted to configurations with +1 on B (zero rows/columns elsewhere)."""
+    h = fields(S, Jo, lam, q, half)
+    free = np.ones(S.shape[1], dtype=bool) if frozen is None else ~np.asarray(frozen, dtype=bool)
+    bh = beta * h[:, free]
+    logZ = np.logaddexp(bh, -bh).sum(axis=1)  # sum_x log 2cosh(beta h_x)
+    logP = bh @ S[:, free].T - logZ[:, None]
+    P = np.exp(logP)
+    ok = allowed(S, frozen)
+    P[~ok, :] = 0.0
+    P[:, ~ok] = 0.0
+    return P
+
+
+def shaken_matrix(S, Jo, lam, q, beta, frozen=None, order=(0, 1)):
+    """P^{sh} = P^{1->2} P^{2->1} (Sec. 2); order=(1, 0) gives P^{sh'} (Sec. 3)."""
+    A = half_matrix(S, Jo, lam, q, beta, order[0], frozen)
+    B = half_matrix(S, Jo, lam, q, beta, order[1], frozen)
+    return A @ B
+
+
+def hamiltonian(S, tails, heads, J, lam):
+    """H(sigma) = -sum_{e} J_e s_tail s_head - 2 sum_x lambda_x s_x, Eq. (ham1)."""
+    S = np.atleast_2d(S)
+    lam = np.broadcast_to(np.asarray(lam, dtype=float), (S.shape[1],))
+    J = np.broadcast_to(np.asarray(J, dtype=float), np.shape(tails))
+    return -(S[:, tails] * S[:, heads] * J).sum(axis=1) - 2.0 * (S * lam).sum(axis=1)
+
+
+def pair_hamiltonian(S1, S2, tails, heads, J, lam, q):
+    """H(s1, s2) = -sum_{(x,y) in E^o} J s1_x s2_y - sum_x (q s1_x s2_x + lambda_x (s1_x + s2_x)),
+    Eq. (ham21)."""
+    S1 = np.atleast_2d(S1)
+    S2 = np.atleast_2d(S2)
+    lam = np.broadcast_to(np.asarray(lam, dtype=float), (S1.shape[1],))
+    J = np.broadcast_to(np.asarray(J, dtype=float), np.shape(tails))
+    return (-(S1[:, tails] * S2[:, heads] * J).sum(axis=1)
+            - (q * S1 * S2 + lam * (S1 + S2)).sum(axis=1))
+
+
+def z_forward(S, tails, heads, J, lam, q, beta, frozen=None):
+    """Z->_sigma = sum_{tau allowed} e^{-beta H(sigma, tau)} by brute force (Thm 2.1)."""
+    ok = allowed(S, frozen)
+    T = S[ok]
+    out = np.zeros(S.shape[0])
+    for a in range(S.shape[0]):
+        H = pair_hamiltonian(np.repeat(S[a:a + 1], T.shape[0], 0), T, tails, heads, J, lam, q)
+        out[a] = np.exp(-beta * H).sum()
+    out[~ok] = 0.0
+    return out
+
+
+def stationary(S, tails, heads, J, lam, q, beta, frozen=None):
+    """pi(sigma) = Z->_sigma / Z, Thm 2.1 (Eq. (mispi))."""
+    z = z_forward(S, tails, heads, J, lam, q, beta, frozen)
+    return z / z.sum()
+
+
+def stationary_product(S, Jo, lam, q, beta, frozen=None):
+    """The same measure written as a product over sites (no frozen sites):
+    pi(sigma) ~ exp(beta sum_x lambda_x sigma_x) prod_x 2cosh(beta h^{1->2}_x(sigma))."""
+    assert frozen is None
+    lam_v = np.broadcast_to(np.asarray(lam, dtype=float), (S.shape[1],))
+    h = fields(S, Jo, lam, q, 0)
+    logw = beta * (S * lam_v).sum(axis=1) + np.logaddexp(beta * h, -beta * h).sum(axis=1)
+    w = np.exp(logw - logw.max())
+    return w / w.sum()
+
+
+def gibbs(S, tails, heads, J, lam, beta, frozen=None):
+    """pi^G(sigma) = e^{-beta H(sigma)} / Z^G, Eq. (piG)."""
+    H = hamiltonian(S, tails, heads, J, lam)
+    w = np.exp(-beta * (H - H.min()))
+    w[~allowed(S, frozen)] = 0.0
+    return w / w.sum()
+
+
+def pair_gibbs(S, tails, heads, J, lam, q, beta):
+    """pi^b(s1, s2) = e^{-beta H(s1, s2)} / Z on pairs (index a*2^n + b), Eq. (pi2)."""
+    N = S.shape[0]
+    a, b = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    H = pair_hamiltonian(S[a.ravel()], S[b.ravel()], tails, heads, J, lam, q)
+    w = np.exp(-beta * (H - H.min()))
+    return w / w.sum()
+
+
+def alt_matrix(S, Jo, lam, q, beta):
+    """P^{alt}((s1, s2), (t1, t2)) = P^{1->2}(s1, t2) P^{2->1}(t2, t1), Eq. (Palt).
+    Pair states are indexed a*2^n + b for (s1 = S[a], s2 = S[b])."""
+    A = half_matrix(S, Jo, lam, q, beta, 0)
+    B = half_matrix(S, Jo, lam, q, beta, 1)
+    N = S.shape[0]
+    P = np.zeros((N * N, N * N))
+    for a1 in range(N):
+        for t1 in range(N):
+            # independent of s2: same row for every b1
+            row = A[a1, :] * B[:, t1]  # indexed by t2
+            for b1 in range(N):
+                P[a1 * N + b1, t1 * N + np.arange(N)] = row
+    return P
+
+
+def total_variation(mu, nu):
+    """||mu - nu||_TV = (1/2) sum |mu - nu|, Eq. (dist)."""
+    return 0.5 * np.abs(np.asarray(mu) - np.asarray(nu)).sum()
+
+
+def evolve(mu0, P, t):
+    mu = np.asarray(mu0, dtype=float)
+    for _ in range(t):
+        mu = mu @ P
+    return mu
+
+
+def triangular_gibbs_lambda0(S, L, J, q, beta):
+    """Gibbs measure of the anisotropic triangular Ising model obtained from the
+    shaken measure at lambda = 0 by summing out the second copy: couplings
+    K1 on (x, x_down) and (x, x_left), K2 on (x_down, x_left), with K = beta J,
+    Q = beta q:  K1 = (1/4) ln[cosh(2K+Q)/cosh(2K-Q)],
+    K2 = (1/4) ln[cosh(2K+Q) cosh(2K-Q)/cosh^2 Q]."""
+    K, Q = beta * J, beta * q
+    K1 = 0.25 * np.log(np.cosh(2 * K + Q) / np.cosh(2 * K - Q))
+    K2 = 0.25 * np.log(np.cosh(2 * K + Q) * np.cosh(2 * K - Q) / np.cosh(Q) ** 2)
+    logw = np.zeros(S.shape[0])
+    for i, j in itertools.product(range(L), range(L)):
+        x = i * L + j
+        dn = ((i - 1) % L) * L + j
+        lf = i * L + (j - 1) % L
+        logw += K1 * S[:, x] * (S[:, dn] + S[:, lf]) + K2 * S[:, dn] * S[:, lf]
+    w = np.exp(logw - logw.max())
+    return w / w.sum()
