@@ -1,0 +1,385 @@
+#!/usr/bin/env python3
+"""Throughput of the shaken-dynamics half-step update (arXiv:1904.06257) on GB300.
+
+Workload (one "step" = one full shaken step P^dl then P^ur of every replica):
+  batched multispin lattices -- 128 groups of 32 replicas (4096 replicas), each
+  group an L x L periodic torus with L drawn uniformly from {32, 64, 128, 256,
+  512}, J = 1, q = 1, lambda = 0, beta_r = 0.3 + 0.3 (r mod 64) / 63, random
+  start, all groups stepped by one launch per half step.
+Metric: site-updates/s (2 |V| R per step), whole job over all ranks.
+
+Also reported: the plain single-lattice kernel (L = 4096, int8, one replica)
+on the same GPU, end-to-end throughput through the public C ABI with host
+buffers, the roofline of the dominant kernel and the CPU oracle baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1904_06257_gb300 import workloads as W  # noqa: E402
+
+GROUPS = 128
+REPLICAS_PER_GROUP = 32
+L_CHOICES = (32, 64, 128, 256, 512)
+Q, J, LAM = 1.0, 1.0, 0.0
+FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def workload(rank: int):
+    Ls = W.multispin_group_sizes(GROUPS, W.BASE_SEED, L_CHOICES)
+    betas = W.beta_grid(GROUPS * REPLICAS_PER_GROUP, 0.3, 0.6, 64)
+    seeds = [W.BASE_SEED + 100003 * rank + g for g in range(GROUPS)]
+    return Ls, betas, seeds
+
+
+def updates_per_step(Ls) -> float:
+    return 2.0 * REPLICAS_PER_GROUP * float(np.sum(np.asarray(Ls, dtype=np.float64) ** 2))
+
+
+# ------------------------------------------------------------------------ clocks
+class Clocks:
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------ oracle (CPU)
+def _oracle_group(args):
+    L, betas, seed, steps = args
+    from oracle import core
+    s = core.lattice_init(L, REPLICAS_PER_GROUP, seed, core.MODE_MULTISPIN, 0)
+    t0 = time.perf_counter()
+    core.lattice_run(s, J, Q, LAM, betas, seed, 0, steps, core.MODE_MULTISPIN)
+    dt = time.perf_counter() - t0
+    return 2.0 * REPLICAS_PER_GROUP * L * L * steps, dt
+
+
+def _warm(_):
+    from oracle import core  # noqa: F401
+    return 0
+
+
+def oracle_pool(n_groups):
+    """A spawned process pool for the oracle (spawn: safe after CUDA is initialised)."""
+    from oracle import core
+    core.build()
+    workers = max(1, min(n_groups, os.cpu_count() or 1))
+    pool = mp.get_context("spawn").Pool(workers)
+    pool.map(_warm, range(workers))
+    return pool, workers
+
+
+def oracle_sample(pool, workers, Ls, betas, seeds, steps_per_group=1, max_groups=None):
+    """Run the CPU oracle, as it stands, on the smallest groups of the workload
+    (L = 32 and 64), one task per group on the pool, and return
+    (updates/s over the wall time, cores used, description, updates, wall)."""
+    idx = [g for g in range(len(Ls)) if Ls[g] <= 64]
+    if max_groups:
+        idx = idx[:max_groups]
+    workers = min(workers, len(idx))
+    jobs = [(int(Ls[g]), betas[32 * g:32 * g + 32], seeds[g], steps_per_group) for g in idx]
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_group, jobs)
+    wall = time.perf_counter() - t0
+    upd = sum(r[0] for r in res)
+    desc = (f"{len(jobs)} groups of the workload with L in {{32, 64}} (32 replicas each), "
+            f"{steps_per_group} full step(s) each, one spawned process per group")
+    return upd / wall, workers, desc, upd, wall
+
+
+# ------------------------------------------------------------------------ GPU arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1904_06257_gb300 import build
+    build.build()
+    from paper_1904_06257_gb300 import shaken as S
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    Ls, betas, seeds = workload(rank)
+    ups = updates_per_step(Ls)
+
+    # ---- batched multispin groups
+    ctxs = []
+    batch = S.shaken_batch_create(stream)
+    for g in range(GROUPS):
+        p = S.Problem(S.LATTICE, S.MULTISPIN, REPLICAS_PER_GROUP, betas[32 * g:32 * g + 32], Q,
+                      L=int(Ls[g]), J=J, lambda_const=LAM)
+        c = S.shaken_init(p, seeds[g], stream)
+        S.shaken_batch_add(batch, c)
+        ctxs.append(c)
+    # RNG accounting over two warm-up steps (not timed)
+    counter = torch.zeros(1, dtype=torch.int64, device=dev)
+    S.shaken_batch_set_rng_counter(batch, counter.data_ptr())
+    S.shaken_batch_step(batch, 2, False)
+    S.shaken_batch_sync(batch)
+    calls_per_launch = float(counter.item()) / 4.0
+    S.shaken_batch_set_rng_counter(batch, None)
+    S.shaken_batch_step(batch, max(args.warmup, 3), False)
+    S.shaken_batch_sync(batch)
+
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    S.shaken_batch_set_timing(batch, True)
+    l0 = S.shaken_batch_launch_count(batch)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local_rank)
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()  # L2 flush between timed steps (outside the events)
+            ev[k][0].record(stream)
+        S.shaken_batch_step(batch, 1, False)
+        with torch.cuda.stream(stream):
+            ev[k][1].record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    launches = S.shaken_batch_launch_count(batch) - l0
+    step_ms = sum(a.elapsed_time(b) for a, b in ev)
+    kern_ms, kern_n = S.shaken_batch_kernel_time(batch)
+    S.shaken_batch_set_timing(batch, False)
+    tot = torch.tensor([step_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(tot, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+    step_ms_max = float(tot.item())
+    value = ups * args.steps * world / (step_ms_max * 1e-3)
+
+    # ---- CUDA-graph replay of the same batch (steady state, no flush): context
+    S.shaken_batch_step(batch, 64, True)
+    S.shaken_batch_sync(batch)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+    S.shaken_batch_step(batch, 128, True)
+    with torch.cuda.stream(stream):
+        e1.record(stream)
+    stream.synchronize()
+    graph_rate = ups * 128 / (e0.elapsed_time(e1) * 1e-3)
+
+    # ---- unbatched: each group on its own (one launch sequence per group)
+    for c in ctxs:
+        S.shaken_batch_remove(batch, c)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nst = 4
+    for c in ctxs:
+        S.shaken_step(c, nst)
+    for c in ctxs:
+        S.shaken_sync(c)
+    torch.cuda.synchronize()
+    unbatched_rate = ups * nst / (time.perf_counter() - t0)
+    for c in ctxs:
+        S.shaken_batch_add(batch, c)
+
+    # ---- e2e through the C ABI with host buffers: a job uploads every group's
+    # state from pinned host memory, runs K steps, reads every state and the
+    # observables back.
+    nbytes = [S.shaken_state_bytes(c) for c in ctxs]
+    host_in = [torch.empty(n, dtype=torch.uint8, pin_memory=True) for n in nbytes]
+    host_out = [torch.empty(n, dtype=torch.uint8, pin_memory=True) for n in nbytes]
+    g = np.random.default_rng(5)
+    for h in host_in:
+        h.numpy()[:] = g.integers(0, 256, size=h.numel(), dtype=np.uint8)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c, h, n in zip(ctxs, host_in, nbytes):
+        S.shaken_set_state_raw(c, h.data_ptr(), n)
+    S.shaken_batch_step(batch, args.steps, True)
+    obs_bytes = 0
+    for c, h, n in zip(ctxs, host_out, nbytes):
+        S.shaken_get_state_raw(c, h.data_ptr(), n)
+        o = S.shaken_observables(c, REPLICAS_PER_GROUP)
+        obs_bytes += o.nbytes
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": ups * args.steps * world / e2e_s, "unit": "updates/s",
+           "h2d_bytes_per_step": int(sum(nbytes) / args.steps),
+           "d2h_bytes_per_step": int((sum(nbytes) + obs_bytes) / args.steps),
+           "what": "per job of K steps: raw state of all 128 groups H2D from pinned memory, "
+                   "K batched steps (CUDA graph), states and observables D2H; wall clock"}
+
+    # ---- plain single-lattice kernel: L = 4096 int8, one replica
+    Lp = 4096
+    pp = S.Problem(S.LATTICE, S.INT8, 1, 0.4407, Q, L=Lp, J=J, lambda_const=LAM)
+    cp = S.shaken_init(pp, W.BASE_SEED + 7, stream)
+    S.shaken_step(cp, 3)
+    S.shaken_sync(cp)
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        pe0.record(stream)
+    S.shaken_step(cp, 64)
+    with torch.cuda.stream(stream):
+        pe1.record(stream)
+    stream.synchronize()
+    plain_rate = 2.0 * Lp * Lp * 64 / (pe0.elapsed_time(pe1) * 1e-3)
+    S.shaken_free(cp)
+
+    # ---- roofline of the dominant kernel (multispin half step)
+    rb_calls, _ = S.shaken_microbench(0)
+    rb_lop3, _ = S.shaken_microbench(1)
+    rb_imad, _ = S.shaken_microbench(2)
+    avg_kernel_s = (kern_ms / max(kern_n, 1)) * 1e-3
+    achieved = calls_per_launch / avg_kernel_s
+    roofline = {"bound": "alu", "kernel": "lattice_half_kernel<MULTISPIN>",
+                "achieved": achieved / 1e9, "peak": rb_calls / 1e9,
+                "unit": "G Philox-4x32-10 calls/s", "frac": achieved / rb_calls,
+                "traffic": None,
+                "calls_per_launch": calls_per_launch,
+                "updates_per_launch": ups / 2.0,
+                "avg_launch_ms": avg_kernel_s * 1e3,
+                "timed_launches": kern_n,
+                "peak_source": "register-only Philox microbenchmark on this GPU, all SMs "
+                               "(shaken_microbench kind 0), measured in this run",
+                "int32_lop3_per_s": rb_lop3, "int32_imad_per_s": rb_imad}
+
+    out = None
+    if rank == 0:
+        cpu = None
+        if world == 1:
+            pool, workers = oracle_pool(GROUPS)
+            v, cores, desc, upd, wall = oracle_sample(pool, workers, Ls, betas, seeds,
+                                                      steps_per_group=8)
+            pool.close()
+            pool.join()
+            cpu = {"value": v, "unit": "updates/s", "cores": cores, "kind": "oracle",
+                   "sample": desc, "updates": upd, "wall_s": wall}
+        out = {
+            "metric": "site-updates/s (batched multispin shaken dynamics)",
+            "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": "batched multispin: 128 groups x 32 replicas (4096), "
+                                   "L uniform in {32,64,128,256,512}, beta grid of 64 in "
+                                   "[0.3,0.6], J=1, q=1, lambda=0, periodic",
+                       "L_per_group_sum_sq": int(np.sum(np.asarray(Ls) ** 2)),
+                       "updates_per_step": ups, "replicas": GROUPS * REPLICAS_PER_GROUP,
+                       "l2": "flushed between timed steps (256 MiB write outside the events)",
+                       "parallelism": f"replicas/groups sharded over {world} GPU(s)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks,
+            "batched_vs_plain": {
+                "batched_updates_per_s": value / world,
+                "batched_graph_replay_updates_per_s": graph_rate,
+                "unbatched_same_groups_updates_per_s": unbatched_rate,
+                "plain_int8_L4096_updates_per_s": plain_rate},
+        }
+    for c in ctxs:
+        S.shaken_batch_remove(batch, c)
+        S.shaken_free(c)
+    S.shaken_batch_free(batch)
+    return out
+
+
+# ------------------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    Ls, betas, seeds = workload(0)
+    tot_upd, tot_wall, cores, desc = 0.0, 0.0, 1, ""
+    pool, workers = oracle_pool(16)
+    for k in range(args.warmup + args.steps):
+        v, cores, desc, upd, wall = oracle_sample(pool, workers, Ls, betas, seeds, 1,
+                                                  max_groups=16)
+        if k >= args.warmup:
+            tot_upd += upd
+            tot_wall += wall
+    pool.close()
+    pool.join()
+    val = tot_upd / tot_wall
+    return {"impl": "reference", "metric": "site-updates/s (batched multispin shaken dynamics)",
+            "value": val, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_wall * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "batched multispin: 128 groups x 32 replicas (4096), "
+                                   "L uniform in {32,64,128,256,512}, beta grid of 64 in "
+                                   "[0.3,0.6], J=1, q=1, lambda=0, periodic"},
+            "cpu_baseline": {"value": val, "unit": "updates/s", "kind": "oracle", "cores": cores,
+                             "sample": "each step: " + desc},
+            "e2e": {"value": val, "unit": "updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            torch.cuda.set_device(local_rank)
+            torch.distributed.init_process_group("nccl")
+        out = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

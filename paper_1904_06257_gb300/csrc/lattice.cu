@@ -1,0 +1,508 @@
+// lattice.cu -- half-step kernels of the shaken dynamics on the L x L torus
+// (Sec. 3 of arXiv:1904.06257) for three spin encodings, the threshold-table
+// builder and the lattice observables.
+//
+// Half step 0 is P^dl: tau_x from h^dl_x = J (s_down + s_left) + q s_x + lambda
+// (Eq. (hdl)); half step 1 is P^ur with h^ur_x = J (s_up + s_right) + q s_x +
+// lambda (Eq. (hur)).  Every site of a half step is resampled at once from the
+// other buffer (the parallel product form below Eq. (pasymm)).
+//
+// Work unit: a lane word = 32 decisions sharing Philox counter words (a, b):
+//   INT8 / PACKED: 32 consecutive sites (i, 32c .. 32c+31) of one replica,
+//                  a = i*L/32 + c, b = replica;
+//   MULTISPIN:     one site x of 32 replicas (bit k = replica 32g+k), a = x, b = g.
+// Decision: u_k < T(c_k, beta_k) where u_k's bit (31-j) is bit k of the plane
+// word W_j = Philox(key, (a, b, t, half + 2(j>>2)))[j & 3].  The comparison is
+// done for all 32 lanes at once, most significant plane first, and stops when
+// every lane differs from its threshold in some plane already seen (later
+// planes cannot change the result; the draws are counter-based, so planes never
+// generated are simply never needed).  Per plane the lane's threshold bit is
+// OR_c (class_mask_c & tm[j][c]).
+#include <cstdint>
+
+#include "shaken_internal.cuh"
+
+namespace shk {
+
+// --------------------------------------------------------------------------- tables
+// One block per table, one warp per field class c (6 classes): lane k computes
+// T(h_c, beta_k) in fp64 and the warp ballots its bit planes.
+__global__ void __launch_bounds__(256) build_lattice_tables_kernel(
+    const double* __restrict__ beta_lanes, int ntab, double J, double q, double lam,
+    LatTable* __restrict__ out) {
+  const int tab = blockIdx.x;
+  if (tab >= ntab) return;
+  const int lane = threadIdx.x & 31;
+  const int c = threadIdx.x >> 5;  // 0..7
+  LatTable* T = out + tab;
+  if (c >= 6) {
+    if (lane < 32) {
+      T->tm[lane][c] = 0u;
+      if (lane == 0) {
+        T->satp[c] = 0u;
+        T->satm[c] = 0u;
+      }
+    }
+    return;
+  }
+  const int n = c >> 1, s = c & 1;
+  const double beta = beta_lanes[(size_t)tab * 32 + lane];
+  const double h = field_h(J, 2 * n - 2, q, 2 * s - 1, lam);
+  const unsigned long long Tv = threshold_T(h, beta);
+  const bool satp = Tv == 4294967296ULL;
+  const bool satm = Tv == 0ULL;
+  const unsigned sp = __ballot_sync(0xffffffffu, satp);
+  const unsigned sm = __ballot_sync(0xffffffffu, satm);
+  if (lane == 0) {
+    T->satp[c] = sp;
+    T->satm[c] = sm;
+  }
+  const uint32_t t32 = (satp || satm) ? 0u : (uint32_t)Tv;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const unsigned m = __ballot_sync(0xffffffffu, (t32 >> (31 - j)) & 1u);
+    if (lane == 0) T->tm[j][c] = m;
+  }
+}
+
+// --------------------------------------------------------------------------- decision core
+// S = sigma_x bits, V / H = the two in-neighbour bits (vertical / horizontal),
+// F = frozen lanes.  Returns tau bits (1 = +1).
+__device__ __forceinline__ uint32_t decide32(uint32_t S, uint32_t V, uint32_t H, uint32_t F,
+                                             const LatTable* __restrict__ tab, const PhKey& K,
+                                             uint32_t a, uint32_t b, uint32_t t, uint32_t half,
+                                             uint32_t& calls) {
+  const uint32_t n2 = V & H;
+  const uint32_t n1 = V ^ H;
+  const uint32_t n0 = ~(V | H);
+  uint32_t M[6];
+  M[0] = n0 & ~S;
+  M[1] = n0 & S;
+  M[2] = n1 & ~S;
+  M[3] = n1 & S;
+  M[4] = n2 & ~S;
+  M[5] = n2 & S;
+  uint32_t dec = F, res = F;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const uint32_t sp = __ldg(&tab->satp[c]);
+    const uint32_t sm = __ldg(&tab->satm[c]);
+    dec |= M[c] & (sp | sm);
+    res |= M[c] & sp;
+  }
+#pragma unroll 1
+  for (uint32_t call = 0; call < 8; ++call) {
+    if (dec == 0xffffffffu) break;
+    const uint4 w = ph_call(K, a, b, t, half + 2u * call);
+    ++calls;
+    const uint32_t Wj[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint4* row = reinterpret_cast<const uint4*>(tab->tm[4 * call + i]);
+      const uint4 lo = __ldg(row);
+      const uint4 hi = __ldg(row + 1);
+      const uint32_t P = (M[0] & lo.x) | (M[1] & lo.y) | (M[2] & lo.z) | (M[3] & lo.w) |
+                         (M[4] & hi.x) | (M[5] & hi.y);
+      const uint32_t diff = (Wj[i] ^ P) & ~dec;
+      res |= diff & P;
+      dec |= diff;
+    }
+  }
+  return res;
+}
+
+// --------------------------------------------------------------------------- int8 <-> bits
+// 4 bytes of +1/-1 -> 4 bits (bit k = byte k is +1).  +1 = 0x01, -1 = 0xFF: the
+// sign bit of each byte is clear for +1.
+__device__ __forceinline__ uint32_t bits4(uint32_t w) {
+  const uint32_t pos = (~w >> 7) & 0x01010101u;        // 1 per +1 byte at bit 0 of each byte
+  return ((pos * 0x00204081u) >> 21) & 0xFu;           // gather bytes 0..3 -> bits 0..3
+}
+__device__ __forceinline__ uint32_t bits16(uint4 v) {
+  return bits4(v.x) | (bits4(v.y) << 4) | (bits4(v.z) << 8) | (bits4(v.w) << 12);
+}
+// 4 bits -> 4 bytes of +1/-1
+__device__ __forceinline__ uint32_t bytes4(uint32_t b) {
+  const uint32_t spread = ((b & 0xFu) * 0x00204081u) & 0x01010101u;  // bit k -> byte k
+  return ~(spread * 0xFEu);                                           // 1 -> 0x01, 0 -> 0xFF
+}
+__device__ __forceinline__ uint4 bytes16(uint32_t b) {
+  return make_uint4(bytes4(b), bytes4(b >> 4), bytes4(b >> 8), bytes4(b >> 12));
+}
+
+// --------------------------------------------------------------------------- reductions
+template <int NV>
+__device__ __forceinline__ void block_sum_atomic(double (&v)[NV], double* dst, double* smem) {
+  // smem: at least (blockDim/32) * NV doubles
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) smem[warp * NV + k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += smem[w * NV + threadIdx.x];
+    if (s != 0.0) atomicAdd(dst + threadIdx.x, s);
+  }
+  __syncthreads();
+}
+
+// --------------------------------------------------------------------------- half step
+enum { kEncInt8 = 0, kEncPacked = 1, kEncMultispin = 2 };
+
+template <int ENC>
+__global__ void __launch_bounds__(kTile) lattice_half_kernel(const LatJob* __restrict__ jobs,
+                                                             const Tile* __restrict__ tiles,
+                                                             int n_tiles, uint32_t half,
+                                                             unsigned long long* rng_calls) {
+  __shared__ double red[(kTile / 32) * 3];
+  uint32_t calls = 0;
+  for (int ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
+    const Tile tl = tiles[ti];
+    const LatJob& J = jobs[tl.job];
+    const CtxDev* cd = J.cd;
+    const uint32_t t = cd->step;
+    if (t >= cd->t_end) continue;  // uniform per block
+    const LatTable* tab = J.table;
+    if (J.anneal_tables != nullptr && cd->anneal_len != 0u) {
+      uint32_t k = t - cd->anneal_t0;
+      if (k >= cd->anneal_len) k = cd->anneal_len - 1u;
+      tab = J.anneal_tables + k;
+    }
+    const uint32_t w = tl.w0 + threadIdx.x;
+    const bool active = w < J.nwords;
+    const bool fuse = (ENC != kEncMultispin) && half == 0u && J.sums != nullptr && cd->tracking;
+    double acc[3] = {0.0, 0.0, 0.0};
+    if (active) {
+      const uint32_t L = J.L, wpr = J.wpr;
+      const uint32_t i = w / wpr, c = w - i * wpr;
+      const uint32_t iv = half == 0u ? (i == 0u ? L - 1u : i - 1u) : (i + 1u == L ? 0u : i + 1u);
+      uint32_t S, V, H;
+      const void* src = half == 0u ? J.A : J.B;
+      void* dstbuf = half == 0u ? J.B : J.A;
+      if (ENC == kEncInt8) {
+        const uint8_t* A = static_cast<const uint8_t*>(src);
+        const uint4* own = reinterpret_cast<const uint4*>(A + (size_t)i * L + 32u * c);
+        const uint4* ver = reinterpret_cast<const uint4*>(A + (size_t)iv * L + 32u * c);
+        S = bits16(own[0]) | (bits16(own[1]) << 16);
+        V = bits16(ver[0]) | (bits16(ver[1]) << 16);
+        uint32_t jn = half == 0u ? (c == 0u ? L - 1u : 32u * c - 1u)
+                                 : (32u * c + 32u == L ? 0u : 32u * c + 32u);
+        const uint32_t nb = (A[(size_t)i * L + jn] >> 7) ^ 1u;  // 1 if +1
+        H = half == 0u ? ((S << 1) | nb) : ((S >> 1) | (nb << 31));
+      } else if (ENC == kEncPacked) {
+        const uint32_t* A = static_cast<const uint32_t*>(src);
+        S = A[(size_t)i * wpr + c];
+        V = A[(size_t)iv * wpr + c];
+        if (half == 0u) {
+          const uint32_t cl = c == 0u ? wpr - 1u : c - 1u;
+          H = (S << 1) | (A[(size_t)i * wpr + cl] >> 31);
+        } else {
+          const uint32_t cr = c + 1u == wpr ? 0u : c + 1u;
+          H = (S >> 1) | (A[(size_t)i * wpr + cr] << 31);
+        }
+      } else {
+        const uint32_t* A = static_cast<const uint32_t*>(src);
+        const uint32_t jn = half == 0u ? (c == 0u ? L - 1u : c - 1u) : (c + 1u == L ? 0u : c + 1u);
+        S = A[w];
+        V = A[(size_t)iv * L + c];
+        H = A[(size_t)i * L + jn];
+      }
+      const uint32_t F = J.frozen != nullptr ? J.frozen[w] : 0u;
+      const PhKey K = ph_key(J.key0, J.key1);
+      const uint32_t tau = decide32(S, V, H, F, tab, K, w, J.b, t, half, calls);
+      if (ENC == kEncInt8) {
+        uint8_t* B = static_cast<uint8_t*>(dstbuf);
+        uint4* dst = reinterpret_cast<uint4*>(B + (size_t)i * L + 32u * c);
+        dst[0] = bytes16(tau);
+        dst[1] = bytes16(tau >> 16);
+      } else {
+        static_cast<uint32_t*>(dstbuf)[w] = tau;
+      }
+      if (fuse) {
+        // sums of sigma_t over the lane word: M, E (in-edges down and left), cut
+        const int dv = __popc(S ^ V), dh = __popc(S ^ H);
+        acc[0] = (double)(2 * __popc(S) - 32);
+        acc[1] = (double)(64 - 2 * dv - 2 * dh);
+        acc[2] = (double)(dv + dh);
+      }
+    }
+    if (fuse) {
+      // slots: M -> kSumM, E -> kSumE, cut -> kSumCut (write M, E, then cut separately)
+      double v2[2] = {acc[0], acc[1]};
+      block_sum_atomic<2>(v2, J.sums + kSumM, red);
+      double v1[1] = {acc[2]};
+      block_sum_atomic<1>(v1, J.sums + kSumCut, red);
+    }
+  }
+  if (rng_calls != nullptr) {
+    const uint32_t wsum = __reduce_add_sync(0xffffffffu, calls);
+    if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(rng_calls, (unsigned long long)wsum);
+  }
+}
+
+// --------------------------------------------------------------------------- init
+// sigma = +1 iff u < 2^31 with u the draw of step 0xFFFFFFFF, half 0: bit 31 of u
+// is bit k of the first plane word W_0, so sigma_k = +1 iff that bit is 0.
+// kind: 0 random, 1 plus, 2 minus.  Frozen lanes +1.  Writes A and B.
+template <int ENC>
+__global__ void __launch_bounds__(kTile) lattice_init_kernel(const LatJob* __restrict__ jobs,
+                                                             const Tile* __restrict__ tiles,
+                                                             int n_tiles, int kind) {
+  for (int ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
+    const Tile tl = tiles[ti];
+    const LatJob& J = jobs[tl.job];
+    const uint32_t w = tl.w0 + threadIdx.x;
+    if (w >= J.nwords) continue;
+    uint32_t s;
+    if (kind == 1) {
+      s = 0xffffffffu;
+    } else if (kind == 2) {
+      s = 0u;
+    } else {
+      const PhKey K = ph_key(J.key0, J.key1);
+      const uint4 W = ph_call(K, w, J.b, kInitStep, 0u);
+      s = ~W.x;
+    }
+    if (J.frozen != nullptr) s |= J.frozen[w];
+    if (ENC == kEncInt8) {
+      const uint32_t L = J.L, wpr = J.wpr;
+      const uint32_t i = w / wpr, c = w - i * wpr;
+      const size_t off = (size_t)i * L + 32u * c;
+      uint4* a = reinterpret_cast<uint4*>(static_cast<uint8_t*>(J.A) + off);
+      uint4* b = reinterpret_cast<uint4*>(static_cast<uint8_t*>(J.B) + off);
+      a[0] = b[0] = bytes16(s);
+      a[1] = b[1] = bytes16(s >> 16);
+    } else {
+      static_cast<uint32_t*>(J.A)[w] = s;
+      static_cast<uint32_t*>(J.B)[w] = s;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------- observables
+// INT8 / PACKED: per lane word, integer sums of sigma (A) and sigma' (B):
+//   M, E = in-edge agreement sum (down, left), P1 = sum sigma_x (sigma'_up + sigma'_right),
+//   P2 = sum sigma_x sigma'_x, M2 = sum sigma', cut.
+template <int ENC>
+__device__ __forceinline__ void load_lane_words(const LatJob& J, const void* buf, uint32_t w,
+                                                uint32_t half, uint32_t& S, uint32_t& V,
+                                                uint32_t& H) {
+  const uint32_t L = J.L, wpr = J.wpr;
+  const uint32_t i = w / wpr, c = w - i * wpr;
+  const uint32_t iv = half == 0u ? (i == 0u ? L - 1u : i - 1u) : (i + 1u == L ? 0u : i + 1u);
+  if (ENC == kEncInt8) {
+    const uint8_t* A = static_cast<const uint8_t*>(buf);
+    const uint4* own = reinterpret_cast<const uint4*>(A + (size_t)i * L + 32u * c);
+    const uint4* ver = reinterpret_cast<const uint4*>(A + (size_t)iv * L + 32u * c);
+    S = bits16(own[0]) | (bits16(own[1]) << 16);
+    V = bits16(ver[0]) | (bits16(ver[1]) << 16);
+    const uint32_t jn = half == 0u ? (c == 0u ? L - 1u : 32u * c - 1u)
+                                   : (32u * c + 32u == L ? 0u : 32u * c + 32u);
+    const uint32_t nb = (A[(size_t)i * L + jn] >> 7) ^ 1u;
+    H = half == 0u ? ((S << 1) | nb) : ((S >> 1) | (nb << 31));
+  } else if (ENC == kEncPacked) {
+    const uint32_t* A = static_cast<const uint32_t*>(buf);
+    S = A[(size_t)i * wpr + c];
+    V = A[(size_t)iv * wpr + c];
+    if (half == 0u) {
+      const uint32_t cl = c == 0u ? wpr - 1u : c - 1u;
+      H = (S << 1) | (A[(size_t)i * wpr + cl] >> 31);
+    } else {
+      const uint32_t cr = c + 1u == wpr ? 0u : c + 1u;
+      H = (S >> 1) | (A[(size_t)i * wpr + cr] << 31);
+    }
+  } else {
+    const uint32_t* A = static_cast<const uint32_t*>(buf);
+    const uint32_t jn = half == 0u ? (c == 0u ? L - 1u : c - 1u) : (c + 1u == L ? 0u : c + 1u);
+    S = A[w];
+    V = A[(size_t)iv * L + c];
+    H = A[(size_t)i * L + jn];
+  }
+}
+
+template <int ENC>
+__global__ void __launch_bounds__(kTile) lattice_obs_single_kernel(
+    const LatJob* __restrict__ jobs, const Tile* __restrict__ tiles, int n_tiles, int which,
+    int full) {
+  __shared__ double red[(kTile / 32) * 6];
+  for (int ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
+    const Tile tl = tiles[ti];
+    const LatJob& J = jobs[tl.job];
+    const uint32_t w = tl.w0 + threadIdx.x;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    if (w < J.nwords) {
+      uint32_t S, V, H;
+      load_lane_words<ENC>(J, J.A, w, 0u, S, V, H);
+      const int dv = __popc(S ^ V), dh = __popc(S ^ H);
+      v[0] = (double)(2 * __popc(S) - 32);
+      v[1] = (double)(64 - 2 * dv - 2 * dh);
+      v[5] = (double)(dv + dh);
+      if (full) {
+        uint32_t S2, U2, R2;
+        load_lane_words<ENC>(J, J.B, w, 1u, S2, U2, R2);  // sigma', its up and right bits
+        v[2] = (double)(64 - 2 * __popc(S ^ U2) - 2 * __popc(S ^ R2));
+        v[3] = (double)(32 - 2 * __popc(S ^ S2));
+        v[4] = (double)(2 * __popc(S2) - 32);
+      }
+    }
+    // slots 0:M 1:E 2:P1 3:P2 4:M2 5:cut -> kSumM, kSumE, kSumP1, kSumP2, kSumM2, kSumCut
+    double* dst = which ? J.obs : J.sums;
+    double a[2] = {v[0], v[1]};
+    block_sum_atomic<2>(a, dst + kSumM, red);
+    double b3[3] = {v[2], v[3], v[4]};
+    block_sum_atomic<3>(b3, dst + kSumP1, red);
+    double c1[1] = {v[5]};
+    block_sum_atomic<1>(c1, dst + kSumCut, red);
+  }
+}
+
+// MULTISPIN: per-lane (= per replica) sums.  Each warp covers 32 consecutive
+// sites; for every mask the warp ballots bit k and lane k adds the popcount.
+__global__ void __launch_bounds__(kTile) lattice_obs_multispin_kernel(
+    const LatJob* __restrict__ jobs, const Tile* __restrict__ tiles, int n_tiles, int which,
+    int full) {
+  __shared__ int red[kTile / 32][32][6];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
+    const Tile tl = tiles[ti];
+    const LatJob& J = jobs[tl.job];
+    const uint32_t w = tl.w0 + threadIdx.x;
+    const bool act = w < J.nwords;
+    uint32_t S = 0, V = 0, H = 0, S2 = 0, U2 = 0, R2 = 0;
+    if (act) {
+      load_lane_words<kEncMultispin>(J, J.A, w, 0u, S, V, H);
+      if (full) load_lane_words<kEncMultispin>(J, J.B, w, 1u, S2, U2, R2);
+    }
+    // agreement masks (1 = product +1)
+    const uint32_t act_m = act ? 0xffffffffu : 0u;
+    const uint32_t m_plus = S & act_m;
+    const uint32_t ag_v = ~(S ^ V) & act_m, ag_h = ~(S ^ H) & act_m;
+    const uint32_t ag_u = ~(S ^ U2) & act_m, ag_r = ~(S ^ R2) & act_m;
+    const uint32_t ag_s = ~(S ^ S2) & act_m, p2 = S2 & act_m;
+    int cnt[6] = {0, 0, 0, 0, 0, 0};
+    const int nact = __popc(__ballot_sync(0xffffffffu, act));
+#pragma unroll 4
+    for (int k = 0; k < 32; ++k) {
+      const int c0 = __popc(__ballot_sync(0xffffffffu, (m_plus >> k) & 1u));
+      const int c1 = __popc(__ballot_sync(0xffffffffu, (ag_v >> k) & 1u)) +
+                     __popc(__ballot_sync(0xffffffffu, (ag_h >> k) & 1u));
+      int c2 = 0, c3 = 0, c4 = 0;
+      if (full) {
+        c2 = __popc(__ballot_sync(0xffffffffu, (ag_u >> k) & 1u)) +
+             __popc(__ballot_sync(0xffffffffu, (ag_r >> k) & 1u));
+        c3 = __popc(__ballot_sync(0xffffffffu, (ag_s >> k) & 1u));
+        c4 = __popc(__ballot_sync(0xffffffffu, (p2 >> k) & 1u));
+      }
+      if (lane == k) {
+        cnt[0] = 2 * c0 - nact;          // sum sigma
+        cnt[1] = 2 * c1 - 2 * nact;      // in-edge products
+        cnt[2] = 2 * c2 - 2 * nact;      // P1
+        cnt[3] = 2 * c3 - nact;          // P2
+        cnt[4] = 2 * c4 - nact;          // M2
+        cnt[5] = 2 * nact - c1;          // cut = disagreements
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) red[warp][lane][q] = cnt[q];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      int tot[6] = {0, 0, 0, 0, 0, 0};
+      for (int wv = 0; wv < kTile / 32; ++wv)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) tot[q] += red[wv][threadIdx.x][q];
+      double* dst = (which ? J.obs : J.sums) + (size_t)threadIdx.x * kNumSums;
+      if (tot[0]) atomicAdd(dst + kSumM, (double)tot[0]);
+      if (tot[1]) atomicAdd(dst + kSumE, (double)tot[1]);
+      if (full) {
+        if (tot[2]) atomicAdd(dst + kSumP1, (double)tot[2]);
+        if (tot[3]) atomicAdd(dst + kSumP2, (double)tot[3]);
+        if (tot[4]) atomicAdd(dst + kSumM2, (double)tot[4]);
+      }
+      if (tot[5]) atomicAdd(dst + kSumCut, (double)tot[5]);
+    }
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------------------------------- launchers
+static int grid_for(int n_tiles, int per_sm) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int g = sms * per_sm;
+  return n_tiles < g ? (n_tiles > 0 ? n_tiles : 1) : g;
+}
+
+cudaError_t launch_build_lattice_tables(const double* beta_lanes, int ntab, double J, double q,
+                                        double lam, LatTable* out, cudaStream_t st) {
+  if (ntab <= 0) return cudaSuccess;
+  build_lattice_tables_kernel<<<ntab, 256, 0, st>>>(beta_lanes, ntab, J, q, lam, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lattice_half(int enc, const LatJob* jobs, const Tile* tiles, int n_tiles,
+                                uint32_t half, int blocks_per_sm, unsigned long long* rng_calls,
+                                cudaStream_t st) {
+  if (n_tiles <= 0) return cudaSuccess;
+  const int grid = grid_for(n_tiles, blocks_per_sm);
+  switch (enc) {
+    case kEncInt8:
+      lattice_half_kernel<kEncInt8><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, half, rng_calls);
+      break;
+    case kEncPacked:
+      lattice_half_kernel<kEncPacked><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, half,
+                                                              rng_calls);
+      break;
+    default:
+      lattice_half_kernel<kEncMultispin><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, half,
+                                                                 rng_calls);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lattice_init(int enc, const LatJob* jobs, const Tile* tiles, int n_tiles,
+                                int kind, cudaStream_t st) {
+  if (n_tiles <= 0) return cudaSuccess;
+  const int grid = grid_for(n_tiles, 8);
+  switch (enc) {
+    case kEncInt8:
+      lattice_init_kernel<kEncInt8><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, kind);
+      break;
+    case kEncPacked:
+      lattice_init_kernel<kEncPacked><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, kind);
+      break;
+    default:
+      lattice_init_kernel<kEncMultispin><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, kind);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lattice_obs(int enc, const LatJob* jobs, const Tile* tiles, int n_tiles,
+                               int which, int full, cudaStream_t st) {
+  if (n_tiles <= 0) return cudaSuccess;
+  const int grid = grid_for(n_tiles, 8);
+  switch (enc) {
+    case kEncInt8:
+      lattice_obs_single_kernel<kEncInt8><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, which, full);
+      break;
+    case kEncPacked:
+      lattice_obs_single_kernel<kEncPacked><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, which,
+                                                                    full);
+      break;
+    default:
+      lattice_obs_multispin_kernel<<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, which, full);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace shk

@@ -1,0 +1,1503 @@
+// runtime.cu -- host runtime of libshaken: the C ABI declared in include/shaken.h.
+//
+// A context owns one problem (lattice or graph), its double-buffered device
+// state, the threshold tables, the oriented in/out CSR of a graph (Sec. 2:
+// E^o from an orientation rule; in-neighbours feed h^{1->2}, out-neighbours
+// h^{2->1}) and a launch plan.  A plan holds the device job and tile lists of
+// a set of contexts (one context alone, or the members of a batch); one step
+// of a plan is
+//   [tracking sums of multispin / graph members] -> half 0 (one launch per
+//   encoding family) -> half 1 -> epilogue (best energy, series, t += 1).
+// The step counter of each context lives on the device (CtxDev), so a chunk
+// of steps can be captured once into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/shaken.h"
+#include "shaken_internal.cuh"
+
+namespace shk {
+cudaError_t launch_build_lattice_tables(const double*, int, double, double, double, LatTable*,
+                                        cudaStream_t);
+cudaError_t launch_lattice_half(int, const LatJob*, const Tile*, int, uint32_t, int,
+                                unsigned long long*, cudaStream_t);
+cudaError_t run_microbench(int, double*, double*);
+cudaError_t launch_lattice_init(int, const LatJob*, const Tile*, int, int, cudaStream_t);
+cudaError_t launch_lattice_obs(int, const LatJob*, const Tile*, int, int, int, cudaStream_t);
+cudaError_t launch_graph_half(bool, const GraphJob*, const Tile*, int, uint32_t, int, int,
+                              cudaStream_t);
+cudaError_t launch_graph_init(const GraphJob*, const Tile*, int, int, cudaStream_t);
+cudaError_t launch_graph_obs(const GraphJob*, const Tile*, int, int, int, cudaStream_t);
+cudaError_t launch_graph_fields(const GraphJob*, const Tile*, int, uint32_t, float*,
+                                cudaStream_t);
+cudaError_t launch_epilogue(CtxDev* const*, int, cudaStream_t);
+cudaError_t launch_philox(uint64_t, const uint32_t*, uint32_t*, int64_t, cudaStream_t);
+cudaError_t launch_threshold(const double*, const double*, uint64_t*, int64_t, cudaStream_t);
+}  // namespace shk
+
+using shk::CtxDev;
+using shk::GraphJob;
+using shk::LatJob;
+using shk::LatTable;
+using shk::Tile;
+using shk::kNumSums;
+using shk::kTile;
+
+// ============================================================================ errors
+static thread_local std::string g_last_error;
+
+static shaken_status fail(shaken_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define CU(call)                                                                    \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      cudaGetLastError();                                                           \
+      return fail(e_ == cudaErrorMemoryAllocation ? SHAKEN_E_NOMEM : SHAKEN_E_CUDA, \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));              \
+    }                                                                               \
+  } while (0)
+
+#define TRY(expr)                   \
+  do {                              \
+    shaken_status s_ = (expr);      \
+    if (s_ != SHAKEN_OK) return s_; \
+  } while (0)
+
+// ============================================================================ device memory
+struct DevMem {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevMem() = default;
+  DevMem(const DevMem&) = delete;
+  DevMem& operator=(const DevMem&) = delete;
+  ~DevMem() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  shaken_status alloc(size_t n) {
+    release();
+    if (n == 0) n = 16;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      return fail(SHAKEN_E_NOMEM,
+                  "cudaMalloc(" + std::to_string(n) + "): " + cudaGetErrorString(e));
+    }
+    bytes = n;
+    return SHAKEN_OK;
+  }
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+static shaken_status upload(DevMem& d, const void* src, size_t n, cudaStream_t st) {
+  if (d.p == nullptr || d.bytes < n) TRY(d.alloc(n));
+  if (n) CU(cudaMemcpyAsync(d.p, src, n, cudaMemcpyHostToDevice, st));
+  return SHAKEN_OK;
+}
+
+// ============================================================================ plan
+struct Family {
+  int kind = 0;  // 0 lattice, 1 graph
+  int enc = 0;   // lattice encoding; graph: 1 integer couplings, 0 real
+  DevMem jobs, tiles;
+  int n_tiles = 0;
+};
+
+struct Plan {
+  std::vector<shaken_ctx*> members;
+  std::vector<std::unique_ptr<Family>> fams;
+  DevMem ctxlist;
+  int n_ctx = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int graph_steps = 0;
+  uint64_t graph_launches = 0;
+  bool dirty = true;
+  int blocks_per_sm = 8;
+  bool timing = false;
+  unsigned long long* rng_counter = nullptr;  // device counter of Philox calls (lattice), or null
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+  double timed_ms = 0.0;
+  uint64_t timed_n = 0;
+  ~Plan() {
+    drop_graph();
+    for (auto& pr : ev_pending) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+    for (cudaEvent_t e : ev_free) cudaEventDestroy(e);
+  }
+  cudaEvent_t get_event() {
+    if (!ev_free.empty()) {
+      cudaEvent_t e = ev_free.back();
+      ev_free.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void collect() {
+    for (auto& pr : ev_pending) {
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
+        timed_ms += ms;
+        timed_n++;
+      }
+      ev_free.push_back(pr.first);
+      ev_free.push_back(pr.second);
+    }
+    ev_pending.clear();
+  }
+  void drop_graph() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    gexec = nullptr;
+    graph = nullptr;
+    graph_steps = 0;
+  }
+  void invalidate() {
+    dirty = true;
+    drop_graph();
+  }
+};
+
+// ============================================================================ context
+struct shaken_ctx {
+  int kind = 0, enc = 0;
+  int64_t L = 0, n = 0, m = 0;
+  int R = 0;
+  double J = 0, q = 0, lam_c = 0;
+  bool has_lambda = false, integer = false;
+  std::vector<float> lambda;
+  std::vector<uint8_t> frozen;  // [n], empty = none
+  std::vector<double> beta;     // [R]
+  double sumJ = 0.0;            // sum of couplings over E (cut weight)
+  uint64_t seed = 0;
+  cudaStream_t stream = nullptr;
+  DevMem A, B;
+  size_t spin_bytes = 0;
+  DevMem frozen_lanes;
+  DevMem tables, beta_lanes;
+  DevMem anneal_tables, anneal_sched, anneal_lanes;
+  DevMem cd;
+  DevMem step_sums, obs_sums, best, best_step;
+  DevMem series_m, series_H;
+  DevMem in_ptr, in_col, in_J, out_ptr, out_col, out_J, lam_dev;
+  CtxDev hcd{};
+  uint64_t host_step = 0;
+  bool tracking = false;
+  shaken_batch* owner = nullptr;
+  Plan solo;
+  std::atomic<uint64_t> launches{0};
+  int exact_always = 0;
+
+  int64_t sites() const { return kind == SHAKEN_LATTICE ? L * L : n; }
+};
+
+struct shaken_batch {
+  cudaStream_t stream = nullptr;
+  Plan plan;
+  std::atomic<uint64_t> launches{0};
+};
+
+static cudaStream_t ctx_stream(const shaken_ctx* c) {
+  return c->owner ? c->owner->stream : c->stream;
+}
+
+static void add_tiles(std::vector<Tile>& tiles, uint32_t job, uint64_t count) {
+  for (uint64_t w = 0; w < count; w += kTile) tiles.push_back(Tile{job, (uint32_t)w});
+}
+
+static shaken_status build_plan(Plan& P, cudaStream_t st) {
+  P.fams.clear();
+  P.drop_graph();
+  std::vector<std::vector<LatJob>> ljobs(3);
+  std::vector<std::vector<GraphJob>> gjobs(2);  // 0 integer, 1 real
+  std::vector<std::vector<Tile>> tiles(5);
+  std::vector<CtxDev*> cds;
+  for (shaken_ctx* c : P.members) {
+    CtxDev* cdp = c->cd.as<CtxDev>();
+    cds.push_back(cdp);
+    const uint32_t key0 = (uint32_t)(c->seed & 0xffffffffu), key1 = (uint32_t)(c->seed >> 32);
+    if (c->kind == SHAKEN_LATTICE) {
+      const int e = c->enc;
+      const bool multi = e == SHAKEN_MULTISPIN;
+      const int njobs = multi ? c->R / 32 : c->R;
+      const uint32_t L = (uint32_t)c->L;
+      const uint32_t wpr = multi ? L : L / 32u;
+      const uint32_t nwords = L * wpr;
+      const size_t job_bytes = c->spin_bytes / (size_t)njobs;
+      for (int j = 0; j < njobs; ++j) {
+        LatJob J{};
+        J.A = c->A.as<uint8_t>() + job_bytes * j;
+        J.B = c->B.as<uint8_t>() + job_bytes * j;
+        J.frozen = c->frozen_lanes.p ? c->frozen_lanes.as<uint32_t>() : nullptr;
+        J.table = c->tables.as<LatTable>() + j;
+        J.anneal_tables = c->anneal_tables.p ? c->anneal_tables.as<LatTable>() : nullptr;
+        J.cd = cdp;
+        const int rep0 = multi ? 32 * j : j;
+        J.sums = c->step_sums.as<double>() + (size_t)rep0 * kNumSums;
+        J.obs = c->obs_sums.as<double>() + (size_t)rep0 * kNumSums;
+        J.L = L;
+        J.wpr = wpr;
+        J.nwords = nwords;
+        J.b = (uint32_t)j;
+        J.key0 = key0;
+        J.key1 = key1;
+        J.rep0 = (uint32_t)rep0;
+        add_tiles(tiles[e], (uint32_t)ljobs[e].size(), nwords);
+        ljobs[e].push_back(J);
+      }
+    } else {
+      const int fi = c->integer ? 0 : 1;
+      const int ng = c->R / 32;
+      for (int g = 0; g < ng; ++g) {
+        GraphJob J{};
+        J.A = c->A.as<uint32_t>() + (size_t)g * c->n;
+        J.B = c->B.as<uint32_t>() + (size_t)g * c->n;
+        J.in_ptr = c->in_ptr.as<int32_t>();
+        J.in_col = c->in_col.as<uint32_t>();
+        J.in_J = c->integer ? nullptr : c->in_J.as<float>();
+        J.out_ptr = c->out_ptr.as<int32_t>();
+        J.out_col = c->out_col.as<uint32_t>();
+        J.out_J = c->integer ? nullptr : c->out_J.as<float>();
+        J.lambda = c->has_lambda ? c->lam_dev.as<float>() : nullptr;
+        J.frozen = c->frozen_lanes.p ? c->frozen_lanes.as<uint32_t>() : nullptr;
+        J.beta_lane = c->beta_lanes.as<double>() + 32 * g;
+        J.beta_sched = c->anneal_sched.p ? c->anneal_sched.as<double>() : nullptr;
+        J.cd = cdp;
+        J.sums = c->step_sums.as<double>() + (size_t)32 * g * kNumSums;
+        J.obs = c->obs_sums.as<double>() + (size_t)32 * g * kNumSums;
+        J.q = c->q;
+        J.lambda_c = (float)c->lam_c;
+        J.n = (uint32_t)c->n;
+        J.b = (uint32_t)g;
+        J.key0 = key0;
+        J.key1 = key1;
+        J.integer = c->integer ? 1u : 0u;
+        J.rep0 = (uint32_t)(32 * g);
+        add_tiles(tiles[3 + fi], (uint32_t)gjobs[fi].size(), (uint64_t)c->n);
+        gjobs[fi].push_back(J);
+      }
+    }
+  }
+  for (int e = 0; e < 3; ++e) {
+    if (ljobs[e].empty()) continue;
+    auto F = std::make_unique<Family>();
+    F->kind = 0;
+    F->enc = e;
+    TRY(upload(F->jobs, ljobs[e].data(), ljobs[e].size() * sizeof(LatJob), st));
+    TRY(upload(F->tiles, tiles[e].data(), tiles[e].size() * sizeof(Tile), st));
+    F->n_tiles = (int)tiles[e].size();
+    P.fams.push_back(std::move(F));
+  }
+  for (int fi = 0; fi < 2; ++fi) {
+    if (gjobs[fi].empty()) continue;
+    auto F = std::make_unique<Family>();
+    F->kind = 1;
+    F->enc = fi == 0 ? 1 : 0;
+    TRY(upload(F->jobs, gjobs[fi].data(), gjobs[fi].size() * sizeof(GraphJob), st));
+    TRY(upload(F->tiles, tiles[3 + fi].data(), tiles[3 + fi].size() * sizeof(Tile), st));
+    F->n_tiles = (int)tiles[3 + fi].size();
+    P.fams.push_back(std::move(F));
+  }
+  TRY(upload(P.ctxlist, cds.data(), cds.size() * sizeof(CtxDev*), st));
+  P.n_ctx = (int)cds.size();
+  P.dirty = false;
+  return SHAKEN_OK;
+}
+
+static shaken_status plan_step_launch(Plan& P, cudaStream_t st, uint64_t* nl,
+                                      bool capturing = false) {
+  uint64_t count = 0;
+  const bool timed = P.timing && !capturing;
+  bool obs_needed = false;
+  int ex = 0;
+  for (shaken_ctx* c : P.members) {
+    if (c->hcd.tracking && (c->kind == SHAKEN_GRAPH || c->enc == SHAKEN_MULTISPIN))
+      obs_needed = true;
+    ex |= c->exact_always;
+  }
+  if (obs_needed) {
+    for (auto& F : P.fams) {
+      if (F->kind == 0 && F->enc == SHAKEN_MULTISPIN) {
+        CU(shk::launch_lattice_obs(F->enc, F->jobs.as<LatJob>(), F->tiles.as<Tile>(), F->n_tiles,
+                                   0, 0, st));
+        ++count;
+      } else if (F->kind == 1) {
+        CU(shk::launch_graph_obs(F->jobs.as<GraphJob>(), F->tiles.as<Tile>(), F->n_tiles, 0, 0,
+                                 st));
+        ++count;
+      }
+    }
+  }
+  for (uint32_t half = 0; half < 2; ++half) {
+    for (auto& F : P.fams) {
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (timed) {
+        e0 = P.get_event();
+        e1 = P.get_event();
+        CU(cudaEventRecord(e0, st));
+      }
+      if (F->kind == 0)
+        CU(shk::launch_lattice_half(F->enc, F->jobs.as<LatJob>(), F->tiles.as<Tile>(),
+                                    F->n_tiles, half, P.blocks_per_sm, P.rng_counter, st));
+      else
+        CU(shk::launch_graph_half(F->enc != 0, F->jobs.as<GraphJob>(), F->tiles.as<Tile>(),
+                                  F->n_tiles, half, ex, P.blocks_per_sm, st));
+      ++count;
+      if (timed) {
+        CU(cudaEventRecord(e1, st));
+        P.ev_pending.emplace_back(e0, e1);
+      }
+    }
+  }
+  CU(shk::launch_epilogue(P.ctxlist.as<CtxDev*>(), P.n_ctx, st));
+  ++count;
+  *nl += count;
+  return SHAKEN_OK;
+}
+
+static constexpr int kGraphChunk = 32;
+
+static shaken_status plan_run(Plan& P, cudaStream_t st, uint64_t n_steps, bool use_graph,
+                              uint64_t* nl) {
+  if (P.dirty) TRY(build_plan(P, st));
+  uint64_t done = 0;
+  if (use_graph && n_steps >= (uint64_t)kGraphChunk) {
+    if (!P.gexec) {
+      cudaStream_t cap = nullptr;
+      CU(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+      cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) {
+        cudaStreamDestroy(cap);
+        cudaGetLastError();
+        return fail(SHAKEN_E_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+      }
+      uint64_t cnt = 0;
+      shaken_status s = SHAKEN_OK;
+      for (int k = 0; k < kGraphChunk && s == SHAKEN_OK; ++k)
+        s = plan_step_launch(P, cap, &cnt, true);
+      cudaGraph_t g = nullptr;
+      e = cudaStreamEndCapture(cap, &g);
+      cudaStreamDestroy(cap);
+      if (s != SHAKEN_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+      }
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SHAKEN_E_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
+      }
+      e = cudaGraphInstantiate(&P.gexec, g, 0);
+      if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(SHAKEN_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      }
+      P.graph = g;
+      P.graph_steps = kGraphChunk;
+      P.graph_launches = cnt;
+    }
+    while (n_steps - done >= (uint64_t)P.graph_steps) {
+      CU(cudaGraphLaunch(P.gexec, st));
+      *nl += P.graph_launches;
+      done += (uint64_t)P.graph_steps;
+    }
+  }
+  for (; done < n_steps; ++done) TRY(plan_step_launch(P, st, nl));
+  return SHAKEN_OK;
+}
+
+// ============================================================================ helpers
+static shaken_status push_cd(shaken_ctx* c) {
+  c->hcd.step = (uint32_t)c->host_step;
+  CU(cudaMemcpyAsync(c->cd.p, &c->hcd, sizeof(CtxDev), cudaMemcpyHostToDevice, ctx_stream(c)));
+  CU(cudaStreamSynchronize(ctx_stream(c)));
+  return SHAKEN_OK;
+}
+
+static bool is_finite_d(double x) { return std::isfinite(x); }
+
+static shaken_status build_tables_for_betas(shaken_ctx* c, const std::vector<double>& lanes,
+                                            DevMem& dst_tables, DevMem& dst_lanes, int ntab,
+                                            cudaStream_t st) {
+  TRY(upload(dst_lanes, lanes.data(), lanes.size() * sizeof(double), st));
+  if (dst_tables.p == nullptr || dst_tables.bytes < (size_t)ntab * sizeof(LatTable))
+    TRY(dst_tables.alloc((size_t)ntab * sizeof(LatTable)));
+  CU(shk::launch_build_lattice_tables(dst_lanes.as<double>(), ntab, c->J, c->q, c->lam_c,
+                                      dst_tables.as<LatTable>(), st));
+  c->launches++;
+  return SHAKEN_OK;
+}
+
+// Expand per-replica betas to the lanes of each table (lattice).
+static std::vector<double> lattice_table_lanes(const shaken_ctx* c) {
+  std::vector<double> lanes;
+  if (c->enc == SHAKEN_MULTISPIN) {
+    lanes.assign(c->beta.begin(), c->beta.end());
+  } else {
+    lanes.resize((size_t)c->R * 32);
+    for (int r = 0; r < c->R; ++r)
+      for (int k = 0; k < 32; ++k) lanes[(size_t)r * 32 + k] = c->beta[r];
+  }
+  return lanes;
+}
+
+static int lattice_ntab(const shaken_ctx* c) {
+  return c->enc == SHAKEN_MULTISPIN ? c->R / 32 : c->R;
+}
+
+// host spins [R][n] int8 <-> device encoding
+static void encode_spins(const shaken_ctx* c, const int8_t* in, std::vector<uint8_t>& out) {
+  const int64_t N = c->sites();
+  out.assign(c->spin_bytes, 0);
+  if (c->kind == SHAKEN_LATTICE && c->enc == SHAKEN_INT8) {
+    std::memcpy(out.data(), in, (size_t)c->R * N);
+    return;
+  }
+  uint32_t* w = reinterpret_cast<uint32_t*>(out.data());
+  if (c->kind == SHAKEN_LATTICE && c->enc == SHAKEN_PACKED) {
+    const int64_t words = N / 32;
+    for (int r = 0; r < c->R; ++r)
+      for (int64_t x = 0; x < N; ++x)
+        if (in[(size_t)r * N + x] > 0) w[(size_t)r * words + (x >> 5)] |= 1u << (x & 31);
+    return;
+  }
+  for (int r = 0; r < c->R; ++r) {
+    const int g = r >> 5, k = r & 31;
+    for (int64_t x = 0; x < N; ++x)
+      if (in[(size_t)r * N + x] > 0) w[(size_t)g * N + x] |= 1u << k;
+  }
+}
+
+static void decode_spins(const shaken_ctx* c, const std::vector<uint8_t>& in, int8_t* out) {
+  const int64_t N = c->sites();
+  if (c->kind == SHAKEN_LATTICE && c->enc == SHAKEN_INT8) {
+    std::memcpy(out, in.data(), (size_t)c->R * N);
+    return;
+  }
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(in.data());
+  if (c->kind == SHAKEN_LATTICE && c->enc == SHAKEN_PACKED) {
+    const int64_t words = N / 32;
+    for (int r = 0; r < c->R; ++r)
+      for (int64_t x = 0; x < N; ++x)
+        out[(size_t)r * N + x] = (w[(size_t)r * words + (x >> 5)] >> (x & 31)) & 1u ? 1 : -1;
+    return;
+  }
+  for (int r = 0; r < c->R; ++r) {
+    const int g = r >> 5, k = r & 31;
+    for (int64_t x = 0; x < N; ++x) out[(size_t)r * N + x] = (w[(size_t)g * N + x] >> k) & 1u ? 1 : -1;
+  }
+}
+
+static shaken_status validate(const shaken_problem* p) {
+  if (!p) return fail(SHAKEN_E_INVAL, "problem is NULL");
+  if (!(p->q > 0.0) || !is_finite_d(p->q)) return fail(SHAKEN_E_INVAL, "q must be finite and > 0");
+  if (p->replicas < 1) return fail(SHAKEN_E_INVAL, "replicas must be >= 1");
+  if (!p->beta) return fail(SHAKEN_E_INVAL, "beta is NULL");
+  for (int r = 0; r < p->replicas; ++r)
+    if (!is_finite_d(p->beta[r]) || p->beta[r] < 0.0)
+      return fail(SHAKEN_E_INVAL, "beta must be finite and >= 0");
+  if (!is_finite_d(p->lambda_const)) return fail(SHAKEN_E_INVAL, "lambda_const not finite");
+  if (p->init < 0 || p->init > 3) return fail(SHAKEN_E_INVAL, "bad init kind");
+  if (p->init == SHAKEN_INIT_GIVEN && !p->init_spins)
+    return fail(SHAKEN_E_INVAL, "init_spins is NULL");
+  if (p->kind == SHAKEN_LATTICE) {
+    if (p->L < 32 || p->L > 32768 || p->L % 32 != 0)
+      return fail(SHAKEN_E_INVAL, "lattice L must be a multiple of 32 in [32, 32768]");
+    if (p->encoding < 0 || p->encoding > 2) return fail(SHAKEN_E_INVAL, "bad encoding");
+    if (p->encoding == SHAKEN_MULTISPIN && p->replicas % 32 != 0)
+      return fail(SHAKEN_E_INVAL, "MULTISPIN needs replicas % 32 == 0");
+    if (!is_finite_d(p->J)) return fail(SHAKEN_E_INVAL, "J not finite");
+    if (p->boundary != 0 && p->boundary != 1) return fail(SHAKEN_E_INVAL, "bad boundary");
+  } else if (p->kind == SHAKEN_GRAPH) {
+    if (p->encoding != SHAKEN_MULTISPIN)
+      return fail(SHAKEN_E_INVAL, "graphs use the MULTISPIN encoding");
+    if (p->replicas % 32 != 0) return fail(SHAKEN_E_INVAL, "graphs need replicas % 32 == 0");
+    if (p->n < 1 || p->n >= (int64_t)1 << 31) return fail(SHAKEN_E_INVAL, "graph n out of range");
+    if (p->m < 0 || p->m >= (int64_t)1 << 31) return fail(SHAKEN_E_INVAL, "graph m out of range");
+    if (p->m > 0 && (!p->u || !p->v || !p->J_edge))
+      return fail(SHAKEN_E_INVAL, "graph edge arrays are NULL");
+    if (p->orientation != SHAKEN_ORIENT_MIN_MAX && p->orientation != SHAKEN_ORIENT_GIVEN)
+      return fail(SHAKEN_E_INVAL, "bad orientation");
+    for (int64_t e = 0; e < p->m; ++e) {
+      if (p->u[e] < 0 || p->u[e] >= p->n || p->v[e] < 0 || p->v[e] >= p->n)
+        return fail(SHAKEN_E_INVAL, "edge endpoint out of range at edge " + std::to_string(e));
+      if (p->u[e] == p->v[e]) return fail(SHAKEN_E_INVAL, "self-loop at edge " + std::to_string(e));
+      if (!std::isfinite(p->J_edge[e])) return fail(SHAKEN_E_INVAL, "J_edge not finite");
+      if (p->J_is_integer && p->J_edge[e] != 1.0f && p->J_edge[e] != -1.0f)
+        return fail(SHAKEN_E_INVAL, "J_is_integer but J_edge is not +-1");
+    }
+  } else {
+    return fail(SHAKEN_E_INVAL, "bad kind");
+  }
+  const int64_t N = p->kind == SHAKEN_LATTICE ? p->L * p->L : p->n;
+  if (p->lambda)
+    for (int64_t x = 0; x < N; ++x)
+      if (!std::isfinite(p->lambda[x])) return fail(SHAKEN_E_INVAL, "lambda not finite");
+  if (p->init == SHAKEN_INIT_GIVEN) {
+    for (int64_t i = 0; i < (int64_t)p->replicas * N; ++i) {
+      const int8_t s = p->init_spins[i];
+      if (s != 1 && s != -1) return fail(SHAKEN_E_INVAL, "init_spins must be +1/-1");
+    }
+  }
+  return SHAKEN_OK;
+}
+
+static shaken_status build_graph(shaken_ctx* c, const shaken_problem* p, cudaStream_t st) {
+  const int64_t n = p->n, m = p->m;
+  std::vector<int32_t> tail(m), head(m);
+  for (int64_t e = 0; e < m; ++e) {
+    if (p->orientation == SHAKEN_ORIENT_MIN_MAX) {
+      tail[e] = std::min(p->u[e], p->v[e]);
+      head[e] = std::max(p->u[e], p->v[e]);
+    } else {
+      tail[e] = p->u[e];
+      head[e] = p->v[e];
+    }
+  }
+  // in-CSR keyed by head (sources tail), out-CSR keyed by tail (heads); entries in edge order
+  auto csr = [&](const std::vector<int32_t>& key, const std::vector<int32_t>& other,
+                 std::vector<int32_t>& ptr, std::vector<uint32_t>& col, std::vector<float>& Jv) {
+    ptr.assign(n + 1, 0);
+    for (int64_t e = 0; e < m; ++e) ptr[key[e] + 1]++;
+    for (int64_t x = 0; x < n; ++x) ptr[x + 1] += ptr[x];
+    std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+    col.assign(m, 0);
+    Jv.assign(m, 0.0f);
+    for (int64_t e = 0; e < m; ++e) {
+      const int32_t pos = fill[key[e]]++;
+      uint32_t cv = (uint32_t)other[e];
+      if (c->integer && p->J_edge[e] < 0.0f) cv |= 0x80000000u;
+      col[pos] = cv;
+      Jv[pos] = p->J_edge[e];
+    }
+  };
+  std::vector<int32_t> iptr, optr;
+  std::vector<uint32_t> icol, ocol;
+  std::vector<float> iJ, oJ;
+  csr(head, tail, iptr, icol, iJ);
+  csr(tail, head, optr, ocol, oJ);
+  c->sumJ = 0.0;
+  for (int64_t e = 0; e < m; ++e) c->sumJ += (double)p->J_edge[e];
+  TRY(upload(c->in_ptr, iptr.data(), iptr.size() * 4, st));
+  TRY(upload(c->out_ptr, optr.data(), optr.size() * 4, st));
+  TRY(upload(c->in_col, icol.data(), icol.size() * 4, st));
+  TRY(upload(c->out_col, ocol.data(), ocol.size() * 4, st));
+  if (!c->integer) {
+    TRY(upload(c->in_J, iJ.data(), iJ.size() * 4, st));
+    TRY(upload(c->out_J, oJ.data(), oJ.size() * 4, st));
+  }
+  CU(cudaStreamSynchronize(st));  // host vectors die here
+  return SHAKEN_OK;
+}
+
+static shaken_status ctx_init_spins(shaken_ctx* c, int kind, const int8_t* given) {
+  cudaStream_t st = ctx_stream(c);
+  if (kind == SHAKEN_INIT_GIVEN) {
+    std::vector<uint8_t> enc;
+    encode_spins(c, given, enc);
+    CU(cudaMemcpyAsync(c->A.p, enc.data(), enc.size(), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(c->B.p, enc.data(), enc.size(), cudaMemcpyHostToDevice, st));
+    CU(cudaStreamSynchronize(st));
+    return SHAKEN_OK;
+  }
+  if (c->solo.dirty) TRY(build_plan(c->solo, st));
+  for (auto& F : c->solo.fams) {
+    if (F->kind == 0)
+      CU(shk::launch_lattice_init(F->enc, F->jobs.as<LatJob>(), F->tiles.as<Tile>(), F->n_tiles,
+                                  kind, st));
+    else
+      CU(shk::launch_graph_init(F->jobs.as<GraphJob>(), F->tiles.as<Tile>(), F->n_tiles, kind,
+                                st));
+    c->launches++;
+  }
+  return SHAKEN_OK;
+}
+
+static shaken_status reset_best(shaken_ctx* c) {
+  std::vector<double> b(c->R, INFINITY);
+  std::vector<long long> bs(c->R, -1);
+  cudaStream_t st = ctx_stream(c);
+  CU(cudaMemcpyAsync(c->best.p, b.data(), b.size() * 8, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(c->best_step.p, bs.data(), bs.size() * 8, cudaMemcpyHostToDevice, st));
+  CU(cudaStreamSynchronize(st));
+  return SHAKEN_OK;
+}
+
+// ============================================================================ C ABI: contexts
+extern "C" {
+
+shaken_status shaken_init(shaken_ctx** out, const shaken_problem* p, uint64_t seed,
+                          void* cuda_stream) {
+  if (!out) return fail(SHAKEN_E_INVAL, "out is NULL");
+  *out = nullptr;
+  TRY(validate(p));
+  std::unique_ptr<shaken_ctx> c(new shaken_ctx());
+  c->kind = p->kind;
+  c->enc = p->encoding;
+  c->L = p->L;
+  c->n = p->kind == SHAKEN_LATTICE ? p->L * p->L : p->n;
+  c->m = p->kind == SHAKEN_LATTICE ? 2 * c->n : p->m;
+  c->R = p->replicas;
+  c->J = p->J;
+  c->q = p->q;
+  c->lam_c = p->lambda_const;
+  c->seed = seed;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->integer = p->kind == SHAKEN_GRAPH && p->J_is_integer;
+  c->beta.assign(p->beta, p->beta + p->replicas);
+  const int64_t N = c->sites();
+  if (p->lambda) {
+    if (p->kind == SHAKEN_LATTICE)
+      return fail(SHAKEN_E_INVAL, "lattices take a constant lambda (lambda_const)");
+    c->has_lambda = true;
+    c->lambda.assign(p->lambda, p->lambda + N);
+  }
+  if (p->frozen_mask || (p->kind == SHAKEN_LATTICE && p->boundary == 1)) {
+    c->frozen.assign(N, 0);
+    if (p->frozen_mask) {
+      for (int64_t x = 0; x < N; ++x) c->frozen[x] = p->frozen_mask[x] ? 1 : 0;
+    } else {
+      for (int64_t j = 0; j < c->L; ++j) c->frozen[j] = 1;
+      for (int64_t i = 0; i < c->L; ++i) c->frozen[i * c->L] = 1;
+    }
+    if (p->init == SHAKEN_INIT_GIVEN)
+      for (int r = 0; r < c->R; ++r)
+        for (int64_t x = 0; x < N; ++x)
+          if (c->frozen[x] && p->init_spins[(size_t)r * N + x] != 1)
+            return fail(SHAKEN_E_INVAL, "frozen sites must be +1 in init_spins");
+  }
+  cudaStream_t st = c->stream;
+  // spin buffers
+  if (c->kind == SHAKEN_LATTICE) {
+    if (c->enc == SHAKEN_INT8)
+      c->spin_bytes = (size_t)c->R * N;
+    else if (c->enc == SHAKEN_PACKED)
+      c->spin_bytes = (size_t)c->R * N / 8;
+    else
+      c->spin_bytes = (size_t)(c->R / 32) * N * 4;
+  } else {
+    c->spin_bytes = (size_t)(c->R / 32) * N * 4;
+  }
+  TRY(c->A.alloc(c->spin_bytes));
+  TRY(c->B.alloc(c->spin_bytes));
+  // frozen lane masks
+  if (!c->frozen.empty()) {
+    std::vector<uint32_t> fl;
+    if (c->kind == SHAKEN_LATTICE && c->enc != SHAKEN_MULTISPIN) {
+      fl.assign(N / 32, 0u);
+      for (int64_t x = 0; x < N; ++x)
+        if (c->frozen[x]) fl[x >> 5] |= 1u << (x & 31);
+    } else {
+      fl.assign(N, 0u);
+      for (int64_t x = 0; x < N; ++x) fl[x] = c->frozen[x] ? 0xffffffffu : 0u;
+    }
+    TRY(upload(c->frozen_lanes, fl.data(), fl.size() * 4, st));
+    CU(cudaStreamSynchronize(st));
+  }
+  // graph structure, lambda, betas
+  if (c->kind == SHAKEN_GRAPH) {
+    TRY(build_graph(c.get(), p, st));
+    if (c->has_lambda) TRY(upload(c->lam_dev, c->lambda.data(), c->lambda.size() * 4, st));
+    TRY(upload(c->beta_lanes, c->beta.data(), c->beta.size() * 8, st));
+    CU(cudaStreamSynchronize(st));
+  } else {
+    const std::vector<double> lanes = lattice_table_lanes(c.get());
+    TRY(build_tables_for_betas(c.get(), lanes, c->tables, c->beta_lanes, lattice_ntab(c.get()),
+                               st));
+    CU(cudaStreamSynchronize(st));
+  }
+  // sums, best, ctx record
+  const size_t sums_bytes = (size_t)c->R * kNumSums * sizeof(double);
+  TRY(c->step_sums.alloc(sums_bytes));
+  TRY(c->obs_sums.alloc(sums_bytes));
+  CU(cudaMemsetAsync(c->step_sums.p, 0, sums_bytes, st));
+  TRY(c->best.alloc((size_t)c->R * 8));
+  TRY(c->best_step.alloc((size_t)c->R * 8));
+  TRY(c->cd.alloc(sizeof(CtxDev)));
+  CtxDev& h = c->hcd;
+  std::memset(&h, 0, sizeof(h));
+  h.step = 0;
+  h.t_end = 0xFFFFFFFEu;
+  h.R = (uint32_t)c->R;
+  h.kind = (uint32_t)c->kind;
+  h.Jc = c->kind == SHAKEN_LATTICE ? c->J : 1.0;
+  h.lamc = c->kind == SHAKEN_LATTICE ? c->lam_c : 0.0;
+  h.inv_n = 1.0 / (double)N;
+  h.step_sums = c->step_sums.as<double>();
+  h.best = c->best.as<double>();
+  h.best_step = c->best_step.as<long long>();
+  TRY(push_cd(c.get()));
+  TRY(reset_best(c.get()));
+  c->solo.members = {c.get()};
+  c->solo.dirty = true;
+  TRY(ctx_init_spins(c.get(), p->init, p->init_spins));
+  CU(cudaStreamSynchronize(st));
+  *out = c.release();
+  return SHAKEN_OK;
+}
+
+void shaken_free(shaken_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->owner) shaken_batch_remove(ctx->owner, ctx);
+  cudaStreamSynchronize(ctx->stream);
+  delete ctx;
+}
+
+static shaken_status check_steps(shaken_ctx* c, uint64_t n) {
+  if (c->host_step + n >= 0xFFFFFFFEull)
+    return fail(SHAKEN_E_INVAL, "step counter would reach 2^32 - 2");
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_step(shaken_ctx* ctx, uint64_t n_steps) {
+  if (!ctx) return fail(SHAKEN_E_INVAL, "ctx is NULL");
+  if (ctx->owner) return fail(SHAKEN_E_STATE, "context belongs to a batch");
+  TRY(check_steps(ctx, n_steps));
+  uint64_t nl = 0;
+  shaken_status s = plan_run(ctx->solo, ctx->stream, n_steps, n_steps >= 64, &nl);
+  ctx->launches += nl;
+  if (s != SHAKEN_OK) return s;
+  ctx->host_step += n_steps;
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_set_tracking(shaken_ctx* ctx, int enable) {
+  if (!ctx) return fail(SHAKEN_E_INVAL, "ctx is NULL");
+  ctx->tracking = enable != 0;
+  ctx->hcd.tracking = ctx->tracking ? 1u : 0u;
+  ctx->solo.invalidate();
+  if (ctx->owner) ctx->owner->plan.invalidate();
+  return push_cd(ctx);
+}
+
+// Prepare an anneal of n steps from the current step (tables / schedule on the
+// device, tracking on).  Used by shaken_anneal and by the server.
+static shaken_status begin_anneal(shaken_ctx* c, const double* sched, uint64_t n) {
+  if (!sched) return fail(SHAKEN_E_INVAL, "beta_schedule is NULL");
+  for (uint64_t k = 0; k < n; ++k)
+    if (!std::isfinite(sched[k]) || sched[k] < 0.0)
+      return fail(SHAKEN_E_INVAL, "beta_schedule must be finite and >= 0");
+  cudaStream_t st = ctx_stream(c);
+  if (c->kind == SHAKEN_LATTICE) {
+    std::vector<double> lanes((size_t)n * 32);
+    for (uint64_t k = 0; k < n; ++k)
+      for (int l = 0; l < 32; ++l) lanes[k * 32 + l] = sched[k];
+    TRY(build_tables_for_betas(c, lanes, c->anneal_tables, c->anneal_lanes, (int)n, st));
+  } else {
+    TRY(upload(c->anneal_sched, sched, n * sizeof(double), st));
+  }
+  CU(cudaStreamSynchronize(st));
+  c->hcd.anneal_t0 = (uint32_t)c->host_step;
+  c->hcd.anneal_len = (uint32_t)n;
+  c->hcd.tracking = 1u;
+  c->solo.invalidate();
+  if (c->owner) c->owner->plan.invalidate();
+  return push_cd(c);
+}
+
+static shaken_status end_anneal(shaken_ctx* c) {
+  c->hcd.anneal_len = 0u;
+  c->hcd.tracking = c->tracking ? 1u : 0u;
+  c->solo.invalidate();
+  if (c->owner) c->owner->plan.invalidate();
+  return push_cd(c);
+}
+
+shaken_status shaken_anneal(shaken_ctx* ctx, const double* beta_schedule, uint64_t n_steps) {
+  if (!ctx) return fail(SHAKEN_E_INVAL, "ctx is NULL");
+  if (ctx->owner) return fail(SHAKEN_E_STATE, "context belongs to a batch");
+  if (n_steps == 0) return SHAKEN_OK;
+  TRY(check_steps(ctx, n_steps));
+  TRY(begin_anneal(ctx, beta_schedule, n_steps));
+  uint64_t nl = 0;
+  shaken_status s = plan_run(ctx->solo, ctx->stream, n_steps, n_steps >= 64, &nl);
+  ctx->launches += nl;
+  if (s != SHAKEN_OK) return s;
+  ctx->host_step += n_steps;
+  return end_anneal(ctx);
+}
+
+shaken_status shaken_step_record(shaken_ctx* ctx, uint64_t n_steps, double* mag, double* energy) {
+  if (!ctx) return fail(SHAKEN_E_INVAL, "ctx is NULL");
+  if (ctx->owner) return fail(SHAKEN_E_STATE, "context belongs to a batch");
+  TRY(check_steps(ctx, n_steps));
+  if (n_steps == 0) return SHAKEN_OK;
+  const size_t bytes = (size_t)n_steps * ctx->R * sizeof(double);
+  TRY(ctx->series_m.alloc(bytes));
+  TRY(ctx->series_H.alloc(bytes));
+  ctx->hcd.record = 1u;
+  ctx->hcd.series_t0 = (uint32_t)ctx->host_step;
+  ctx->hcd.series_cap = (uint32_t)n_steps;
+  ctx->hcd.series_m = ctx->series_m.as<double>();
+  ctx->hcd.series_H = ctx->series_H.as<double>();
+  ctx->hcd.tracking = 1u;
+  ctx->solo.invalidate();
+  TRY(push_cd(ctx));
+  uint64_t nl = 0;
+  shaken_status s = plan_run(ctx->solo, ctx->stream, n_steps, n_steps >= 64, &nl);
+  ctx->launches += nl;
+  if (s != SHAKEN_OK) return s;
+  ctx->host_step += n_steps;
+  if (mag) CU(cudaMemcpyAsync(mag, ctx->series_m.p, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  if (energy)
+    CU(cudaMemcpyAsync(energy, ctx->series_H.p, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  ctx->hcd.record = 0u;
+  ctx->hcd.series_m = nullptr;
+  ctx->hcd.series_H = nullptr;
+  ctx->hcd.tracking = ctx->tracking ? 1u : 0u;
+  ctx->solo.invalidate();
+  TRY(push_cd(ctx));
+  ctx->series_m.release();
+  ctx->series_H.release();
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_observables(shaken_ctx* ctx, shaken_obs* out) {
+  if (!ctx || !out) return fail(SHAKEN_E_INVAL, "NULL argument");
+  cudaStream_t st = ctx_stream(ctx);
+  if (ctx->solo.dirty) TRY(build_plan(ctx->solo, st));
+  CU(cudaMemsetAsync(ctx->obs_sums.p, 0, ctx->obs_sums.bytes, st));
+  for (auto& F : ctx->solo.fams) {
+    if (F->kind == 0)
+      CU(shk::launch_lattice_obs(F->enc, F->jobs.as<LatJob>(), F->tiles.as<Tile>(), F->n_tiles, 1,
+                                 1, st));
+    else
+      CU(shk::launch_graph_obs(F->jobs.as<GraphJob>(), F->tiles.as<Tile>(), F->n_tiles, 1, 1,
+                               st));
+    ctx->launches++;
+  }
+  const int R = ctx->R;
+  std::vector<double> sums((size_t)R * kNumSums), best(R);
+  std::vector<long long> bstep(R);
+  CU(cudaMemcpyAsync(sums.data(), ctx->obs_sums.p, sums.size() * 8, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(best.data(), ctx->best.p, best.size() * 8, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(bstep.data(), ctx->best_step.p, bstep.size() * 8, cudaMemcpyDeviceToHost,
+                     st));
+  CU(cudaStreamSynchronize(st));
+  const double N = (double)ctx->sites();
+  bool changed = false;
+  for (int r = 0; r < R; ++r) {
+    const double* s = &sums[(size_t)r * kNumSums];
+    shaken_obs& o = out[r];
+    o.magnetization = s[shk::kSumM] / N;
+    o.cut_edges = (int64_t)llround(s[shk::kSumCut]);
+    if (ctx->kind == SHAKEN_LATTICE) {
+      const double J = ctx->J, lam = ctx->lam_c, q = ctx->q;
+      o.energy = -(J * s[shk::kSumE]) - 2.0 * lam * s[shk::kSumM];
+      o.pair_energy = -(J * s[shk::kSumP1] + q * s[shk::kSumP2] +
+                        lam * (s[shk::kSumM] + s[shk::kSumM2]));
+      o.cut_weight = -J * s[shk::kSumCut];
+    } else {
+      o.energy = -s[shk::kSumE] - 2.0 * s[shk::kSumLS];
+      o.pair_energy = -(s[shk::kSumP1] + ctx->q * s[shk::kSumP2] + s[shk::kSumLS] +
+                        s[shk::kSumLS2]);
+      o.cut_weight = 0.5 * (s[shk::kSumE] - ctx->sumJ);
+    }
+    if (o.energy < best[r]) {
+      best[r] = o.energy;
+      bstep[r] = (long long)ctx->host_step;
+      changed = true;
+    }
+    o.best_energy = best[r];
+    o.best_step = bstep[r];
+  }
+  if (changed) {
+    CU(cudaMemcpyAsync(ctx->best.p, best.data(), best.size() * 8, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(ctx->best_step.p, bstep.data(), bstep.size() * 8, cudaMemcpyHostToDevice,
+                       st));
+    CU(cudaStreamSynchronize(st));
+  }
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_get_spins(shaken_ctx* ctx, int8_t* out) {
+  if (!ctx || !out) return fail(SHAKEN_E_INVAL, "NULL argument");
+  std::vector<uint8_t> buf(ctx->spin_bytes);
+  cudaStream_t st = ctx_stream(ctx);
+  CU(cudaMemcpyAsync(buf.data(), ctx->A.p, buf.size(), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  decode_spins(ctx, buf, out);
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_set_spins(shaken_ctx* ctx, const int8_t* in) {
+  if (!ctx || !in) return fail(SHAKEN_E_INVAL, "NULL argument");
+  const int64_t N = ctx->sites();
+  for (int64_t i = 0; i < (int64_t)ctx->R * N; ++i) {
+    if (in[i] != 1 && in[i] != -1) return fail(SHAKEN_E_INVAL, "spins must be +1/-1");
+    if (!ctx->frozen.empty() && ctx->frozen[i % N] && in[i] != 1)
+      return fail(SHAKEN_E_INVAL, "frozen sites must be +1");
+  }
+  return ctx_init_spins(ctx, SHAKEN_INIT_GIVEN, in);
+}
+
+shaken_status shaken_state_bytes(shaken_ctx* ctx, size_t* bytes) {
+  if (!ctx || !bytes) return fail(SHAKEN_E_INVAL, "NULL argument");
+  *bytes = ctx->spin_bytes;
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_set_state_raw(shaken_ctx* ctx, const void* host_words, size_t bytes) {
+  if (!ctx || !host_words) return fail(SHAKEN_E_INVAL, "NULL argument");
+  if (bytes != ctx->spin_bytes) return fail(SHAKEN_E_INVAL, "state size mismatch");
+  cudaStream_t st = ctx_stream(ctx);
+  CU(cudaMemcpyAsync(ctx->A.p, host_words, bytes, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(ctx->B.p, ctx->A.p, bytes, cudaMemcpyDeviceToDevice, st));
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_get_state_raw(shaken_ctx* ctx, void* host_words, size_t bytes) {
+  if (!ctx || !host_words) return fail(SHAKEN_E_INVAL, "NULL argument");
+  if (bytes != ctx->spin_bytes) return fail(SHAKEN_E_INVAL, "state size mismatch");
+  cudaStream_t st = ctx_stream(ctx);
+  CU(cudaMemcpyAsync(host_words, ctx->A.p, bytes, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_get_step(shaken_ctx* ctx, uint64_t* t) {
+  if (!ctx || !t) return fail(SHAKEN_E_INVAL, "NULL argument");
+  *t = ctx->host_step;
+  return SHAKEN_OK;
+}
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, kind, enc, R;
+  int64_t n;
+  uint64_t step;
+  uint64_t spin_bytes;
+  uint32_t tracking, pad;
+};
+
+shaken_status shaken_save(shaken_ctx* ctx, void* buf, size_t* len) {
+  if (!ctx || !len) return fail(SHAKEN_E_INVAL, "NULL argument");
+  const size_t need = sizeof(CkptHeader) + 2 * ctx->spin_bytes + (size_t)ctx->R * 16;
+  if (!buf) {
+    *len = need;
+    return SHAKEN_OK;
+  }
+  if (*len < need) return fail(SHAKEN_E_INVAL, "checkpoint buffer too small");
+  CkptHeader h{};
+  std::memcpy(h.magic, "SHAKEN01", 8);
+  h.version = 1;
+  h.kind = (uint32_t)ctx->kind;
+  h.enc = (uint32_t)ctx->enc;
+  h.R = (uint32_t)ctx->R;
+  h.n = ctx->sites();
+  h.step = ctx->host_step;
+  h.spin_bytes = ctx->spin_bytes;
+  h.tracking = ctx->tracking ? 1u : 0u;
+  uint8_t* b = static_cast<uint8_t*>(buf);
+  std::memcpy(b, &h, sizeof(h));
+  cudaStream_t st = ctx_stream(ctx);
+  uint8_t* p = b + sizeof(h);
+  CU(cudaMemcpyAsync(p, ctx->A.p, ctx->spin_bytes, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(p + ctx->spin_bytes, ctx->B.p, ctx->spin_bytes, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(p + 2 * ctx->spin_bytes, ctx->best.p, (size_t)ctx->R * 8,
+                     cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(p + 2 * ctx->spin_bytes + (size_t)ctx->R * 8, ctx->best_step.p,
+                     (size_t)ctx->R * 8, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  *len = need;
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_load(shaken_ctx* ctx, const void* buf, size_t len) {
+  if (!ctx || !buf) return fail(SHAKEN_E_INVAL, "NULL argument");
+  if (len < sizeof(CkptHeader)) return fail(SHAKEN_E_INVAL, "checkpoint too short");
+  CkptHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (std::memcmp(h.magic, "SHAKEN01", 8) != 0 || h.version != 1)
+    return fail(SHAKEN_E_INVAL, "not a checkpoint");
+  if (h.kind != (uint32_t)ctx->kind || h.enc != (uint32_t)ctx->enc || h.R != (uint32_t)ctx->R ||
+      h.n != ctx->sites() || h.spin_bytes != ctx->spin_bytes)
+    return fail(SHAKEN_E_INVAL, "checkpoint does not match this context");
+  const size_t need = sizeof(CkptHeader) + 2 * ctx->spin_bytes + (size_t)ctx->R * 16;
+  if (len < need) return fail(SHAKEN_E_INVAL, "checkpoint truncated");
+  const uint8_t* p = static_cast<const uint8_t*>(buf) + sizeof(h);
+  cudaStream_t st = ctx_stream(ctx);
+  CU(cudaMemcpyAsync(ctx->A.p, p, ctx->spin_bytes, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(ctx->B.p, p + ctx->spin_bytes, ctx->spin_bytes, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(ctx->best.p, p + 2 * ctx->spin_bytes, (size_t)ctx->R * 8,
+                     cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(ctx->best_step.p, p + 2 * ctx->spin_bytes + (size_t)ctx->R * 8,
+                     (size_t)ctx->R * 8, cudaMemcpyHostToDevice, st));
+  CU(cudaStreamSynchronize(st));
+  ctx->host_step = h.step;
+  ctx->tracking = h.tracking != 0;
+  ctx->hcd.tracking = h.tracking;
+  ctx->hcd.anneal_len = 0;
+  ctx->solo.invalidate();
+  return push_cd(ctx);
+}
+
+shaken_status shaken_debug_fields(shaken_ctx* ctx, int half, float* out) {
+  if (!ctx || !out || (half != 0 && half != 1)) return fail(SHAKEN_E_INVAL, "bad argument");
+  if (ctx->kind != SHAKEN_GRAPH) return fail(SHAKEN_E_STATE, "field dump is for graphs");
+  cudaStream_t st = ctx_stream(ctx);
+  if (ctx->solo.dirty) TRY(build_plan(ctx->solo, st));
+  DevMem d;
+  const size_t bytes = (size_t)ctx->R * ctx->n * sizeof(float);
+  TRY(d.alloc(bytes));
+  for (auto& F : ctx->solo.fams) {
+    CU(shk::launch_graph_fields(F->jobs.as<GraphJob>(), F->tiles.as<Tile>(), F->n_tiles,
+                                (uint32_t)half, d.as<float>(), st));
+    ctx->launches++;
+  }
+  CU(cudaMemcpyAsync(out, d.p, bytes, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_launch_count(shaken_ctx* ctx, uint64_t* count) {
+  if (!ctx || !count) return fail(SHAKEN_E_INVAL, "NULL argument");
+  *count = ctx->launches.load();
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_sync(shaken_ctx* ctx) {
+  if (!ctx) return fail(SHAKEN_E_INVAL, "ctx is NULL");
+  CU(cudaStreamSynchronize(ctx_stream(ctx)));
+  return SHAKEN_OK;
+}
+
+// Diagnostics: force the fp64 path of the integer graph decision (not in the header).
+shaken_status shaken_debug_exact_always(shaken_ctx* ctx, int on) {
+  if (!ctx) return fail(SHAKEN_E_INVAL, "ctx is NULL");
+  ctx->exact_always = on ? 1 : 0;
+  return SHAKEN_OK;
+}
+
+// ============================================================================ C ABI: batches
+shaken_status shaken_batch_create(shaken_batch** out, void* cuda_stream) {
+  if (!out) return fail(SHAKEN_E_INVAL, "out is NULL");
+  shaken_batch* b = new shaken_batch();
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  *out = b;
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_batch_add(shaken_batch* b, shaken_ctx* ctx) {
+  if (!b || !ctx) return fail(SHAKEN_E_INVAL, "NULL argument");
+  if (ctx->owner) return fail(SHAKEN_E_STATE, "context already belongs to a batch");
+  CU(cudaStreamSynchronize(ctx->stream));
+  ctx->owner = b;
+  b->plan.members.push_back(ctx);
+  b->plan.invalidate();
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_batch_remove(shaken_batch* b, shaken_ctx* ctx) {
+  if (!b || !ctx) return fail(SHAKEN_E_INVAL, "NULL argument");
+  if (ctx->owner != b) return fail(SHAKEN_E_STATE, "context is not a member");
+  CU(cudaStreamSynchronize(b->stream));
+  auto& M = b->plan.members;
+  M.erase(std::remove(M.begin(), M.end(), ctx), M.end());
+  ctx->owner = nullptr;
+  b->plan.invalidate();
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_batch_step(shaken_batch* b, uint64_t n_steps, int use_graph) {
+  if (!b) return fail(SHAKEN_E_INVAL, "batch is NULL");
+  if (b->plan.members.empty() || n_steps == 0) return SHAKEN_OK;
+  for (shaken_ctx* c : b->plan.members) TRY(check_steps(c, n_steps));
+  uint64_t nl = 0;
+  shaken_status s = plan_run(b->plan, b->stream, n_steps, use_graph != 0, &nl);
+  b->launches += nl;
+  if (s != SHAKEN_OK) return s;
+  for (shaken_ctx* c : b->plan.members) c->host_step += n_steps;
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_batch_sync(shaken_batch* b) {
+  if (!b) return fail(SHAKEN_E_INVAL, "batch is NULL");
+  CU(cudaStreamSynchronize(b->stream));
+  return SHAKEN_OK;
+}
+
+void shaken_batch_free(shaken_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  for (shaken_ctx* c : b->plan.members) c->owner = nullptr;
+  delete b;
+}
+
+shaken_status shaken_batch_set_timing(shaken_batch* b, int on) {
+  if (!b) return fail(SHAKEN_E_INVAL, "batch is NULL");
+  CU(cudaStreamSynchronize(b->stream));
+  b->plan.collect();
+  b->plan.timing = on != 0;
+  b->plan.timed_ms = 0.0;
+  b->plan.timed_n = 0;
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_batch_kernel_time(shaken_batch* b, double* ms, uint64_t* launches) {
+  if (!b) return fail(SHAKEN_E_INVAL, "batch is NULL");
+  CU(cudaStreamSynchronize(b->stream));
+  b->plan.collect();
+  if (ms) *ms = b->plan.timed_ms;
+  if (launches) *launches = b->plan.timed_n;
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_batch_set_rng_counter(shaken_batch* b, uint64_t* device_counter) {
+  if (!b) return fail(SHAKEN_E_INVAL, "batch is NULL");
+  CU(cudaStreamSynchronize(b->stream));
+  b->plan.rng_counter = reinterpret_cast<unsigned long long*>(device_counter);
+  b->plan.drop_graph();
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_microbench(int kind, double* rate, double* ms) {
+  if (!rate) return fail(SHAKEN_E_INVAL, "rate is NULL");
+  CU(shk::run_microbench(kind, rate, ms));
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_batch_launch_count(shaken_batch* b, uint64_t* count) {
+  if (!b || !count) return fail(SHAKEN_E_INVAL, "NULL argument");
+  *count = b->launches.load();
+  return SHAKEN_OK;
+}
+
+// ============================================================================ C ABI: primitives
+shaken_status shaken_philox_device(uint64_t seed, const uint32_t* ctr, uint32_t* out, int64_t n,
+                                   void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!ctr || !out))) return fail(SHAKEN_E_INVAL, "bad argument");
+  CU(shk::launch_philox(seed, ctr, out, n, static_cast<cudaStream_t>(cuda_stream)));
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_threshold_device(const double* h, const double* beta, uint64_t* out,
+                                      int64_t n, void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!h || !beta || !out))) return fail(SHAKEN_E_INVAL, "bad argument");
+  CU(shk::launch_threshold(h, beta, out, n, static_cast<cudaStream_t>(cuda_stream)));
+  return SHAKEN_OK;
+}
+
+const char* shaken_strerror(shaken_status s) {
+  switch (s) {
+    case SHAKEN_OK: return "ok";
+    case SHAKEN_E_INVAL: return "invalid argument";
+    case SHAKEN_E_NOMEM: return "out of memory";
+    case SHAKEN_E_CUDA: return "CUDA error";
+    case SHAKEN_E_TIMEOUT: return "timeout";
+    case SHAKEN_E_STATE: return "invalid state";
+    case SHAKEN_E_BUDGET: return "over device-memory budget";
+  }
+  return "unknown status";
+}
+
+const char* shaken_last_error(void) { return g_last_error.c_str(); }
+
+const char* shaken_version(void) { return "libshaken 0.1 (sm_103a)"; }
+
+}  // extern "C"
+
+// ============================================================================ server
+// Continuous batching of annealing jobs.  A worker thread owns every device
+// call of the server: it admits queued jobs in arrival order while their
+// device state fits the budget, steps all running jobs together in chunks of
+// chunk_steps (each job stops exactly at its own last step: the kernels skip a
+// context once its step reaches t_end), and retires finished jobs.
+struct ServerJob {
+  int64_t id = 0;
+  shaken_problem p{};
+  std::vector<int32_t> u, v;
+  std::vector<float> J, lambda;
+  std::vector<uint8_t> frozen;
+  std::vector<double> beta, sched;
+  std::vector<int8_t> init;
+  uint64_t seed = 0, n_steps = 0;
+  size_t bytes = 0;
+  int state = 0;  // 0 queued, 1 running, 2 done, 3 failed
+  shaken_ctx* ctx = nullptr;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  std::vector<shaken_obs> result;
+  std::string error;
+};
+
+struct shaken_server {
+  size_t budget = 0, used = 0;
+  uint32_t chunk = 64;
+  cudaStream_t stream = nullptr;
+  std::mutex mu;
+  std::condition_variable cv, done_cv;
+  std::deque<int64_t> queue;
+  std::map<int64_t, std::unique_ptr<ServerJob>> jobs;
+  std::vector<ServerJob*> running;
+  shaken_batch batch;
+  int64_t next_id = 0;
+  int64_t n_done = 0;
+  double updates = 0.0;
+  bool stop = false;
+  std::thread worker;
+  std::chrono::steady_clock::time_point t0;
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+static size_t job_bytes(const shaken_problem* p) {
+  const int64_t N = p->kind == SHAKEN_LATTICE ? p->L * p->L : p->n;
+  size_t b = 2 * (size_t)(p->replicas / 32) * N * 4;  // A, B
+  if (p->kind == SHAKEN_GRAPH) {
+    b += 2 * (size_t)(N + 1) * 4 + 2 * (size_t)p->m * 4;  // CSR
+    if (!p->J_is_integer) b += 2 * (size_t)p->m * 4;
+    if (p->lambda) b += (size_t)N * 4;
+    if (p->frozen_mask) b += (size_t)N * 4;
+  }
+  b += (size_t)p->replicas * (2 * kNumSums * 8 + 16 + 8);
+  return b + 4096;
+}
+
+static void server_loop(shaken_server* s) {
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (true) {
+    // admit
+    while (!s->queue.empty()) {
+      ServerJob* j = s->jobs[s->queue.front()].get();
+      if (s->used + j->bytes > s->budget && !s->running.empty()) break;
+      s->queue.pop_front();
+      lk.unlock();
+      shaken_ctx* c = nullptr;
+      shaken_status st = shaken_init(&c, &j->p, j->seed, s->stream);
+      if (st == SHAKEN_OK) {
+        c->owner = &s->batch;
+        st = begin_anneal(c, j->sched.data(), j->n_steps);
+        c->hcd.t_end = (uint32_t)j->n_steps;
+        if (st == SHAKEN_OK) st = push_cd(c);
+      }
+      lk.lock();
+      if (st != SHAKEN_OK) {
+        j->state = 3;
+        j->error = g_last_error;
+        if (c) {
+          c->owner = nullptr;
+          shaken_free(c);
+        }
+        s->n_done++;
+        s->done_cv.notify_all();
+        continue;
+      }
+      j->ctx = c;
+      j->state = 1;
+      j->t_admit = s->now();
+      s->used += j->bytes;
+      s->running.push_back(j);
+      s->batch.plan.members.push_back(c);
+      s->batch.plan.invalidate();
+    }
+    if (s->stop && s->queue.empty() && s->running.empty()) break;
+    if (s->running.empty()) {
+      s->cv.wait_for(lk, std::chrono::milliseconds(2));
+      if (s->stop && s->queue.empty()) break;
+      continue;
+    }
+    // step every running job one chunk
+    uint64_t chunk = s->chunk;
+    lk.unlock();
+    uint64_t nl = 0;
+    shaken_status st = plan_run(s->batch.plan, s->stream, chunk, true, &nl);
+    if (st == SHAKEN_OK) {
+      cudaError_t e = cudaStreamSynchronize(s->stream);
+      if (e != cudaSuccess) st = fail(SHAKEN_E_CUDA, cudaGetErrorString(e));
+    }
+    lk.lock();
+    s->batch.launches += nl;
+    std::vector<ServerJob*> still;
+    for (ServerJob* j : s->running) {
+      shaken_ctx* c = j->ctx;
+      const uint64_t before = c->host_step;
+      c->host_step = std::min<uint64_t>(c->host_step + chunk, j->n_steps);
+      s->updates += 2.0 * (double)(c->host_step - before) * (double)c->R * (double)c->sites();
+      if (st != SHAKEN_OK || c->host_step >= j->n_steps) {
+        j->result.resize(c->R);
+        lk.unlock();
+        shaken_status so = st == SHAKEN_OK ? shaken_observables(c, j->result.data()) : st;
+        lk.lock();
+        j->state = so == SHAKEN_OK ? 2 : 3;
+        if (so != SHAKEN_OK) j->error = g_last_error;
+        j->t_done = s->now();
+        auto& M = s->batch.plan.members;
+        M.erase(std::remove(M.begin(), M.end(), c), M.end());
+        s->batch.plan.invalidate();
+        c->owner = nullptr;
+        shaken_free(c);
+        j->ctx = nullptr;
+        s->used -= j->bytes;
+        s->n_done++;
+        s->done_cv.notify_all();
+      } else {
+        still.push_back(j);
+      }
+    }
+    s->running.swap(still);
+  }
+}
+
+extern "C" {
+
+shaken_status shaken_server_create(shaken_server** out, size_t hbm_budget_bytes,
+                                   uint32_t chunk_steps, void* cuda_stream) {
+  if (!out || hbm_budget_bytes == 0 || chunk_steps == 0)
+    return fail(SHAKEN_E_INVAL, "bad argument");
+  shaken_server* s = new shaken_server();
+  s->budget = hbm_budget_bytes;
+  s->chunk = chunk_steps;
+  s->stream = static_cast<cudaStream_t>(cuda_stream);
+  s->batch.stream = s->stream;
+  s->t0 = std::chrono::steady_clock::now();
+  s->worker = std::thread(server_loop, s);
+  *out = s;
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_server_submit(shaken_server* s, const shaken_problem* p, uint64_t seed,
+                                   const double* beta_schedule, uint64_t n_steps,
+                                   int64_t* job_id) {
+  if (!s || !p || !beta_schedule || !job_id || n_steps == 0)
+    return fail(SHAKEN_E_INVAL, "bad argument");
+  TRY(validate(p));
+  if (n_steps >= 0xFFFFFFFEull) return fail(SHAKEN_E_INVAL, "too many steps");
+  auto j = std::make_unique<ServerJob>();
+  j->p = *p;
+  const int64_t N = p->kind == SHAKEN_LATTICE ? p->L * p->L : p->n;
+  if (p->m > 0 && p->kind == SHAKEN_GRAPH) {
+    j->u.assign(p->u, p->u + p->m);
+    j->v.assign(p->v, p->v + p->m);
+    j->J.assign(p->J_edge, p->J_edge + p->m);
+    j->p.u = j->u.data();
+    j->p.v = j->v.data();
+    j->p.J_edge = j->J.data();
+  }
+  if (p->lambda) {
+    j->lambda.assign(p->lambda, p->lambda + N);
+    j->p.lambda = j->lambda.data();
+  }
+  if (p->frozen_mask) {
+    j->frozen.assign(p->frozen_mask, p->frozen_mask + N);
+    j->p.frozen_mask = j->frozen.data();
+  }
+  j->beta.assign(p->beta, p->beta + p->replicas);
+  j->p.beta = j->beta.data();
+  if (p->init == SHAKEN_INIT_GIVEN) {
+    j->init.assign(p->init_spins, p->init_spins + (size_t)p->replicas * N);
+    j->p.init_spins = j->init.data();
+  }
+  j->sched.assign(beta_schedule, beta_schedule + n_steps);
+  j->seed = seed;
+  j->n_steps = n_steps;
+  j->bytes = job_bytes(p);
+  if (j->bytes > s->budget) return fail(SHAKEN_E_BUDGET, "job exceeds the device-memory budget");
+  std::lock_guard<std::mutex> lk(s->mu);
+  j->id = s->next_id++;
+  j->t_submit = s->now();
+  *job_id = j->id;
+  s->queue.push_back(j->id);
+  s->jobs[j->id] = std::move(j);
+  s->cv.notify_all();
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_server_poll(shaken_server* s, int64_t job_id, int* state) {
+  if (!s || !state) return fail(SHAKEN_E_INVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(job_id);
+  if (it == s->jobs.end()) return fail(SHAKEN_E_INVAL, "unknown job");
+  *state = it->second->state;
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_server_result(shaken_server* s, int64_t job_id, shaken_obs* out,
+                                   double* t_admit, double* t_done) {
+  if (!s) return fail(SHAKEN_E_INVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(job_id);
+  if (it == s->jobs.end()) return fail(SHAKEN_E_INVAL, "unknown job");
+  ServerJob* j = it->second.get();
+  if (j->state == 3) return fail(SHAKEN_E_CUDA, "job failed: " + j->error);
+  if (j->state != 2) return fail(SHAKEN_E_STATE, "job not finished");
+  if (out) std::copy(j->result.begin(), j->result.end(), out);
+  if (t_admit) *t_admit = j->t_admit;
+  if (t_done) *t_done = j->t_done;
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_server_drain(shaken_server* s, double timeout_s) {
+  if (!s) return fail(SHAKEN_E_INVAL, "NULL argument");
+  std::unique_lock<std::mutex> lk(s->mu);
+  const auto deadline = std::chrono::steady_clock::now() +
+                        std::chrono::microseconds((int64_t)(timeout_s * 1e6));
+  while (s->n_done < (int64_t)s->jobs.size()) {
+    if (s->done_cv.wait_until(lk, deadline) == std::cv_status::timeout &&
+        s->n_done < (int64_t)s->jobs.size())
+      return fail(SHAKEN_E_TIMEOUT, "server drain timed out");
+  }
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_server_stats(shaken_server* s, double* site_updates, uint64_t* launches,
+                                  int64_t* jobs_done) {
+  if (!s) return fail(SHAKEN_E_INVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (site_updates) *site_updates = s->updates;
+  if (launches) *launches = s->batch.launches.load();
+  if (jobs_done) *jobs_done = s->n_done;
+  return SHAKEN_OK;
+}
+
+void shaken_server_free(shaken_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->queue.clear();
+    for (auto& kv : s->jobs)
+      if (kv.second->state == 0) kv.second->state = 3;
+    s->cv.notify_all();
+  }
+  if (s->worker.joinable()) s->worker.join();
+  for (ServerJob* j : s->running) {
+    if (j->ctx) {
+      j->ctx->owner = nullptr;
+      shaken_free(j->ctx);
+    }
+  }
+  delete s;
+}
+
+}  // extern "C"

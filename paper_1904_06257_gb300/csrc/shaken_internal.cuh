@@ -1,0 +1,206 @@
+// shaken_internal.cuh -- device math and launch descriptors shared by the
+// kernels and the host runtime of libshaken (sm_103a).
+//
+// Device math (one definition of the random stream and of the heat-bath
+// decision, used by every kernel):
+//   * Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): multipliers
+//     0xD2511F53 / 0xCD9E8D57, Weyl key increments 0x9E3779B9 / 0xBB67AE85,
+//     key = (seed low, seed high), counter = (a, b, t, half + 2c).
+//   * exp_sd: Cody & Waite reduction x = k ln2 + r with ln2 split in a 29-bit
+//     head and a tail, Taylor polynomial of e^r to degree 13 (Horner with
+//     fused multiply-add), scaling by 2^k; |x| >= 64 clamps (the threshold is
+//     already exactly 0 or 2^32 there).  Every operation is an explicitly
+//     rounded intrinsic so the result does not depend on contraction.
+//   * threshold T(h, beta) = floor(2^32 p), p = 1 / (1 + exp_sd(-2 beta h)):
+//     the heat-bath probability e^{beta h} / (2 cosh(beta h)) of tau_x = +1
+//     (Sec. 2, laws of P^{1->2} and P^{2->1}; Sec. 3, P^dl and P^ur), and
+//     tau_x = +1 iff u < T for the 32-bit draw u.
+//   * field h = (Jc * s + q * sigma) + lambda, s the integer neighbour sum.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace shk {
+
+constexpr uint32_t kPhM0 = 0xD2511F53u;
+constexpr uint32_t kPhM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhW0 = 0x9E3779B9u;
+constexpr uint32_t kPhW1 = 0xBB67AE85u;
+constexpr uint32_t kInitStep = 0xFFFFFFFFu;  // step index of the initial draw
+
+constexpr int kTile = 256;  // lane words (or vertices) per tile = threads per block
+
+// ---------------------------------------------------------------- Philox-4x32-10
+struct PhKey {
+  uint32_t k0[10];
+  uint32_t k1[10];
+};
+
+__device__ __forceinline__ PhKey ph_key(uint32_t key0, uint32_t key1) {
+  PhKey K;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    K.k0[r] = key0 + (uint32_t)r * kPhW0;
+    K.k1[r] = key1 + (uint32_t)r * kPhW1;
+  }
+  return K;
+}
+
+__device__ __forceinline__ uint4 ph_call(const PhKey& K, uint32_t c0, uint32_t c1, uint32_t c2,
+                                         uint32_t c3) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p0 = (unsigned long long)kPhM0 * c0;
+    const unsigned long long p1 = (unsigned long long)kPhM1 * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ K.k0[r];
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ K.k1[r];
+    c1 = (uint32_t)p1;
+    c3 = (uint32_t)p0;
+    c0 = n0;
+    c2 = n2;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// ---------------------------------------------------------------- exp and threshold
+__device__ __forceinline__ double exp_sd(double x) {
+  if (x <= -64.0) return 0.0;
+  if (x >= 64.0) return __longlong_as_double(0x7ff0000000000000LL);
+  const double inv_ln2 = 0x1.71547652b82fep+0;
+  const double ln2_hi = 0x1.62e42ff000000p-1;
+  const double ln2_lo = -0x1.718432a1b0e26p-35;
+  const double k = rint(__dmul_rn(x, inv_ln2));
+  const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(k, ln2_hi)), __dmul_rn(k, ln2_lo));
+  // Taylor coefficients 1/n!, n = 13 .. 0 (correctly rounded)
+  double p = 0x1.6124613a86d09p-33;
+  p = __fma_rn(p, r, 0x1.1eed8eff8d898p-29);
+  p = __fma_rn(p, r, 0x1.ae64567f544e4p-26);
+  p = __fma_rn(p, r, 0x1.27e4fb7789f5cp-22);
+  p = __fma_rn(p, r, 0x1.71de3a556c734p-19);
+  p = __fma_rn(p, r, 0x1.a01a01a01a01ap-16);
+  p = __fma_rn(p, r, 0x1.a01a01a01a01ap-13);
+  p = __fma_rn(p, r, 0x1.6c16c16c16c17p-10);
+  p = __fma_rn(p, r, 0x1.1111111111111p-7);
+  p = __fma_rn(p, r, 0x1.5555555555555p-5);
+  p = __fma_rn(p, r, 0x1.5555555555555p-3);
+  p = __fma_rn(p, r, 0x1.0000000000000p-1);
+  p = __fma_rn(p, r, 1.0);
+  p = __fma_rn(p, r, 1.0);
+  const long long ki = (long long)k;  // |k| <= 93: 2^k is a normal double
+  return __dmul_rn(p, __longlong_as_double((ki + 1023LL) << 52));
+}
+
+// T = floor(2^32 / (1 + e^{-2 beta h})) in [0, 2^32].
+__device__ __forceinline__ unsigned long long threshold_T(double h, double beta) {
+  const double y = __dmul_rn(beta, h);
+  const double e = exp_sd(-2.0 * y);
+  const double p = __ddiv_rn(1.0, __dadd_rn(1.0, e));
+  return (unsigned long long)floor(__dmul_rn(p, 4294967296.0));
+}
+
+__device__ __forceinline__ double field_h(double Jc, int s, double q, int sigma, double lam) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(Jc, (double)s), __dmul_rn(q, (double)sigma)), lam);
+}
+
+// ---------------------------------------------------------------- lattice tables
+// Per beta-set (one int8/packed replica, or one 32-replica multispin group) the
+// threshold of each field class c = 2 n + s (n = number of +1 in-neighbours,
+// s = 1 if sigma_x = +1) as bit planes over the 32 lanes of a lane word:
+//   tm[j][c]  bit k set iff T(c, beta_k) < 2^32, T(c, beta_k) > 0 and bit (31-j)
+//             of T(c, beta_k) is 1 (planes most significant first);
+//   satp[c]   lanes with T == 2^32 (always +1), satm[c] lanes with T == 0.
+struct __align__(16) LatTable {
+  uint32_t tm[32][8];
+  uint32_t satp[8];
+  uint32_t satm[8];
+};
+
+// ---------------------------------------------------------------- descriptors
+// Device-resident state of one context, read by every kernel of a step and
+// advanced by the step epilogue.
+struct CtxDev {
+  uint32_t step;        // current step t
+  uint32_t t_end;       // kernels skip this context once step >= t_end
+  uint32_t anneal_t0;   // first step of the running anneal (table / schedule index base)
+  uint32_t anneal_len;  // schedule length (0 = no anneal)
+  uint32_t tracking;    // evaluate H(sigma_t) each step
+  uint32_t record;      // write the per-step series
+  uint32_t series_t0;
+  uint32_t series_cap;
+  uint32_t R;
+  uint32_t kind;        // 0 lattice, 1 graph
+  double Jc;            // energy: H = -Jc E - 2 lamc M - 2 LS
+  double lamc;
+  double inv_n;
+  double* step_sums;    // [R][8] sums of sigma_t for tracking (zeroed by the epilogue)
+  double* best;         // [R]
+  long long* best_step; // [R]
+  double* series_m;     // [cap][R] or null
+  double* series_H;     // [cap][R] or null
+};
+
+// Sum slots of a replica (all integer valued except the real-J graph sums).
+enum : int {
+  kSumM = 0,   // sum sigma
+  kSumE = 1,   // sum over E^o of (J) sigma_tail sigma_head (lattice: unweighted)
+  kSumLS = 2,  // graph: sum lambda_x sigma_x
+  kSumP1 = 3,  // sum over E^o of (J) sigma_tail sigma'_head
+  kSumP2 = 4,  // sum sigma_x sigma'_x
+  kSumM2 = 5,  // lattice: sum sigma'
+  kSumLS2 = 6, // graph: sum lambda_x sigma'_x
+  kSumCut = 7, // edges with sigma_x != sigma_y
+  kNumSums = 8
+};
+
+// One lattice lane-word job: an int8/packed replica or a multispin group.
+struct LatJob {
+  void* A;                       // sigma buffer of this replica / group
+  void* B;                       // sigma' buffer
+  const uint32_t* frozen;        // frozen lane masks per lane word, or null
+  const LatTable* table;         // static table of this job
+  const LatTable* anneal_tables; // per-step tables (index step - anneal_t0) or null
+  CtxDev* cd;
+  double* sums;                  // step sums of this job's replicas (tracking), [1 or 32][8]
+  double* obs;                   // on-demand observable sums of this job's replicas
+  uint32_t L;
+  uint32_t wpr;                  // lane words per row (L/32 or L)
+  uint32_t nwords;
+  uint32_t b;                    // counter word b: replica (int8/packed) or group (multispin)
+  uint32_t key0, key1;
+  uint32_t rep0;                 // first replica index of the job within its context
+  uint32_t pad;
+};
+
+// One graph job: a 32-replica group of a graph context.
+struct GraphJob {
+  uint32_t* A;
+  uint32_t* B;
+  const int32_t* in_ptr;   // in-CSR (sources y of (y -> x) in E^o)
+  const uint32_t* in_col;  // bit 31: J < 0 (integer couplings)
+  const float* in_J;       // real couplings (null for integer)
+  const int32_t* out_ptr;  // out-CSR (heads y of (x -> y))
+  const uint32_t* out_col;
+  const float* out_J;
+  const float* lambda;     // [n] or null (lambda_c)
+  const uint32_t* frozen;  // [n] lane masks or null
+  const double* beta_lane; // [32] betas of this group
+  const double* beta_sched;// anneal schedule (index step - anneal_t0) or null
+  CtxDev* cd;
+  double* sums;            // [32][8] step sums of the group's replicas (tracking)
+  double* obs;             // [32][8] on-demand observable sums
+  double q;
+  float lambda_c;
+  uint32_t n;
+  uint32_t b;
+  uint32_t key0, key1;
+  uint32_t integer;
+  uint32_t rep0;
+};
+
+struct Tile {
+  uint32_t job;
+  uint32_t w0;
+};
+
+}  // namespace shk

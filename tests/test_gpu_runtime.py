@@ -1,0 +1,154 @@
+"""Runtime behaviour through the C ABI on the GPU: batching (uneven sizes in
+one launch per half step, CUDA-graph replay) gives each member the trajectory
+it has alone; checkpoint/resume is bit-exact; the serving loop's results equal
+running each job alone; the device Philox and thresholds equal the oracle's."""
+import numpy as np
+import pytest
+
+from oracle import core
+from paper_1904_06257_gb300 import workloads as W
+from tests.gpu_util import graph_problem, lattice_problem, lib, require_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    require_cuda()
+    return lib()
+
+
+def make_members(S):
+    u, v = W.erdos_renyi(700, 5.0, 3)
+    J = W.couplings_pm1(u.size, 4)
+    lam = W.fields_normal(700, 0.1, 5)
+    probs = [
+        (lattice_problem(S, S.INT8, 64, 2, [0.4, 0.5]), 1, 64 * 64, 2),
+        (lattice_problem(S, S.PACKED, 96, 1, 0.44, lam=0.01), 2, 96 * 96, 1),
+        (lattice_problem(S, S.MULTISPIN, 32, 32, W.beta_grid(32)), 3, 32 * 32, 32),
+        (lattice_problem(S, S.MULTISPIN, 128, 64, W.beta_grid(64)), 4, 128 * 128, 64),
+        (graph_problem(S, 700, u, v, J, 32, 0.8, lam=lam), 5, 700, 32),
+    ]
+    return probs
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_equals_alone(S, use_graph):
+    steps = 70
+    alone = []
+    for p, seed, n, R in make_members(S):
+        c = S.shaken_init(p, seed)
+        S.shaken_step(c, steps)
+        alone.append(S.shaken_get_spins(c, R, n))
+        S.shaken_free(c)
+    b = S.shaken_batch_create()
+    ctxs = []
+    for p, seed, n, R in make_members(S):
+        c = S.shaken_init(p, seed)
+        S.shaken_batch_add(b, c)
+        ctxs.append((c, n, R))
+    S.shaken_batch_step(b, steps, use_graph)
+    S.shaken_batch_sync(b)
+    assert S.shaken_batch_launch_count(b) > 0
+    for (c, n, R), ref in zip(ctxs, alone):
+        assert np.array_equal(S.shaken_get_spins(c, R, n), ref)
+        assert S.shaken_get_step(c) == steps
+    for c, _, _ in ctxs:
+        S.shaken_batch_remove(b, c)
+        S.shaken_free(c)
+    S.shaken_batch_free(b)
+
+
+def test_checkpoint_resume_bit_exact(S):
+    p = lattice_problem(S, S.MULTISPIN, 64, 32, W.beta_grid(32))
+    c = S.shaken_init(p, 12)
+    S.shaken_set_tracking(c, True)
+    S.shaken_step(c, 10)
+    ck = S.shaken_save(c)
+    S.shaken_step(c, 15)
+    ref = S.shaken_get_spins(c, 32, 64 * 64)
+    ref_obs = S.shaken_observables(c, 32)
+    c2 = S.shaken_init(p, 12)
+    S.shaken_load(c2, ck)
+    assert S.shaken_get_step(c2) == 10
+    S.shaken_step(c2, 15)
+    assert np.array_equal(S.shaken_get_spins(c2, 32, 64 * 64), ref)
+    o2 = S.shaken_observables(c2, 32)
+    assert np.array_equal(o2["best_energy"], ref_obs["best_energy"])
+    S.shaken_free(c)
+    S.shaken_free(c2)
+
+
+def test_server_results_equal_alone(S):
+    jobs = []
+    for k in range(5):
+        n = 300 + 150 * k
+        u, v = W.erdos_renyi(n, 4.0 + k, 100 + k)
+        J = W.couplings_pm1(u.size, 200 + k)
+        lam = W.fields_normal(n, 0.1, 300 + k)
+        R = 32 * (1 + k % 2)
+        steps = 40 + 23 * k
+        sched = W.linear_schedule(0.1, 3.0, steps)
+        jobs.append((graph_problem(S, n, u, v, J, R, 1.0, lam=lam), 900 + k, sched, n, R))
+    alone = []
+    for p, seed, sched, n, R in jobs:
+        c = S.shaken_init(p, seed)
+        S.shaken_anneal(c, sched)
+        alone.append((S.shaken_get_spins(c, R, n), S.shaken_observables(c, R)))
+        S.shaken_free(c)
+    srv = S.shaken_server_create(1 << 30, 16)
+    ids = [S.shaken_server_submit(srv, p, seed, sched) for p, seed, sched, n, R in jobs]
+    S.shaken_server_drain(srv, 120.0)
+    for jid, (p, seed, sched, n, R), (spins, obs) in zip(ids, jobs, alone):
+        assert S.shaken_server_poll(srv, jid) == 2
+        res, ta, td = S.shaken_server_result(srv, jid, R)
+        assert td >= ta
+        assert np.allclose(res["energy"], obs["energy"], rtol=0, atol=1e-9)
+        assert np.allclose(res["best_energy"], obs["best_energy"], rtol=0, atol=1e-9)
+        assert np.array_equal(res["best_step"], obs["best_step"])
+    upd, launches, done = S.shaken_server_stats(srv)
+    assert done == len(jobs) and launches > 0
+    S.shaken_server_free(srv)
+
+
+def test_server_budget_serialises_jobs(S):
+    # a budget that fits one job at a time still completes every job
+    n = 2000
+    u, v = W.erdos_renyi(n, 6.0, 7)
+    J = W.couplings_pm1(u.size, 8)
+    p = graph_problem(S, n, u, v, J, 64, 1.0)
+    srv = S.shaken_server_create(600_000, 8)
+    sched = W.linear_schedule(0.2, 2.0, 30)
+    ids = [S.shaken_server_submit(srv, p, s, sched) for s in range(4)]
+    S.shaken_server_drain(srv, 120.0)
+    t = [S.shaken_server_result(srv, i, 64)[1:] for i in ids]
+    for (a0, d0), (a1, d1) in zip(t, t[1:]):
+        assert a1 >= d0 - 1e-9  # admitted only after the previous job freed its memory
+    S.shaken_server_free(srv)
+
+
+def test_device_philox_and_thresholds_match_oracle(S):
+    import torch
+    g = np.random.default_rng(0)
+    n = 4096
+    ctr = g.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    seed = 0x5348414B12345
+    dc = torch.from_numpy(ctr.view(np.int32).copy()).cuda()
+    do = torch.zeros_like(dc)
+    S.shaken_philox_device(seed, dc.data_ptr(), do.data_ptr(), n)
+    torch.cuda.synchronize()
+    got = do.cpu().numpy().view(np.uint32)
+    key = np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint32)
+    for i in range(0, n, 37):
+        assert np.array_equal(got[i], core.philox(key, ctr[i]))
+    h = np.concatenate([g.uniform(-10, 10, 20000), np.array([0.0, 7.0, -20.0, 1e-300]),
+                        g.integers(-30, 30, 4000) + g.choice([-0.5, 0.0, 0.25, 0.5], 4000)])
+    beta = np.concatenate([g.uniform(0, 3.5, h.size - 1), [100.0]])
+    dh = torch.from_numpy(h).cuda()
+    db = torch.from_numpy(beta).cuda()
+    dout = torch.zeros(h.size, dtype=torch.int64, device="cuda")
+    S.shaken_threshold_device(dh.data_ptr(), db.data_ptr(), dout.data_ptr(), h.size)
+    torch.cuda.synchronize()
+    T = dout.cpu().numpy().astype(np.uint64)
+    for i in range(h.size):
+        assert int(T[i]) == core.threshold(h[i], beta[i]), (h[i], beta[i])
