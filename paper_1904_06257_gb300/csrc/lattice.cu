@@ -66,49 +66,78 @@ __global__ void __launch_bounds__(256) build_lattice_tables_kernel(
 }
 
 // --------------------------------------------------------------------------- decision core
-// S = sigma_x bits, V / H = the two in-neighbour bits (vertical / horizontal),
-// F = frozen lanes.  Returns tau bits (1 = +1).
-__device__ __forceinline__ uint32_t decide32(uint32_t S, uint32_t V, uint32_t H, uint32_t F,
-                                             const LatTable* __restrict__ tab, const PhKey& K,
-                                             uint32_t a, uint32_t b, uint32_t t, uint32_t half,
-                                             uint32_t& calls) {
-  const uint32_t n2 = V & H;
-  const uint32_t n1 = V ^ H;
-  const uint32_t n0 = ~(V | H);
-  uint32_t M[6];
-  M[0] = n0 & ~S;
-  M[1] = n0 & S;
-  M[2] = n1 & ~S;
-  M[3] = n1 & S;
-  M[4] = n2 & ~S;
-  M[5] = n2 & S;
+// Field classes of a lane word.  S = sigma_x bits, V / H = the two in-neighbour
+// bits (vertical / horizontal); x = V ^ H marks one +1 neighbour (n = 1), and
+// where V == H the class is n = 0 (V = 0) or n = 2 (V = 1).
+struct LaneWord {
+  uint32_t S, V, X, U, res;  // U = lanes still undecided
+};
+
+// Threshold bit of plane j for every lane: first select by sigma within each
+// n-class, then by n: 5 three-input selects.
+__device__ __forceinline__ uint32_t plane_bits(const LaneWord& L, const uint32_t* tm) {
+  const uint4 lo = *reinterpret_cast<const uint4*>(tm);      // classes 0..3
+  const uint2 hi = *reinterpret_cast<const uint2*>(tm + 4);  // classes 4, 5
+  const uint32_t b0 = (L.S & lo.y) | (~L.S & lo.x);  // n = 0
+  const uint32_t b1 = (L.S & lo.w) | (~L.S & lo.z);  // n = 1
+  const uint32_t b2 = (L.S & hi.y) | (~L.S & hi.x);  // n = 2
+  const uint32_t m = (L.V & b2) | (~L.V & b0);       // V == H
+  return (L.X & b1) | (~L.X & m);
+}
+
+// MSB-first comparison of u_k with T_k over the four planes of one Philox call.
+__device__ __forceinline__ void apply_call(LaneWord& L, const uint4 w, const uint32_t* tm_rows) {
+  const uint32_t Wj[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t P = plane_bits(L, tm_rows + 8 * i);
+    const uint32_t diff = (Wj[i] ^ P) & L.U;  // first plane where u and T differ
+    L.res |= diff & P;                        // T has the 1 there: u < T
+    L.U &= ~diff;
+  }
+}
+
+// Initial classification: frozen lanes and saturated thresholds (T = 0 or 2^32)
+// are decided before any draw.
+__device__ __forceinline__ LaneWord classify(uint32_t S, uint32_t V, uint32_t H, uint32_t F,
+                                             const LatTable& tab) {
+  LaneWord L;
+  L.S = S;
+  L.V = V;
+  L.X = V ^ H;
+  const uint32_t n2 = V & H, n0 = ~(V | H), n1 = L.X;
+  const uint32_t M[6] = {n0 & ~S, n0 & S, n1 & ~S, n1 & S, n2 & ~S, n2 & S};
   uint32_t dec = F, res = F;
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
-    const uint32_t sp = __ldg(&tab->satp[c]);
-    const uint32_t sm = __ldg(&tab->satm[c]);
-    dec |= M[c] & (sp | sm);
-    res |= M[c] & sp;
+    dec |= M[c] & (tab.satp[c] | tab.satm[c]);
+    res |= M[c] & tab.satp[c];
   }
+  L.U = ~dec;
+  L.res = res;
+  return L;
+}
+
+// Full decision of one lane word: calls 0 and 1 (planes 31..24) are made
+// unconditionally (independent, so they overlap), later calls only while
+// some lane is still undecided.
+__device__ __forceinline__ uint32_t decide_word(LaneWord L, const LatTable& tab, const PhKey& K,
+                                                uint32_t a, uint32_t b, uint32_t t, uint32_t half,
+                                                uint32_t& calls) {
+  if (L.U != 0u) {
+    const uint4 w0 = ph_call(K, a, b, t, half);
+    const uint4 w1 = ph_call(K, a, b, t, half + 2u);
+    calls += 2;
+    apply_call(L, w0, &tab.tm[0][0]);
+    apply_call(L, w1, &tab.tm[4][0]);
 #pragma unroll 1
-  for (uint32_t call = 0; call < 8; ++call) {
-    if (dec == 0xffffffffu) break;
-    const uint4 w = ph_call(K, a, b, t, half + 2u * call);
-    ++calls;
-    const uint32_t Wj[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const uint4* row = reinterpret_cast<const uint4*>(tab->tm[4 * call + i]);
-      const uint4 lo = __ldg(row);
-      const uint4 hi = __ldg(row + 1);
-      const uint32_t P = (M[0] & lo.x) | (M[1] & lo.y) | (M[2] & lo.z) | (M[3] & lo.w) |
-                         (M[4] & hi.x) | (M[5] & hi.y);
-      const uint32_t diff = (Wj[i] ^ P) & ~dec;
-      res |= diff & P;
-      dec |= diff;
+    for (uint32_t call = 2; call < 8 && L.U != 0u; ++call) {
+      const uint4 w = ph_call(K, a, b, t, half + 2u * call);
+      ++calls;
+      apply_call(L, w, &tab.tm[4 * call][0]);
     }
   }
-  return res;
+  return L.res;
 }
 
 // --------------------------------------------------------------------------- int8 <-> bits
@@ -156,85 +185,172 @@ __device__ __forceinline__ void block_sum_atomic(double (&v)[NV], double* dst, d
 // --------------------------------------------------------------------------- half step
 enum { kEncInt8 = 0, kEncPacked = 1, kEncMultispin = 2 };
 
+// Lane-word coordinates: row i and word column c of lane word w.
+__device__ __forceinline__ void word_rc(const LatJob& J, uint32_t w, uint32_t& i, uint32_t& c) {
+  if (J.wpr_shift != 0xffffffffu) {
+    i = w >> J.wpr_shift;
+    c = w & (J.wpr - 1u);
+  } else {
+    i = w / J.wpr;
+    c = w - i * J.wpr;
+  }
+}
+
+// Loads the three lane words a decision needs from buffer src: S (own), V (the
+// vertical in-neighbour row: i-1 for half 0, i+1 for half 1) and H (the
+// horizontal in-neighbour: j-1 for half 0, j+1 for half 1).
 template <int ENC>
-__global__ void __launch_bounds__(kTile) lattice_half_kernel(const LatJob* __restrict__ jobs,
-                                                             const Tile* __restrict__ tiles,
-                                                             int n_tiles, uint32_t half,
-                                                             unsigned long long* rng_calls) {
+__device__ __forceinline__ void load_lane_words(const LatJob& J, const void* buf, uint32_t w,
+                                                uint32_t half, uint32_t& S, uint32_t& V,
+                                                uint32_t& H) {
+  const uint32_t L = J.L, wpr = J.wpr;
+  uint32_t i, c;
+  word_rc(J, w, i, c);
+  const uint32_t iv = half == 0u ? (i == 0u ? L - 1u : i - 1u) : (i + 1u == L ? 0u : i + 1u);
+  if (ENC == kEncInt8) {
+    const uint8_t* A = static_cast<const uint8_t*>(buf);
+    const uint4* own = reinterpret_cast<const uint4*>(A + (size_t)i * L + 32u * c);
+    const uint4* ver = reinterpret_cast<const uint4*>(A + (size_t)iv * L + 32u * c);
+    const uint4 o0 = own[0], o1 = own[1], v0 = ver[0], v1 = ver[1];
+    const uint32_t jn = half == 0u ? (c == 0u ? L - 1u : 32u * c - 1u)
+                                   : (32u * c + 32u == L ? 0u : 32u * c + 32u);
+    const uint32_t nb = (A[(size_t)i * L + jn] >> 7) ^ 1u;  // 1 if +1
+    S = bits16(o0) | (bits16(o1) << 16);
+    V = bits16(v0) | (bits16(v1) << 16);
+    H = half == 0u ? ((S << 1) | nb) : ((S >> 1) | (nb << 31));
+  } else if (ENC == kEncPacked) {
+    const uint32_t* A = static_cast<const uint32_t*>(buf);
+    S = A[(size_t)i * wpr + c];
+    V = A[(size_t)iv * wpr + c];
+    if (half == 0u) {
+      const uint32_t cl = c == 0u ? wpr - 1u : c - 1u;
+      H = (S << 1) | (A[(size_t)i * wpr + cl] >> 31);
+    } else {
+      const uint32_t cr = c + 1u == wpr ? 0u : c + 1u;
+      H = (S >> 1) | (A[(size_t)i * wpr + cr] << 31);
+    }
+  } else {
+    const uint32_t* A = static_cast<const uint32_t*>(buf);
+    const uint32_t jn = half == 0u ? (c == 0u ? L - 1u : c - 1u) : (c + 1u == L ? 0u : c + 1u);
+    S = A[w];
+    V = A[(size_t)iv * L + c];
+    H = A[(size_t)i * L + jn];
+  }
+}
+
+// Per-tile state shared by the block: the job descriptor, its threshold table
+// for this step, and the step counter.
+struct TileShared {
+  LatJob job;
+  LatTable tab;
+  uint32_t t;
+  uint32_t skip;
+  uint32_t fuse;
+  int job_id;
+  const LatTable* tab_src;
+};
+
+// Each block walks a contiguous range of tiles (kLatTile lane words each; a
+// tile never spans two jobs).  Per tile: job descriptor and table staged in
+// shared memory, then every thread loads the words of its kWordsPerThread lane
+// words (all loads in flight together) and decides them one after another.
+template <int ENC>
+__global__ void __launch_bounds__(kTile, 3) lattice_half_kernel(const LatJob* __restrict__ jobs,
+                                                                const Tile* __restrict__ tiles,
+                                                                int n_tiles, uint32_t half,
+                                                                unsigned long long* rng_calls) {
+  __shared__ TileShared sh;
+  __shared__ const LatTable* staged;
   __shared__ double red[(kTile / 32) * 3];
   uint32_t calls = 0;
-  for (int ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
+  // balanced contiguous split: block b walks tiles [b n / G, (b+1) n / G)
+  const int tb = (int)(((long long)blockIdx.x * n_tiles) / gridDim.x);
+  const int te = (int)(((long long)(blockIdx.x + 1) * n_tiles) / gridDim.x);
+  if (threadIdx.x == 0) {
+    sh.job_id = -1;
+    sh.tab_src = nullptr;
+    staged = nullptr;
+  }
+  for (int ti = tb; ti < te; ++ti) {
+    __syncthreads();
     const Tile tl = tiles[ti];
-    const LatJob& J = jobs[tl.job];
-    const CtxDev* cd = J.cd;
-    const uint32_t t = cd->step;
-    if (t >= cd->t_end) continue;  // uniform per block
-    const LatTable* tab = J.table;
-    if (J.anneal_tables != nullptr && cd->anneal_len != 0u) {
-      uint32_t k = t - cd->anneal_t0;
-      if (k >= cd->anneal_len) k = cd->anneal_len - 1u;
-      tab = J.anneal_tables + k;
+    if ((int)tl.job != sh.job_id) {
+      // stage the job descriptor (one word per thread)
+      constexpr int nw = sizeof(LatJob) / 4;
+      if (threadIdx.x < nw)
+        reinterpret_cast<uint32_t*>(&sh.job)[threadIdx.x] =
+            reinterpret_cast<const uint32_t*>(jobs + tl.job)[threadIdx.x];
+      __syncthreads();
+      if (threadIdx.x == 0) sh.job_id = (int)tl.job;
     }
-    const uint32_t w = tl.w0 + threadIdx.x;
-    const bool active = w < J.nwords;
-    const bool fuse = (ENC != kEncMultispin) && half == 0u && J.sums != nullptr && cd->tracking;
-    double acc[3] = {0.0, 0.0, 0.0};
-    if (active) {
-      const uint32_t L = J.L, wpr = J.wpr;
-      const uint32_t i = w / wpr, c = w - i * wpr;
-      const uint32_t iv = half == 0u ? (i == 0u ? L - 1u : i - 1u) : (i + 1u == L ? 0u : i + 1u);
-      uint32_t S, V, H;
-      const void* src = half == 0u ? J.A : J.B;
-      void* dstbuf = half == 0u ? J.B : J.A;
-      if (ENC == kEncInt8) {
-        const uint8_t* A = static_cast<const uint8_t*>(src);
-        const uint4* own = reinterpret_cast<const uint4*>(A + (size_t)i * L + 32u * c);
-        const uint4* ver = reinterpret_cast<const uint4*>(A + (size_t)iv * L + 32u * c);
-        S = bits16(own[0]) | (bits16(own[1]) << 16);
-        V = bits16(ver[0]) | (bits16(ver[1]) << 16);
-        uint32_t jn = half == 0u ? (c == 0u ? L - 1u : 32u * c - 1u)
-                                 : (32u * c + 32u == L ? 0u : 32u * c + 32u);
-        const uint32_t nb = (A[(size_t)i * L + jn] >> 7) ^ 1u;  // 1 if +1
-        H = half == 0u ? ((S << 1) | nb) : ((S >> 1) | (nb << 31));
-      } else if (ENC == kEncPacked) {
-        const uint32_t* A = static_cast<const uint32_t*>(src);
-        S = A[(size_t)i * wpr + c];
-        V = A[(size_t)iv * wpr + c];
-        if (half == 0u) {
-          const uint32_t cl = c == 0u ? wpr - 1u : c - 1u;
-          H = (S << 1) | (A[(size_t)i * wpr + cl] >> 31);
-        } else {
-          const uint32_t cr = c + 1u == wpr ? 0u : c + 1u;
-          H = (S >> 1) | (A[(size_t)i * wpr + cr] << 31);
-        }
-      } else {
-        const uint32_t* A = static_cast<const uint32_t*>(src);
-        const uint32_t jn = half == 0u ? (c == 0u ? L - 1u : c - 1u) : (c + 1u == L ? 0u : c + 1u);
-        S = A[w];
-        V = A[(size_t)iv * L + c];
-        H = A[(size_t)i * L + jn];
+    if (threadIdx.x == 0) {
+      const CtxDev* cd = sh.job.cd;
+      const uint32_t t = cd->step;
+      sh.t = t;
+      sh.skip = t >= cd->t_end;
+      sh.fuse = (ENC != kEncMultispin) && half == 0u && sh.job.sums != nullptr && cd->tracking;
+      const LatTable* src = sh.job.table;
+      if (sh.job.anneal_tables != nullptr && cd->anneal_len != 0u) {
+        uint32_t k = t - cd->anneal_t0;
+        if (k >= cd->anneal_len) k = cd->anneal_len - 1u;
+        src = sh.job.anneal_tables + k;
       }
-      const uint32_t F = J.frozen != nullptr ? J.frozen[w] : 0u;
-      const PhKey K = ph_key(J.key0, J.key1);
-      const uint32_t tau = decide32(S, V, H, F, tab, K, w, J.b, t, half, calls);
+      sh.tab_src = src;
+    }
+    __syncthreads();
+    if (sh.skip) continue;
+    {  // stage the table (272 words) when it differs from the one in shared memory
+      if (staged != sh.tab_src) {
+        const uint32_t* g = reinterpret_cast<const uint32_t*>(sh.tab_src);
+        uint32_t* d = reinterpret_cast<uint32_t*>(&sh.tab);
+        for (int k = threadIdx.x; k < (int)(sizeof(LatTable) / 4); k += kTile) d[k] = g[k];
+        __syncthreads();
+        if (threadIdx.x == 0) staged = sh.tab_src;
+      }
+      __syncthreads();
+    }
+    const LatJob& J = sh.job;
+    const uint32_t t = sh.t;
+    const void* src = half == 0u ? J.A : J.B;
+    void* dstbuf = half == 0u ? J.B : J.A;
+    uint32_t S[kWordsPerThread], V[kWordsPerThread], H[kWordsPerThread], F[kWordsPerThread];
+#pragma unroll
+    for (int k = 0; k < kWordsPerThread; ++k) {
+      const uint32_t w = tl.w0 + threadIdx.x + k * kTile;
+      S[k] = V[k] = H[k] = 0u;
+      F[k] = 0u;
+      if (w < J.nwords) {
+        load_lane_words<ENC>(J, src, w, half, S[k], V[k], H[k]);
+        if (J.frozen != nullptr) F[k] = J.frozen[w];
+      }
+    }
+    const PhKey K = ph_key(J.key0, J.key1);
+    double acc[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < kWordsPerThread; ++k) {
+      const uint32_t w = tl.w0 + threadIdx.x + k * kTile;
+      if (w >= J.nwords) continue;
+      const LaneWord Lw = classify(S[k], V[k], H[k], F[k], sh.tab);
+      const uint32_t tau = decide_word(Lw, sh.tab, K, w, J.b, t, half, calls);
       if (ENC == kEncInt8) {
-        uint8_t* B = static_cast<uint8_t*>(dstbuf);
-        uint4* dst = reinterpret_cast<uint4*>(B + (size_t)i * L + 32u * c);
+        uint32_t i, c;
+        word_rc(J, w, i, c);
+        uint4* dst = reinterpret_cast<uint4*>(static_cast<uint8_t*>(dstbuf) + (size_t)i * J.L +
+                                              32u * c);
         dst[0] = bytes16(tau);
         dst[1] = bytes16(tau >> 16);
       } else {
         static_cast<uint32_t*>(dstbuf)[w] = tau;
       }
-      if (fuse) {
+      if (sh.fuse) {
         // sums of sigma_t over the lane word: M, E (in-edges down and left), cut
-        const int dv = __popc(S ^ V), dh = __popc(S ^ H);
-        acc[0] = (double)(2 * __popc(S) - 32);
-        acc[1] = (double)(64 - 2 * dv - 2 * dh);
-        acc[2] = (double)(dv + dh);
+        const int dv = __popc(S[k] ^ V[k]), dh = __popc(S[k] ^ H[k]);
+        acc[0] += (double)(2 * __popc(S[k]) - 32);
+        acc[1] += (double)(64 - 2 * dv - 2 * dh);
+        acc[2] += (double)(dv + dh);
       }
     }
-    if (fuse) {
-      // slots: M -> kSumM, E -> kSumE, cut -> kSumCut (write M, E, then cut separately)
+    if (sh.fuse) {
       double v2[2] = {acc[0], acc[1]};
       block_sum_atomic<2>(v2, J.sums + kSumM, red);
       double v1[1] = {acc[2]};
@@ -258,101 +374,66 @@ __global__ void __launch_bounds__(kTile) lattice_init_kernel(const LatJob* __res
   for (int ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
     const Tile tl = tiles[ti];
     const LatJob& J = jobs[tl.job];
-    const uint32_t w = tl.w0 + threadIdx.x;
-    if (w >= J.nwords) continue;
-    uint32_t s;
-    if (kind == 1) {
-      s = 0xffffffffu;
-    } else if (kind == 2) {
-      s = 0u;
-    } else {
-      const PhKey K = ph_key(J.key0, J.key1);
-      const uint4 W = ph_call(K, w, J.b, kInitStep, 0u);
-      s = ~W.x;
-    }
-    if (J.frozen != nullptr) s |= J.frozen[w];
-    if (ENC == kEncInt8) {
-      const uint32_t L = J.L, wpr = J.wpr;
-      const uint32_t i = w / wpr, c = w - i * wpr;
-      const size_t off = (size_t)i * L + 32u * c;
-      uint4* a = reinterpret_cast<uint4*>(static_cast<uint8_t*>(J.A) + off);
-      uint4* b = reinterpret_cast<uint4*>(static_cast<uint8_t*>(J.B) + off);
-      a[0] = b[0] = bytes16(s);
-      a[1] = b[1] = bytes16(s >> 16);
-    } else {
-      static_cast<uint32_t*>(J.A)[w] = s;
-      static_cast<uint32_t*>(J.B)[w] = s;
+    for (int k = 0; k < kWordsPerThread; ++k) {
+      const uint32_t w = tl.w0 + threadIdx.x + k * kTile;
+      if (w >= J.nwords) break;
+      uint32_t s;
+      if (kind == 1) {
+        s = 0xffffffffu;
+      } else if (kind == 2) {
+        s = 0u;
+      } else {
+        const PhKey K = ph_key(J.key0, J.key1);
+        const uint4 W = ph_call(K, w, J.b, kInitStep, 0u);
+        s = ~W.x;
+      }
+      if (J.frozen != nullptr) s |= J.frozen[w];
+      if (ENC == kEncInt8) {
+        uint32_t i, c;
+        word_rc(J, w, i, c);
+        const size_t off = (size_t)i * J.L + 32u * c;
+        uint4* a = reinterpret_cast<uint4*>(static_cast<uint8_t*>(J.A) + off);
+        uint4* b = reinterpret_cast<uint4*>(static_cast<uint8_t*>(J.B) + off);
+        a[0] = b[0] = bytes16(s);
+        a[1] = b[1] = bytes16(s >> 16);
+      } else {
+        static_cast<uint32_t*>(J.A)[w] = s;
+        static_cast<uint32_t*>(J.B)[w] = s;
+      }
     }
   }
 }
 
 // --------------------------------------------------------------------------- observables
 // INT8 / PACKED: per lane word, integer sums of sigma (A) and sigma' (B):
-//   M, E = in-edge agreement sum (down, left), P1 = sum sigma_x (sigma'_up + sigma'_right),
+//   M, E = in-edge product sum (down, left), P1 = sum sigma_x (sigma'_up + sigma'_right),
 //   P2 = sum sigma_x sigma'_x, M2 = sum sigma', cut.
-template <int ENC>
-__device__ __forceinline__ void load_lane_words(const LatJob& J, const void* buf, uint32_t w,
-                                                uint32_t half, uint32_t& S, uint32_t& V,
-                                                uint32_t& H) {
-  const uint32_t L = J.L, wpr = J.wpr;
-  const uint32_t i = w / wpr, c = w - i * wpr;
-  const uint32_t iv = half == 0u ? (i == 0u ? L - 1u : i - 1u) : (i + 1u == L ? 0u : i + 1u);
-  if (ENC == kEncInt8) {
-    const uint8_t* A = static_cast<const uint8_t*>(buf);
-    const uint4* own = reinterpret_cast<const uint4*>(A + (size_t)i * L + 32u * c);
-    const uint4* ver = reinterpret_cast<const uint4*>(A + (size_t)iv * L + 32u * c);
-    S = bits16(own[0]) | (bits16(own[1]) << 16);
-    V = bits16(ver[0]) | (bits16(ver[1]) << 16);
-    const uint32_t jn = half == 0u ? (c == 0u ? L - 1u : 32u * c - 1u)
-                                   : (32u * c + 32u == L ? 0u : 32u * c + 32u);
-    const uint32_t nb = (A[(size_t)i * L + jn] >> 7) ^ 1u;
-    H = half == 0u ? ((S << 1) | nb) : ((S >> 1) | (nb << 31));
-  } else if (ENC == kEncPacked) {
-    const uint32_t* A = static_cast<const uint32_t*>(buf);
-    S = A[(size_t)i * wpr + c];
-    V = A[(size_t)iv * wpr + c];
-    if (half == 0u) {
-      const uint32_t cl = c == 0u ? wpr - 1u : c - 1u;
-      H = (S << 1) | (A[(size_t)i * wpr + cl] >> 31);
-    } else {
-      const uint32_t cr = c + 1u == wpr ? 0u : c + 1u;
-      H = (S >> 1) | (A[(size_t)i * wpr + cr] << 31);
-    }
-  } else {
-    const uint32_t* A = static_cast<const uint32_t*>(buf);
-    const uint32_t jn = half == 0u ? (c == 0u ? L - 1u : c - 1u) : (c + 1u == L ? 0u : c + 1u);
-    S = A[w];
-    V = A[(size_t)iv * L + c];
-    H = A[(size_t)i * L + jn];
-  }
-}
-
 template <int ENC>
 __global__ void __launch_bounds__(kTile) lattice_obs_single_kernel(
     const LatJob* __restrict__ jobs, const Tile* __restrict__ tiles, int n_tiles, int which,
     int full) {
-  __shared__ double red[(kTile / 32) * 6];
+  __shared__ double red[(kTile / 32) * 3];
   for (int ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
     const Tile tl = tiles[ti];
     const LatJob& J = jobs[tl.job];
-    const uint32_t w = tl.w0 + threadIdx.x;
     double v[6] = {0, 0, 0, 0, 0, 0};
-    if (w < J.nwords) {
+    for (int k = 0; k < kWordsPerThread; ++k) {
+      const uint32_t w = tl.w0 + threadIdx.x + k * kTile;
+      if (w >= J.nwords) break;
       uint32_t S, V, H;
       load_lane_words<ENC>(J, J.A, w, 0u, S, V, H);
       const int dv = __popc(S ^ V), dh = __popc(S ^ H);
-      v[0] = (double)(2 * __popc(S) - 32);
-      v[1] = (double)(64 - 2 * dv - 2 * dh);
-      v[5] = (double)(dv + dh);
+      v[0] += (double)(2 * __popc(S) - 32);
+      v[1] += (double)(64 - 2 * dv - 2 * dh);
+      v[5] += (double)(dv + dh);
       if (full) {
         uint32_t S2, U2, R2;
         load_lane_words<ENC>(J, J.B, w, 1u, S2, U2, R2);  // sigma', its up and right bits
-        v[2] = (double)(64 - 2 * __popc(S ^ U2) - 2 * __popc(S ^ R2));
-        v[3] = (double)(32 - 2 * __popc(S ^ S2));
-        v[4] = (double)(2 * __popc(S2) - 32);
+        v[2] += (double)(64 - 2 * __popc(S ^ U2) - 2 * __popc(S ^ R2));
+        v[3] += (double)(32 - 2 * __popc(S ^ S2));
+        v[4] += (double)(2 * __popc(S2) - 32);
       }
     }
-    // slots 0:M 1:E 2:P1 3:P2 4:M2 5:cut -> kSumM, kSumE, kSumP1, kSumP2, kSumM2, kSumCut
     double* dst = which ? J.obs : J.sums;
     double a[2] = {v[0], v[1]};
     block_sum_atomic<2>(a, dst + kSumM, red);
@@ -364,7 +445,8 @@ __global__ void __launch_bounds__(kTile) lattice_obs_single_kernel(
 }
 
 // MULTISPIN: per-lane (= per replica) sums.  Each warp covers 32 consecutive
-// sites; for every mask the warp ballots bit k and lane k adds the popcount.
+// sites at a time; for every mask the warp ballots bit k and lane k adds the
+// popcount.
 __global__ void __launch_bounds__(kTile) lattice_obs_multispin_kernel(
     const LatJob* __restrict__ jobs, const Tile* __restrict__ tiles, int n_tiles, int which,
     int full) {
@@ -373,40 +455,41 @@ __global__ void __launch_bounds__(kTile) lattice_obs_multispin_kernel(
   for (int ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
     const Tile tl = tiles[ti];
     const LatJob& J = jobs[tl.job];
-    const uint32_t w = tl.w0 + threadIdx.x;
-    const bool act = w < J.nwords;
-    uint32_t S = 0, V = 0, H = 0, S2 = 0, U2 = 0, R2 = 0;
-    if (act) {
-      load_lane_words<kEncMultispin>(J, J.A, w, 0u, S, V, H);
-      if (full) load_lane_words<kEncMultispin>(J, J.B, w, 1u, S2, U2, R2);
-    }
-    // agreement masks (1 = product +1)
-    const uint32_t act_m = act ? 0xffffffffu : 0u;
-    const uint32_t m_plus = S & act_m;
-    const uint32_t ag_v = ~(S ^ V) & act_m, ag_h = ~(S ^ H) & act_m;
-    const uint32_t ag_u = ~(S ^ U2) & act_m, ag_r = ~(S ^ R2) & act_m;
-    const uint32_t ag_s = ~(S ^ S2) & act_m, p2 = S2 & act_m;
     int cnt[6] = {0, 0, 0, 0, 0, 0};
-    const int nact = __popc(__ballot_sync(0xffffffffu, act));
-#pragma unroll 4
-    for (int k = 0; k < 32; ++k) {
-      const int c0 = __popc(__ballot_sync(0xffffffffu, (m_plus >> k) & 1u));
-      const int c1 = __popc(__ballot_sync(0xffffffffu, (ag_v >> k) & 1u)) +
-                     __popc(__ballot_sync(0xffffffffu, (ag_h >> k) & 1u));
-      int c2 = 0, c3 = 0, c4 = 0;
-      if (full) {
-        c2 = __popc(__ballot_sync(0xffffffffu, (ag_u >> k) & 1u)) +
-             __popc(__ballot_sync(0xffffffffu, (ag_r >> k) & 1u));
-        c3 = __popc(__ballot_sync(0xffffffffu, (ag_s >> k) & 1u));
-        c4 = __popc(__ballot_sync(0xffffffffu, (p2 >> k) & 1u));
+    for (int sub = 0; sub < kWordsPerThread; ++sub) {
+      const uint32_t w = tl.w0 + threadIdx.x + sub * kTile;
+      const bool act = w < J.nwords;
+      uint32_t S = 0, V = 0, H = 0, S2 = 0, U2 = 0, R2 = 0;
+      if (act) {
+        load_lane_words<kEncMultispin>(J, J.A, w, 0u, S, V, H);
+        if (full) load_lane_words<kEncMultispin>(J, J.B, w, 1u, S2, U2, R2);
       }
-      if (lane == k) {
-        cnt[0] = 2 * c0 - nact;          // sum sigma
-        cnt[1] = 2 * c1 - 2 * nact;      // in-edge products
-        cnt[2] = 2 * c2 - 2 * nact;      // P1
-        cnt[3] = 2 * c3 - nact;          // P2
-        cnt[4] = 2 * c4 - nact;          // M2
-        cnt[5] = 2 * nact - c1;          // cut = disagreements
+      const uint32_t act_m = act ? 0xffffffffu : 0u;
+      const uint32_t m_plus = S & act_m;
+      const uint32_t ag_v = ~(S ^ V) & act_m, ag_h = ~(S ^ H) & act_m;
+      const uint32_t ag_u = ~(S ^ U2) & act_m, ag_r = ~(S ^ R2) & act_m;
+      const uint32_t ag_s = ~(S ^ S2) & act_m, p2 = S2 & act_m;
+      const int nact = __popc(__ballot_sync(0xffffffffu, act));
+#pragma unroll 4
+      for (int k = 0; k < 32; ++k) {
+        const int c0 = __popc(__ballot_sync(0xffffffffu, (m_plus >> k) & 1u));
+        const int c1 = __popc(__ballot_sync(0xffffffffu, (ag_v >> k) & 1u)) +
+                       __popc(__ballot_sync(0xffffffffu, (ag_h >> k) & 1u));
+        int c2 = 0, c3 = 0, c4 = 0;
+        if (full) {
+          c2 = __popc(__ballot_sync(0xffffffffu, (ag_u >> k) & 1u)) +
+               __popc(__ballot_sync(0xffffffffu, (ag_r >> k) & 1u));
+          c3 = __popc(__ballot_sync(0xffffffffu, (ag_s >> k) & 1u));
+          c4 = __popc(__ballot_sync(0xffffffffu, (p2 >> k) & 1u));
+        }
+        if (lane == k) {
+          cnt[0] += 2 * c0 - nact;      // sum sigma
+          cnt[1] += 2 * c1 - 2 * nact;  // in-edge products
+          cnt[2] += 2 * c2 - 2 * nact;  // P1
+          cnt[3] += 2 * c3 - nact;      // P2
+          cnt[4] += 2 * c4 - nact;      // M2
+          cnt[5] += 2 * nact - c1;      // cut = disagreements
+        }
       }
     }
 #pragma unroll
@@ -451,7 +534,21 @@ cudaError_t launch_lattice_half(int enc, const LatJob* jobs, const Tile* tiles, 
                                 uint32_t half, int blocks_per_sm, unsigned long long* rng_calls,
                                 cudaStream_t st) {
   if (n_tiles <= 0) return cudaSuccess;
-  const int grid = grid_for(n_tiles, blocks_per_sm);
+  // one wave: every block resident, each walking a contiguous range of tiles
+  static int occ[3] = {0, 0, 0};
+  if (occ[enc] == 0) {
+    int o = 1;
+    if (enc == kEncInt8)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lattice_half_kernel<kEncInt8>, kTile, 0);
+    else if (enc == kEncPacked)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lattice_half_kernel<kEncPacked>, kTile, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lattice_half_kernel<kEncMultispin>, kTile,
+                                                    0);
+    occ[enc] = o > 0 ? o : 1;
+  }
+  (void)blocks_per_sm;
+  const int grid = grid_for(n_tiles, occ[enc]);
   switch (enc) {
     case kEncInt8:
       lattice_half_kernel<kEncInt8><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, half, rng_calls);

@@ -230,8 +230,8 @@ static cudaStream_t ctx_stream(const shaken_ctx* c) {
   return c->owner ? c->owner->stream : c->stream;
 }
 
-static void add_tiles(std::vector<Tile>& tiles, uint32_t job, uint64_t count) {
-  for (uint64_t w = 0; w < count; w += kTile) tiles.push_back(Tile{job, (uint32_t)w});
+static void add_tiles(std::vector<Tile>& tiles, uint32_t job, uint64_t count, uint32_t size) {
+  for (uint64_t w = 0; w < count; w += size) tiles.push_back(Tile{job, (uint32_t)w});
 }
 
 static shaken_status build_plan(Plan& P, cudaStream_t st) {
@@ -271,7 +271,10 @@ static shaken_status build_plan(Plan& P, cudaStream_t st) {
         J.key0 = key0;
         J.key1 = key1;
         J.rep0 = (uint32_t)rep0;
-        add_tiles(tiles[e], (uint32_t)ljobs[e].size(), nwords);
+        J.wpr_shift = 0xffffffffu;
+        for (uint32_t sh = 0; sh < 32; ++sh)
+          if ((1u << sh) == wpr) J.wpr_shift = sh;
+        add_tiles(tiles[e], (uint32_t)ljobs[e].size(), nwords, (uint32_t)shk::kLatTile);
         ljobs[e].push_back(J);
       }
     } else {
@@ -302,7 +305,7 @@ static shaken_status build_plan(Plan& P, cudaStream_t st) {
         J.key1 = key1;
         J.integer = c->integer ? 1u : 0u;
         J.rep0 = (uint32_t)(32 * g);
-        add_tiles(tiles[3 + fi], (uint32_t)gjobs[fi].size(), (uint64_t)c->n);
+        add_tiles(tiles[3 + fi], (uint32_t)gjobs[fi].size(), (uint64_t)c->n, (uint32_t)kTile);
         gjobs[fi].push_back(J);
       }
     }

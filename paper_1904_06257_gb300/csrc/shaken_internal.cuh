@@ -29,7 +29,9 @@ constexpr uint32_t kPhW0 = 0x9E3779B9u;
 constexpr uint32_t kPhW1 = 0xBB67AE85u;
 constexpr uint32_t kInitStep = 0xFFFFFFFFu;  // step index of the initial draw
 
-constexpr int kTile = 256;  // lane words (or vertices) per tile = threads per block
+constexpr int kTile = 256;  // threads per block; graph tiles hold kTile vertices
+constexpr int kWordsPerThread = 4;                   // lattice lane words per thread and tile
+constexpr int kLatTile = kTile * kWordsPerThread;    // lattice lane words per tile
 
 // ---------------------------------------------------------------- Philox-4x32-10
 struct PhKey {
@@ -169,7 +171,7 @@ struct LatJob {
   uint32_t b;                    // counter word b: replica (int8/packed) or group (multispin)
   uint32_t key0, key1;
   uint32_t rep0;                 // first replica index of the job within its context
-  uint32_t pad;
+  uint32_t wpr_shift;            // log2(wpr) when wpr is a power of two, else 0xffffffff
 };
 
 // One graph job: a 32-replica group of a graph context.
