@@ -280,6 +280,30 @@ shaken_status shaken_philox_device(uint64_t seed, const uint32_t* ctr, uint32_t*
 shaken_status shaken_threshold_device(const double* h, const double* beta, uint64_t* out,
                                       int64_t n, void* cuda_stream);
 
+/* Observables of a lattice state held by the caller, computed without any
+ * device or host allocation.  The paper has no counterpart: this exists for
+ * callers that cannot call cudaMalloc -- code that manages all device memory
+ * through its own pool or caching allocator, or that must avoid the
+ * synchronisation an allocation may imply in the middle of its work.
+ *   sigma_dev, sigma_prime_dev: DEVICE pointers, 16-byte aligned, in the layout
+ *     of `encoding` (see the enum above; INT8 [R][L][L], PACKED [R][L][L/32]
+ *     uint32, MULTISPIN [R/32][L][L] uint32), owned by the caller, only read.
+ *   out_host: HOST array [replicas] receiving magnetization, energy, pair
+ *     energy, cut_edges and cut_weight as shaken_observables computes them;
+ *     best_energy = energy and best_step = -1 (no history here).
+ * The reduction scratch is a fixed device array inside the library (for at
+ * most 4096 replicas, about 0.5 MiB, held by every GPU that loads the library
+ * until the process exits).  More replicas return SHAKEN_E_INVAL.  The first
+ * call on each device looks up that array's device address; make that first
+ * call before any stream capture.  Every call clears the scratch it uses, but
+ * all calls share it: calls that overlap on the GPU race and must be
+ * serialised by the caller.  Synchronises cuda_stream before returning. */
+shaken_status shaken_lattice_observables_noalloc(const void* sigma_dev,
+                                                 const void* sigma_prime_dev, int32_t encoding,
+                                                 int64_t L, int32_t replicas, double J, double q,
+                                                 double lambda_const, shaken_obs* out_host,
+                                                 void* cuda_stream);
+
 const char* shaken_strerror(shaken_status s);
 const char* shaken_last_error(void);
 const char* shaken_version(void);

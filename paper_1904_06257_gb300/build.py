@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libshaken.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["lattice.cu", "graph.cu", "misc.cu", "runtime.cu"]
+SOURCES = ["lattice.cu", "graph.cu", "misc.cu", "noalloc.cu", "runtime.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -65,6 +65,8 @@ static shaken_status fail(shaken_status s, const std::string& msg) {
   return s;
 }
 
+void shaken_internal_set_error(const char* msg) { g_last_error = msg; }
+
 #define CU(call)                                                                    \
   do {                                                                              \
     cudaError_t e_ = (call);                                                        \

@@ -102,6 +102,7 @@ def _load():
         "shaken_server_drain": [vp, d],
         "shaken_server_stats": [vp, ctypes.POINTER(d), ctypes.POINTER(u64), ctypes.POINTER(i64)],
         "shaken_philox_device": [u64, vp, vp, i64, vp],
+        "shaken_lattice_observables_noalloc": [vp, vp, i32, i64, i32, d, d, d, vp, vp],
         "shaken_threshold_device": [vp, vp, vp, i64, vp],
     }
     for name, args in sigs.items():
@@ -392,6 +393,17 @@ def shaken_threshold_device(h_dev_ptr: int, beta_dev_ptr: int, out_dev_ptr: int,
                             stream=None):
     _check(_lib.shaken_threshold_device(ctypes.c_void_p(h_dev_ptr), ctypes.c_void_p(beta_dev_ptr),
                                         ctypes.c_void_p(out_dev_ptr), n, _stream(stream)))
+
+
+def shaken_lattice_observables_noalloc(sigma_dev_ptr: int, sigma_prime_dev_ptr: int,
+                                       encoding: int, L: int, replicas: int, J: float, q: float,
+                                       lambda_const: float, stream=None):
+    """Observables of caller-held device spin buffers; the library allocates nothing."""
+    out = np.zeros(replicas, dtype=OBS_DTYPE)
+    _check(_lib.shaken_lattice_observables_noalloc(
+        ctypes.c_void_p(sigma_dev_ptr), ctypes.c_void_p(sigma_prime_dev_ptr), encoding, L,
+        replicas, J, q, lambda_const, _ptr(out), _stream(stream)))
+    return out
 
 
 def shaken_version() -> str:
