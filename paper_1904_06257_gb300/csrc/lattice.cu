@@ -118,26 +118,31 @@ __device__ __forceinline__ LaneWord classify(uint32_t S, uint32_t V, uint32_t H,
   return L;
 }
 
-// Full decision of one lane word: calls 0 and 1 (planes 31..24) are made
-// unconditionally (independent, so they overlap), later calls only while
-// some lane is still undecided.
-__device__ __forceinline__ uint32_t decide_word(LaneWord L, const LatTable& tab, const PhKey& K,
-                                                uint32_t a, uint32_t b, uint32_t t, uint32_t half,
-                                                uint32_t& calls) {
+// Calls 0 and 1 (planes 31..24) of a lane word, made unconditionally: the two
+// Philox calls are independent and overlap.  After them about 12% of the words
+// still have an undecided lane (each lane is undecided with probability 2^-8).
+__device__ __forceinline__ void decide_head(LaneWord& L, const LatTable& tab, const PhKey& K,
+                                            uint32_t a, uint32_t b, uint32_t t, uint32_t half,
+                                            uint32_t& calls) {
   if (L.U != 0u) {
     const uint4 w0 = ph_call(K, a, b, t, half);
     const uint4 w1 = ph_call(K, a, b, t, half + 2u);
     calls += 2;
     apply_call(L, w0, &tab.tm[0][0]);
     apply_call(L, w1, &tab.tm[4][0]);
-#pragma unroll 1
-    for (uint32_t call = 2; call < 8 && L.U != 0u; ++call) {
-      const uint4 w = ph_call(K, a, b, t, half + 2u * call);
-      ++calls;
-      apply_call(L, w, &tab.tm[4 * call][0]);
-    }
   }
-  return L.res;
+}
+
+// Calls 2..7 while some lane is undecided.
+__device__ __forceinline__ void decide_tail(LaneWord& L, const LatTable& tab, const PhKey& K,
+                                            uint32_t a, uint32_t b, uint32_t t, uint32_t half,
+                                            uint32_t& calls) {
+#pragma unroll 1
+  for (uint32_t call = 2; call < 8 && L.U != 0u; ++call) {
+    const uint4 w = ph_call(K, a, b, t, half + 2u * call);
+    ++calls;
+    apply_call(L, w, &tab.tm[4 * call][0]);
+  }
 }
 
 // --------------------------------------------------------------------------- int8 <-> bits
@@ -238,84 +243,100 @@ __device__ __forceinline__ void load_lane_words(const LatJob& J, const void* buf
   }
 }
 
-// Per-tile state shared by the block: the job descriptor, its threshold table
-// for this step, and the step counter.
+// Per-job state shared by the block: the job descriptor, its threshold table
+// for this step and the step counter.  Staged only when the job changes (the
+// step counter and the table of a job are fixed for the whole launch).
 struct TileShared {
   LatJob job;
   LatTable tab;
   uint32_t t;
   uint32_t skip;
   uint32_t fuse;
-  int job_id;
   const LatTable* tab_src;
 };
 
-// Each block walks a contiguous range of tiles (kLatTile lane words each; a
-// tile never spans two jobs).  Per tile: job descriptor and table staged in
-// shared memory, then every thread loads the words of its kWordsPerThread lane
-// words (all loads in flight together) and decides them one after another.
+// A lane word still undecided after planes 31..24, parked in its warp's queue.
+struct Pending {
+  uint32_t w, S, V, X, U, res;
+};
+
+
 template <int ENC>
+__device__ __forceinline__ void store_word(const LatJob& J, void* dstbuf, uint32_t w,
+                                           uint32_t tau) {
+  if (ENC == kEncInt8) {
+    uint32_t i, c;
+    word_rc(J, w, i, c);
+    uint4* dst =
+        reinterpret_cast<uint4*>(static_cast<uint8_t*>(dstbuf) + (size_t)i * J.L + 32u * c);
+    dst[0] = bytes16(tau);
+    dst[1] = bytes16(tau >> 16);
+  } else {
+    static_cast<uint32_t*>(dstbuf)[w] = tau;
+  }
+}
+
+// Each block walks a contiguous range of tiles (kLatTile lane words each; a
+// tile never spans two jobs).  Per tile every thread loads the words of its
+// kWordsPerThread lane words (all loads in flight together) and runs planes
+// 31..24 of each; words with lanes still undecided are parked in the warp's
+// queue and finished afterwards 32 at a time, so the warp pays the rare later
+// planes once per 32 such words instead of once per word position.
+template <int ENC, int WPT>
 __global__ void __launch_bounds__(kTile, 3) lattice_half_kernel(const LatJob* __restrict__ jobs,
                                                                 const Tile* __restrict__ tiles,
                                                                 int n_tiles, uint32_t half,
                                                                 unsigned long long* rng_calls) {
   __shared__ TileShared sh;
-  __shared__ const LatTable* staged;
+  __shared__ Pending queue[kTile / 32][32 * WPT];
   __shared__ double red[(kTile / 32) * 3];
   uint32_t calls = 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt_mask = (1u << lane) - 1u;
   // balanced contiguous split: block b walks tiles [b n / G, (b+1) n / G)
   const int tb = (int)(((long long)blockIdx.x * n_tiles) / gridDim.x);
   const int te = (int)(((long long)(blockIdx.x + 1) * n_tiles) / gridDim.x);
-  if (threadIdx.x == 0) {
-    sh.job_id = -1;
-    sh.tab_src = nullptr;
-    staged = nullptr;
-  }
+  int cur_job = -1;
   for (int ti = tb; ti < te; ++ti) {
-    __syncthreads();
     const Tile tl = tiles[ti];
-    if ((int)tl.job != sh.job_id) {
-      // stage the job descriptor (one word per thread)
+    if ((int)tl.job != cur_job) {
+      __syncthreads();  // every warp is done with the previous job's staged state
       constexpr int nw = sizeof(LatJob) / 4;
       if (threadIdx.x < nw)
         reinterpret_cast<uint32_t*>(&sh.job)[threadIdx.x] =
             reinterpret_cast<const uint32_t*>(jobs + tl.job)[threadIdx.x];
       __syncthreads();
-      if (threadIdx.x == 0) sh.job_id = (int)tl.job;
-    }
-    if (threadIdx.x == 0) {
-      const CtxDev* cd = sh.job.cd;
-      const uint32_t t = cd->step;
-      sh.t = t;
-      sh.skip = t >= cd->t_end;
-      sh.fuse = (ENC != kEncMultispin) && half == 0u && sh.job.sums != nullptr && cd->tracking;
-      const LatTable* src = sh.job.table;
-      if (sh.job.anneal_tables != nullptr && cd->anneal_len != 0u) {
-        uint32_t k = t - cd->anneal_t0;
-        if (k >= cd->anneal_len) k = cd->anneal_len - 1u;
-        src = sh.job.anneal_tables + k;
+      if (threadIdx.x == 0) {
+        const CtxDev* cd = sh.job.cd;
+        const uint32_t t = cd->step;
+        sh.t = t;
+        sh.skip = t >= cd->t_end;
+        sh.fuse = (ENC != kEncMultispin) && half == 0u && sh.job.sums != nullptr && cd->tracking;
+        const LatTable* src = sh.job.table;
+        if (sh.job.anneal_tables != nullptr && cd->anneal_len != 0u) {
+          uint32_t k = t - cd->anneal_t0;
+          if (k >= cd->anneal_len) k = cd->anneal_len - 1u;
+          src = sh.job.anneal_tables + k;
+        }
+        sh.tab_src = src;
       }
-      sh.tab_src = src;
-    }
-    __syncthreads();
-    if (sh.skip) continue;
-    {  // stage the table (272 words) when it differs from the one in shared memory
-      if (staged != sh.tab_src) {
+      __syncthreads();
+      if (!sh.skip) {
         const uint32_t* g = reinterpret_cast<const uint32_t*>(sh.tab_src);
         uint32_t* d = reinterpret_cast<uint32_t*>(&sh.tab);
         for (int k = threadIdx.x; k < (int)(sizeof(LatTable) / 4); k += kTile) d[k] = g[k];
-        __syncthreads();
-        if (threadIdx.x == 0) staged = sh.tab_src;
       }
       __syncthreads();
+      cur_job = (int)tl.job;
     }
+    if (sh.skip) continue;
     const LatJob& J = sh.job;
     const uint32_t t = sh.t;
     const void* src = half == 0u ? J.A : J.B;
     void* dstbuf = half == 0u ? J.B : J.A;
-    uint32_t S[kWordsPerThread], V[kWordsPerThread], H[kWordsPerThread], F[kWordsPerThread];
+    uint32_t S[WPT], V[WPT], H[WPT], F[WPT];
 #pragma unroll
-    for (int k = 0; k < kWordsPerThread; ++k) {
+    for (int k = 0; k < WPT; ++k) {
       const uint32_t w = tl.w0 + threadIdx.x + k * kTile;
       S[k] = V[k] = H[k] = 0u;
       F[k] = 0u;
@@ -326,23 +347,29 @@ __global__ void __launch_bounds__(kTile, 3) lattice_half_kernel(const LatJob* __
     }
     const PhKey K = ph_key(J.key0, J.key1);
     double acc[3] = {0.0, 0.0, 0.0};
+    uint32_t qn = 0;  // warp-uniform queue length
 #pragma unroll
-    for (int k = 0; k < kWordsPerThread; ++k) {
+    for (int k = 0; k < WPT; ++k) {
       const uint32_t w = tl.w0 + threadIdx.x + k * kTile;
-      if (w >= J.nwords) continue;
-      const LaneWord Lw = classify(S[k], V[k], H[k], F[k], sh.tab);
-      const uint32_t tau = decide_word(Lw, sh.tab, K, w, J.b, t, half, calls);
-      if (ENC == kEncInt8) {
-        uint32_t i, c;
-        word_rc(J, w, i, c);
-        uint4* dst = reinterpret_cast<uint4*>(static_cast<uint8_t*>(dstbuf) + (size_t)i * J.L +
-                                              32u * c);
-        dst[0] = bytes16(tau);
-        dst[1] = bytes16(tau >> 16);
-      } else {
-        static_cast<uint32_t*>(dstbuf)[w] = tau;
+      const bool act = w < J.nwords;
+      LaneWord Lw = classify(S[k], V[k], H[k], F[k], sh.tab);
+      if (!act) Lw.U = 0u;
+      decide_head(Lw, sh.tab, K, w, J.b, t, half, calls);
+      const bool pend = act && Lw.U != 0u;
+      const uint32_t pm = __ballot_sync(0xffffffffu, pend);
+      if (pend) {
+        Pending& e = queue[warp][qn + __popc(pm & lt_mask)];
+        e.w = w;
+        e.S = Lw.S;
+        e.V = Lw.V;
+        e.X = Lw.X;
+        e.U = Lw.U;
+        e.res = Lw.res;
+      } else if (act) {
+        store_word<ENC>(J, dstbuf, w, Lw.res);
       }
-      if (sh.fuse) {
+      qn += __popc(pm);
+      if (sh.fuse && act) {
         // sums of sigma_t over the lane word: M, E (in-edges down and left), cut
         const int dv = __popc(S[k] ^ V[k]), dh = __popc(S[k] ^ H[k]);
         acc[0] += (double)(2 * __popc(S[k]) - 32);
@@ -350,6 +377,21 @@ __global__ void __launch_bounds__(kTile, 3) lattice_half_kernel(const LatJob* __
         acc[2] += (double)(dv + dh);
       }
     }
+    __syncwarp();
+    for (uint32_t base = 0; base < qn; base += 32u) {
+      if (base + lane < qn) {
+        const Pending e = queue[warp][base + lane];
+        LaneWord Lw;
+        Lw.S = e.S;
+        Lw.V = e.V;
+        Lw.X = e.X;
+        Lw.U = e.U;
+        Lw.res = e.res;
+        decide_tail(Lw, sh.tab, K, e.w, J.b, t, half, calls);
+        store_word<ENC>(J, dstbuf, e.w, Lw.res);
+      }
+    }
+    __syncwarp();
     if (sh.fuse) {
       double v2[2] = {acc[0], acc[1]};
       block_sum_atomic<2>(v2, J.sums + kSumM, red);
@@ -359,7 +401,7 @@ __global__ void __launch_bounds__(kTile, 3) lattice_half_kernel(const LatJob* __
   }
   if (rng_calls != nullptr) {
     const uint32_t wsum = __reduce_add_sync(0xffffffffu, calls);
-    if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(rng_calls, (unsigned long long)wsum);
+    if (lane == 0 && wsum) atomicAdd(rng_calls, (unsigned long long)wsum);
   }
 }
 
@@ -370,11 +412,11 @@ __global__ void __launch_bounds__(kTile, 3) lattice_half_kernel(const LatJob* __
 template <int ENC>
 __global__ void __launch_bounds__(kTile) lattice_init_kernel(const LatJob* __restrict__ jobs,
                                                              const Tile* __restrict__ tiles,
-                                                             int n_tiles, int kind) {
+                                                             int n_tiles, int kind, int wpt) {
   for (int ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
     const Tile tl = tiles[ti];
     const LatJob& J = jobs[tl.job];
-    for (int k = 0; k < kWordsPerThread; ++k) {
+    for (int k = 0; k < wpt; ++k) {
       const uint32_t w = tl.w0 + threadIdx.x + k * kTile;
       if (w >= J.nwords) break;
       uint32_t s;
@@ -411,13 +453,13 @@ __global__ void __launch_bounds__(kTile) lattice_init_kernel(const LatJob* __res
 template <int ENC>
 __global__ void __launch_bounds__(kTile) lattice_obs_single_kernel(
     const LatJob* __restrict__ jobs, const Tile* __restrict__ tiles, int n_tiles, int which,
-    int full) {
+    int full, int wpt) {
   __shared__ double red[(kTile / 32) * 3];
   for (int ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
     const Tile tl = tiles[ti];
     const LatJob& J = jobs[tl.job];
     double v[6] = {0, 0, 0, 0, 0, 0};
-    for (int k = 0; k < kWordsPerThread; ++k) {
+    for (int k = 0; k < wpt; ++k) {
       const uint32_t w = tl.w0 + threadIdx.x + k * kTile;
       if (w >= J.nwords) break;
       uint32_t S, V, H;
@@ -449,14 +491,14 @@ __global__ void __launch_bounds__(kTile) lattice_obs_single_kernel(
 // popcount.
 __global__ void __launch_bounds__(kTile) lattice_obs_multispin_kernel(
     const LatJob* __restrict__ jobs, const Tile* __restrict__ tiles, int n_tiles, int which,
-    int full) {
+    int full, int wpt) {
   __shared__ int red[kTile / 32][32][6];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
     const Tile tl = tiles[ti];
     const LatJob& J = jobs[tl.job];
     int cnt[6] = {0, 0, 0, 0, 0, 0};
-    for (int sub = 0; sub < kWordsPerThread; ++sub) {
+    for (int sub = 0; sub < wpt; ++sub) {
       const uint32_t w = tl.w0 + threadIdx.x + sub * kTile;
       const bool act = w < J.nwords;
       uint32_t S = 0, V = 0, H = 0, S2 = 0, U2 = 0, R2 = 0;
@@ -530,73 +572,80 @@ cudaError_t launch_build_lattice_tables(const double* beta_lanes, int ntab, doub
   return cudaGetLastError();
 }
 
-cudaError_t launch_lattice_half(int enc, const LatJob* jobs, const Tile* tiles, int n_tiles,
-                                uint32_t half, int blocks_per_sm, unsigned long long* rng_calls,
+template <int ENC, int WPT>
+static cudaError_t launch_half_t(const LatJob* jobs, const Tile* tiles, int n_tiles, uint32_t half,
+                                 unsigned long long* rng_calls, cudaStream_t st) {
+  // one wave: every block resident, each walking a contiguous range of tiles
+  static int occ = 0;
+  if (occ == 0) {
+    int o = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lattice_half_kernel<ENC, WPT>, kTile, 0);
+    occ = o > 0 ? o : 1;
+  }
+  const int grid = grid_for(n_tiles, occ);
+  lattice_half_kernel<ENC, WPT><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, half, rng_calls);
+  return cudaGetLastError();
+}
+
+int lattice_resident_blocks() {
+  int o = 1, dev = 0, sms = 152;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lattice_half_kernel<kEncMultispin, 4>, kTile,
+                                                0);
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return (o > 0 ? o : 1) * sms;
+}
+
+cudaError_t launch_lattice_half(int enc, int wpt, const LatJob* jobs, const Tile* tiles,
+                                int n_tiles, uint32_t half, unsigned long long* rng_calls,
                                 cudaStream_t st) {
   if (n_tiles <= 0) return cudaSuccess;
-  // one wave: every block resident, each walking a contiguous range of tiles
-  static int occ[3] = {0, 0, 0};
-  if (occ[enc] == 0) {
-    int o = 1;
-    if (enc == kEncInt8)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lattice_half_kernel<kEncInt8>, kTile, 0);
-    else if (enc == kEncPacked)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lattice_half_kernel<kEncPacked>, kTile, 0);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lattice_half_kernel<kEncMultispin>, kTile,
-                                                    0);
-    occ[enc] = o > 0 ? o : 1;
+  if (wpt == 4) {
+    if (enc == kEncInt8) return launch_half_t<kEncInt8, 4>(jobs, tiles, n_tiles, half, rng_calls, st);
+    if (enc == kEncPacked)
+      return launch_half_t<kEncPacked, 4>(jobs, tiles, n_tiles, half, rng_calls, st);
+    return launch_half_t<kEncMultispin, 4>(jobs, tiles, n_tiles, half, rng_calls, st);
   }
-  (void)blocks_per_sm;
-  const int grid = grid_for(n_tiles, occ[enc]);
+  if (enc == kEncInt8) return launch_half_t<kEncInt8, 1>(jobs, tiles, n_tiles, half, rng_calls, st);
+  if (enc == kEncPacked)
+    return launch_half_t<kEncPacked, 1>(jobs, tiles, n_tiles, half, rng_calls, st);
+  return launch_half_t<kEncMultispin, 1>(jobs, tiles, n_tiles, half, rng_calls, st);
+}
+
+cudaError_t launch_lattice_init(int enc, int wpt, const LatJob* jobs, const Tile* tiles,
+                                int n_tiles, int kind, cudaStream_t st) {
+  if (n_tiles <= 0) return cudaSuccess;
+  const int grid = grid_for(n_tiles, 8);
   switch (enc) {
     case kEncInt8:
-      lattice_half_kernel<kEncInt8><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, half, rng_calls);
+      lattice_init_kernel<kEncInt8><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, kind, wpt);
       break;
     case kEncPacked:
-      lattice_half_kernel<kEncPacked><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, half,
-                                                              rng_calls);
+      lattice_init_kernel<kEncPacked><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, kind, wpt);
       break;
     default:
-      lattice_half_kernel<kEncMultispin><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, half,
-                                                                 rng_calls);
+      lattice_init_kernel<kEncMultispin><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, kind,
+                                                                  wpt);
       break;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_lattice_init(int enc, const LatJob* jobs, const Tile* tiles, int n_tiles,
-                                int kind, cudaStream_t st) {
+cudaError_t launch_lattice_obs(int enc, int wpt, const LatJob* jobs, const Tile* tiles,
+                               int n_tiles, int which, int full, cudaStream_t st) {
   if (n_tiles <= 0) return cudaSuccess;
   const int grid = grid_for(n_tiles, 8);
   switch (enc) {
     case kEncInt8:
-      lattice_init_kernel<kEncInt8><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, kind);
-      break;
-    case kEncPacked:
-      lattice_init_kernel<kEncPacked><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, kind);
-      break;
-    default:
-      lattice_init_kernel<kEncMultispin><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, kind);
-      break;
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_lattice_obs(int enc, const LatJob* jobs, const Tile* tiles, int n_tiles,
-                               int which, int full, cudaStream_t st) {
-  if (n_tiles <= 0) return cudaSuccess;
-  const int grid = grid_for(n_tiles, 8);
-  switch (enc) {
-    case kEncInt8:
-      lattice_obs_single_kernel<kEncInt8><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, which, full);
+      lattice_obs_single_kernel<kEncInt8><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, which, full,
+                                                                   wpt);
       break;
     case kEncPacked:
       lattice_obs_single_kernel<kEncPacked><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, which,
-                                                                    full);
+                                                                    full, wpt);
       break;
     default:
-      lattice_obs_multispin_kernel<<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, which, full);
+      lattice_obs_multispin_kernel<<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, which, full, wpt);
       break;
   }
   return cudaGetLastError();

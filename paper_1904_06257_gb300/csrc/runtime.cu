@@ -33,11 +33,12 @@
 namespace shk {
 cudaError_t launch_build_lattice_tables(const double*, int, double, double, double, LatTable*,
                                         cudaStream_t);
-cudaError_t launch_lattice_half(int, const LatJob*, const Tile*, int, uint32_t, int,
+cudaError_t launch_lattice_half(int, int, const LatJob*, const Tile*, int, uint32_t,
                                 unsigned long long*, cudaStream_t);
+int lattice_resident_blocks();
 cudaError_t run_microbench(int, double*, double*);
-cudaError_t launch_lattice_init(int, const LatJob*, const Tile*, int, int, cudaStream_t);
-cudaError_t launch_lattice_obs(int, const LatJob*, const Tile*, int, int, int, cudaStream_t);
+cudaError_t launch_lattice_init(int, int, const LatJob*, const Tile*, int, int, cudaStream_t);
+cudaError_t launch_lattice_obs(int, int, const LatJob*, const Tile*, int, int, int, cudaStream_t);
 cudaError_t launch_graph_half(bool, const GraphJob*, const Tile*, int, uint32_t, int, int,
                               cudaStream_t);
 cudaError_t launch_graph_init(const GraphJob*, const Tile*, int, int, cudaStream_t);
@@ -125,6 +126,7 @@ static shaken_status upload(DevMem& d, const void* src, size_t n, cudaStream_t s
 struct Family {
   int kind = 0;  // 0 lattice, 1 graph
   int enc = 0;   // lattice encoding; graph: 1 integer couplings, 0 real
+  int wpt = 1;   // lattice: lane words per thread per tile (tile = 256 wpt words)
   DevMem jobs, tiles;
   int n_tiles = 0;
 };
@@ -243,6 +245,21 @@ static shaken_status build_plan(Plan& P, cudaStream_t st) {
   std::vector<std::vector<GraphJob>> gjobs(2);  // 0 integer, 1 real
   std::vector<std::vector<Tile>> tiles(5);
   std::vector<CtxDev*> cds;
+  // lattice tile size per encoding family: 4 lane words per thread when the
+  // family has enough tiles to keep one resident wave busy, else 1
+  int lat_wpt[3] = {1, 1, 1};
+  {
+    uint64_t words[3] = {0, 0, 0};
+    for (shaken_ctx* c : P.members) {
+      if (c->kind != SHAKEN_LATTICE) continue;
+      const bool multi = c->enc == SHAKEN_MULTISPIN;
+      const uint64_t per_job = multi ? (uint64_t)c->L * c->L : (uint64_t)c->L * c->L / 32;
+      words[c->enc] += per_job * (uint64_t)(multi ? c->R / 32 : c->R);
+    }
+    const uint64_t wave = (uint64_t)shk::lattice_resident_blocks();
+    for (int e = 0; e < 3; ++e)
+      lat_wpt[e] = words[e] / (uint64_t)shk::kLatTile >= 8 * wave ? shk::kWordsPerThread : 1;
+  }
   for (shaken_ctx* c : P.members) {
     CtxDev* cdp = c->cd.as<CtxDev>();
     cds.push_back(cdp);
@@ -276,7 +293,7 @@ static shaken_status build_plan(Plan& P, cudaStream_t st) {
         J.wpr_shift = 0xffffffffu;
         for (uint32_t sh = 0; sh < 32; ++sh)
           if ((1u << sh) == wpr) J.wpr_shift = sh;
-        add_tiles(tiles[e], (uint32_t)ljobs[e].size(), nwords, (uint32_t)shk::kLatTile);
+        add_tiles(tiles[e], (uint32_t)ljobs[e].size(), nwords, (uint32_t)(kTile * lat_wpt[e]));
         ljobs[e].push_back(J);
       }
     } else {
@@ -317,6 +334,7 @@ static shaken_status build_plan(Plan& P, cudaStream_t st) {
     auto F = std::make_unique<Family>();
     F->kind = 0;
     F->enc = e;
+    F->wpt = lat_wpt[e];
     TRY(upload(F->jobs, ljobs[e].data(), ljobs[e].size() * sizeof(LatJob), st));
     TRY(upload(F->tiles, tiles[e].data(), tiles[e].size() * sizeof(Tile), st));
     F->n_tiles = (int)tiles[e].size();
@@ -352,8 +370,8 @@ static shaken_status plan_step_launch(Plan& P, cudaStream_t st, uint64_t* nl,
   if (obs_needed) {
     for (auto& F : P.fams) {
       if (F->kind == 0 && F->enc == SHAKEN_MULTISPIN) {
-        CU(shk::launch_lattice_obs(F->enc, F->jobs.as<LatJob>(), F->tiles.as<Tile>(), F->n_tiles,
-                                   0, 0, st));
+        CU(shk::launch_lattice_obs(F->enc, F->wpt, F->jobs.as<LatJob>(), F->tiles.as<Tile>(),
+                                   F->n_tiles, 0, 0, st));
         ++count;
       } else if (F->kind == 1) {
         CU(shk::launch_graph_obs(F->jobs.as<GraphJob>(), F->tiles.as<Tile>(), F->n_tiles, 0, 0,
@@ -371,8 +389,8 @@ static shaken_status plan_step_launch(Plan& P, cudaStream_t st, uint64_t* nl,
         CU(cudaEventRecord(e0, st));
       }
       if (F->kind == 0)
-        CU(shk::launch_lattice_half(F->enc, F->jobs.as<LatJob>(), F->tiles.as<Tile>(),
-                                    F->n_tiles, half, P.blocks_per_sm, P.rng_counter, st));
+        CU(shk::launch_lattice_half(F->enc, F->wpt, F->jobs.as<LatJob>(), F->tiles.as<Tile>(),
+                                    F->n_tiles, half, P.rng_counter, st));
       else
         CU(shk::launch_graph_half(F->enc != 0, F->jobs.as<GraphJob>(), F->tiles.as<Tile>(),
                                   F->n_tiles, half, ex, P.blocks_per_sm, st));
@@ -637,8 +655,8 @@ static shaken_status ctx_init_spins(shaken_ctx* c, int kind, const int8_t* given
   if (c->solo.dirty) TRY(build_plan(c->solo, st));
   for (auto& F : c->solo.fams) {
     if (F->kind == 0)
-      CU(shk::launch_lattice_init(F->enc, F->jobs.as<LatJob>(), F->tiles.as<Tile>(), F->n_tiles,
-                                  kind, st));
+      CU(shk::launch_lattice_init(F->enc, F->wpt, F->jobs.as<LatJob>(), F->tiles.as<Tile>(),
+                                  F->n_tiles, kind, st));
     else
       CU(shk::launch_graph_init(F->jobs.as<GraphJob>(), F->tiles.as<Tile>(), F->n_tiles, kind,
                                 st));
@@ -894,8 +912,8 @@ shaken_status shaken_observables(shaken_ctx* ctx, shaken_obs* out) {
   CU(cudaMemsetAsync(ctx->obs_sums.p, 0, ctx->obs_sums.bytes, st));
   for (auto& F : ctx->solo.fams) {
     if (F->kind == 0)
-      CU(shk::launch_lattice_obs(F->enc, F->jobs.as<LatJob>(), F->tiles.as<Tile>(), F->n_tiles, 1,
-                                 1, st));
+      CU(shk::launch_lattice_obs(F->enc, F->wpt, F->jobs.as<LatJob>(), F->tiles.as<Tile>(),
+                                 F->n_tiles, 1, 1, st));
     else
       CU(shk::launch_graph_obs(F->jobs.as<GraphJob>(), F->tiles.as<Tile>(), F->n_tiles, 1, 1,
                                st));
