@@ -30,38 +30,61 @@ namespace shk {
 __global__ void __launch_bounds__(256) build_lattice_tables_kernel(
     const double* __restrict__ beta_lanes, int ntab, double J, double q, double lam,
     LatTable* __restrict__ out) {
+  __shared__ unsigned long long Ts[8][32];
+  __shared__ uint32_t sat_any[8];
   const int tab = blockIdx.x;
   if (tab >= ntab) return;
   const int lane = threadIdx.x & 31;
   const int c = threadIdx.x >> 5;  // 0..7
   LatTable* T = out + tab;
   if (c >= 6) {
-    if (lane < 32) {
-      T->tm[lane][c] = 0u;
-      if (lane == 0) {
-        T->satp[c] = 0u;
-        T->satm[c] = 0u;
-      }
+    T->tm[lane][c] = 0u;
+    if (lane == 0) {
+      T->satp[c] = 0u;
+      T->satm[c] = 0u;
+      sat_any[c] = 0u;
     }
-    return;
-  }
-  const int n = c >> 1, s = c & 1;
-  const double beta = beta_lanes[(size_t)tab * 32 + lane];
-  const double h = field_h(J, 2 * n - 2, q, 2 * s - 1, lam);
-  const unsigned long long Tv = threshold_T(h, beta);
-  const bool satp = Tv == 4294967296ULL;
-  const bool satm = Tv == 0ULL;
-  const unsigned sp = __ballot_sync(0xffffffffu, satp);
-  const unsigned sm = __ballot_sync(0xffffffffu, satm);
-  if (lane == 0) {
-    T->satp[c] = sp;
-    T->satm[c] = sm;
-  }
-  const uint32_t t32 = (satp || satm) ? 0u : (uint32_t)Tv;
+  } else {
+    const int n = c >> 1, s = c & 1;
+    const double beta = beta_lanes[(size_t)tab * 32 + lane];
+    const double h = field_h(J, 2 * n - 2, q, 2 * s - 1, lam);
+    const unsigned long long Tv = threshold_T(h, beta);
+    Ts[c][lane] = Tv;
+    const bool satp = Tv == 4294967296ULL;
+    const bool satm = Tv == 0ULL;
+    const unsigned sp = __ballot_sync(0xffffffffu, satp);
+    const unsigned sm = __ballot_sync(0xffffffffu, satm);
+    if (lane == 0) {
+      T->satp[c] = sp;
+      T->satm[c] = sm;
+      sat_any[c] = sp | sm;
+    }
+    const uint32_t t32 = (satp || satm) ? 0u : (uint32_t)Tv;
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    const unsigned m = __ballot_sync(0xffffffffu, (t32 >> (31 - j)) & 1u);
-    if (lane == 0) T->tm[j][c] = m;
+    for (int j = 0; j < 32; ++j) {
+      const unsigned m = __ballot_sync(0xffffffffu, (t32 >> (31 - j)) & 1u);
+      if (lane == 0) T->tm[j][c] = m;
+    }
+  }
+  __syncthreads();
+  if (c == 0) {
+    // thresholds depending on n + s only: (0,1) == (1,0) and (1,1) == (2,0) on every lane
+    const bool same = Ts[1][lane] == Ts[2][lane] && Ts[3][lane] == Ts[4][lane];
+    const bool coll = __all_sync(0xffffffffu, same);
+    if (lane == 0) {
+      T->collapsed = coll ? 1u : 0u;
+      uint32_t a = 0u;
+      for (int k = 0; k < 6; ++k) a |= sat_any[k];
+      T->anysat = a != 0u ? 1u : 0u;
+      T->pad[0] = T->pad[1] = 0u;
+    }
+  }
+  __syncthreads();
+  // planes by c = n + s: class 2n + s with (n, s) = (0,0), (0,1), (1,1), (2,1)
+  if (threadIdx.x < 128) {
+    const int j = threadIdx.x >> 2, cc = threadIdx.x & 3;
+    const int cls = cc == 0 ? 0 : cc == 1 ? 1 : cc == 2 ? 3 : 5;
+    T->tmc[j][cc] = T->tm[j][cls];
   }
 }
 
@@ -85,12 +108,25 @@ __device__ __forceinline__ uint32_t plane_bits(const LaneWord& L, const uint32_t
   return (L.X & b1) | (~L.X & m);
 }
 
+// Collapsed tables (thresholds by c = n + s): with c0 = parity and c1 =
+// majority of (V, H, S), c = c0 + 2 c1 and the plane bit is 3 selects.
+// Here L.V holds c1 and L.X holds c0.
+__device__ __forceinline__ uint32_t plane_bits_c(const LaneWord& L, const uint32_t* tmc) {
+  const uint4 t = *reinterpret_cast<const uint4*>(tmc);
+  const uint32_t lo = (L.X & t.y) | (~L.X & t.x);  // c1 = 0
+  const uint32_t hi = (L.X & t.w) | (~L.X & t.z);  // c1 = 1
+  return (L.V & hi) | (~L.V & lo);
+}
+
 // MSB-first comparison of u_k with T_k over the four planes of one Philox call.
-__device__ __forceinline__ void apply_call(LaneWord& L, const uint4 w, const uint32_t* tm_rows) {
+template <bool COLL>
+__device__ __forceinline__ void apply_call(LaneWord& L, const uint4 w, const LatTable& tab,
+                                           uint32_t call) {
   const uint32_t Wj[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const uint32_t P = plane_bits(L, tm_rows + 8 * i);
+    const uint32_t P = COLL ? plane_bits_c(L, &tab.tmc[4 * call + i][0])
+                            : plane_bits(L, &tab.tm[4 * call + i][0]);
     const uint32_t diff = (Wj[i] ^ P) & L.U;  // first plane where u and T differ
     L.res |= diff & P;                        // T has the 1 there: u < T
     L.U &= ~diff;
@@ -98,20 +134,28 @@ __device__ __forceinline__ void apply_call(LaneWord& L, const uint4 w, const uin
 }
 
 // Initial classification: frozen lanes and saturated thresholds (T = 0 or 2^32)
-// are decided before any draw.
+// are decided before any draw.  For collapsed tables V and X are replaced by
+// the majority and the parity of (V, H, S).
+template <bool COLL>
 __device__ __forceinline__ LaneWord classify(uint32_t S, uint32_t V, uint32_t H, uint32_t F,
                                              const LatTable& tab) {
   LaneWord L;
   L.S = S;
   L.V = V;
   L.X = V ^ H;
-  const uint32_t n2 = V & H, n0 = ~(V | H), n1 = L.X;
-  const uint32_t M[6] = {n0 & ~S, n0 & S, n1 & ~S, n1 & S, n2 & ~S, n2 & S};
   uint32_t dec = F, res = F;
+  if (tab.anysat) {
+    const uint32_t n2 = V & H, n0 = ~(V | H), n1 = L.X;
+    const uint32_t M[6] = {n0 & ~S, n0 & S, n1 & ~S, n1 & S, n2 & ~S, n2 & S};
 #pragma unroll
-  for (int c = 0; c < 6; ++c) {
-    dec |= M[c] & (tab.satp[c] | tab.satm[c]);
-    res |= M[c] & tab.satp[c];
+    for (int c = 0; c < 6; ++c) {
+      dec |= M[c] & (tab.satp[c] | tab.satm[c]);
+      res |= M[c] & tab.satp[c];
+    }
+  }
+  if (COLL) {
+    L.V = (V & H) | (S & (V | H));  // majority
+    L.X = V ^ H ^ S;                // parity
   }
   L.U = ~dec;
   L.res = res;
@@ -121,6 +165,7 @@ __device__ __forceinline__ LaneWord classify(uint32_t S, uint32_t V, uint32_t H,
 // Calls 0 and 1 (planes 31..24) of a lane word, made unconditionally: the two
 // Philox calls are independent and overlap.  After them about 12% of the words
 // still have an undecided lane (each lane is undecided with probability 2^-8).
+template <bool COLL>
 __device__ __forceinline__ void decide_head(LaneWord& L, const LatTable& tab, const PhKey& K,
                                             uint32_t a, uint32_t b, uint32_t t, uint32_t half,
                                             uint32_t& calls) {
@@ -128,12 +173,13 @@ __device__ __forceinline__ void decide_head(LaneWord& L, const LatTable& tab, co
     const uint4 w0 = ph_call(K, a, b, t, half);
     const uint4 w1 = ph_call(K, a, b, t, half + 2u);
     calls += 2;
-    apply_call(L, w0, &tab.tm[0][0]);
-    apply_call(L, w1, &tab.tm[4][0]);
+    apply_call<COLL>(L, w0, tab, 0u);
+    apply_call<COLL>(L, w1, tab, 1u);
   }
 }
 
 // Calls 2..7 while some lane is undecided.
+template <bool COLL>
 __device__ __forceinline__ void decide_tail(LaneWord& L, const LatTable& tab, const PhKey& K,
                                             uint32_t a, uint32_t b, uint32_t t, uint32_t half,
                                             uint32_t& calls) {
@@ -141,7 +187,7 @@ __device__ __forceinline__ void decide_tail(LaneWord& L, const LatTable& tab, co
   for (uint32_t call = 2; call < 8 && L.U != 0u; ++call) {
     const uint4 w = ph_call(K, a, b, t, half + 2u * call);
     ++calls;
-    apply_call(L, w, &tab.tm[4 * call][0]);
+    apply_call<COLL>(L, w, tab, call);
   }
 }
 
@@ -348,13 +394,21 @@ __global__ void __launch_bounds__(kTile, 3) lattice_half_kernel(const LatJob* __
     const PhKey K = ph_key(J.key0, J.key1);
     double acc[3] = {0.0, 0.0, 0.0};
     uint32_t qn = 0;  // warp-uniform queue length
+    const bool coll = sh.tab.collapsed != 0u;
 #pragma unroll
     for (int k = 0; k < WPT; ++k) {
       const uint32_t w = tl.w0 + threadIdx.x + k * kTile;
       const bool act = w < J.nwords;
-      LaneWord Lw = classify(S[k], V[k], H[k], F[k], sh.tab);
-      if (!act) Lw.U = 0u;
-      decide_head(Lw, sh.tab, K, w, J.b, t, half, calls);
+      LaneWord Lw;
+      if (coll) {
+        Lw = classify<true>(S[k], V[k], H[k], F[k], sh.tab);
+        if (!act) Lw.U = 0u;
+        decide_head<true>(Lw, sh.tab, K, w, J.b, t, half, calls);
+      } else {
+        Lw = classify<false>(S[k], V[k], H[k], F[k], sh.tab);
+        if (!act) Lw.U = 0u;
+        decide_head<false>(Lw, sh.tab, K, w, J.b, t, half, calls);
+      }
       const bool pend = act && Lw.U != 0u;
       const uint32_t pm = __ballot_sync(0xffffffffu, pend);
       if (pend) {
@@ -387,7 +441,10 @@ __global__ void __launch_bounds__(kTile, 3) lattice_half_kernel(const LatJob* __
         Lw.X = e.X;
         Lw.U = e.U;
         Lw.res = e.res;
-        decide_tail(Lw, sh.tab, K, e.w, J.b, t, half, calls);
+        if (coll)
+          decide_tail<true>(Lw, sh.tab, K, e.w, J.b, t, half, calls);
+        else
+          decide_tail<false>(Lw, sh.tab, K, e.w, J.b, t, half, calls);
         store_word<ENC>(J, dstbuf, e.w, Lw.res);
       }
     }

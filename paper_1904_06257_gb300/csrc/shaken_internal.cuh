@@ -112,10 +112,18 @@ __device__ __forceinline__ double field_h(double Jc, int s, double q, int sigma,
 //   tm[j][c]  bit k set iff T(c, beta_k) < 2^32, T(c, beta_k) > 0 and bit (31-j)
 //             of T(c, beta_k) is 1 (planes most significant first);
 //   satp[c]   lanes with T == 2^32 (always +1), satm[c] lanes with T == 0.
+// When the thresholds of every lane depend on n + s only (classes (0,1) and
+// (1,0) equal, (1,1) and (2,0) equal -- the case J = q), tmc[j][c] holds the
+// planes by c = n + s in 0..3 and `collapsed` is set; `anysat` marks tables
+// with at least one saturated lane.
 struct __align__(16) LatTable {
   uint32_t tm[32][8];
+  uint32_t tmc[32][4];
   uint32_t satp[8];
   uint32_t satm[8];
+  uint32_t collapsed;
+  uint32_t anysat;
+  uint32_t pad[2];
 };
 
 // ---------------------------------------------------------------- descriptors
