@@ -281,6 +281,9 @@ def run_ours(args, rank, world, local_rank):
     plain_rate = 2.0 * Lp * Lp * 64 / (pe0.elapsed_time(pe1) * 1e-3)
     S.shaken_free(cp)
 
+    # ---- arbitrary sparse graphs: n = 1e6, 256 replicas, lambda_x ~ N(0, 0.1^2), q = 1
+    graphs = {} if args.skip_graphs else run_graphs(S, stream, torch, args)
+
     # ---- roofline of the dominant kernel (multispin half step)
     rb_calls, _ = S.shaken_microbench(0)
     rb_lop3, _ = S.shaken_microbench(1)
@@ -325,6 +328,7 @@ def run_ours(args, rank, world, local_rank):
                        "parallelism": f"replicas/groups sharded over {world} GPU(s)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks,
+            "graphs": graphs,
             "batched_vs_plain": {
                 "batched_updates_per_s": value / world,
                 "batched_graph_replay_updates_per_s": graph_rate,
@@ -335,6 +339,74 @@ def run_ours(args, rank, world, local_rank):
         S.shaken_batch_remove(batch, c)
         S.shaken_free(c)
     S.shaken_batch_free(batch)
+    return out
+
+
+# ------------------------------------------------------------------------ graphs
+GRAPH_N, GRAPH_R = 1_000_000, 256
+
+
+def _timed(torch, stream, fn):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+    fn()
+    with torch.cuda.stream(stream):
+        e1.record(stream)
+    stream.synchronize()
+    return e0.elapsed_time(e1) * 1e-3
+
+
+def run_graphs(S, stream, torch, args):
+    """Sparse-graph workloads: Erdos-Renyi (mean degree 8) with +-1 couplings -- the
+    full linear anneal beta 0.1 -> 3.0 over 5000 steps, best energy and cut -- and
+    throughput of the real-coupling path and of a random 3-regular graph."""
+    out = {}
+    n, R = GRAPH_N, GRAPH_R
+    lam = W.fields_normal(n, 0.1, W.BASE_SEED + 3)
+    u, v = W.erdos_renyi(n, 8.0, W.BASE_SEED + 1)
+    Jpm = W.couplings_pm1(u.size, W.BASE_SEED + 2)
+    steps = args.graph_anneal_steps
+    sched = W.linear_schedule(0.1, 3.0, steps)
+    p = S.Problem(S.GRAPH, S.MULTISPIN, R, 0.1, 1.0, n=n, u=u, v=v, J_edge=Jpm,
+                  J_is_integer=True, lambda_=lam)
+    c = S.shaken_init(p, W.BASE_SEED + 11, stream)
+    S.shaken_step(c, 2)
+    S.shaken_sync(c)
+    dt = _timed(torch, stream, lambda: S.shaken_anneal(c, sched))
+    obs = S.shaken_observables(c, R)
+    S.shaken_free(c)
+    out["er_pm1_anneal"] = {
+        "n": n, "m": int(u.size), "replicas": R, "steps": steps,
+        "updates_per_s": 2.0 * n * R * steps / dt, "seconds": dt,
+        "best_energy_min": float(obs["best_energy"].min()),
+        "best_energy_mean": float(obs["best_energy"].mean()),
+        "final_energy_mean": float(obs["energy"].mean()),
+        "cut_weight_best_replica": float(obs["cut_weight"][int(np.argmin(obs["energy"]))]),
+        "cut_edges_best_replica": int(obs["cut_edges"][int(np.argmin(obs["energy"]))]),
+        "note": "anneal with per-step best-energy tracking (observables kernel every step)"}
+    # real couplings N(0,1), fixed beta, throughput without tracking
+    Jr = W.couplings_normal(u.size, W.BASE_SEED + 4)
+    p = S.Problem(S.GRAPH, S.MULTISPIN, R, 1.0, 1.0, n=n, u=u, v=v, J_edge=Jr,
+                  J_is_integer=False, lambda_=lam)
+    c = S.shaken_init(p, W.BASE_SEED + 12, stream)
+    S.shaken_step(c, 2)
+    S.shaken_sync(c)
+    k = 50
+    dt = _timed(torch, stream, lambda: S.shaken_step(c, k))
+    S.shaken_free(c)
+    out["er_real_step"] = {"updates_per_s": 2.0 * n * R * k / dt, "steps": k}
+    # +-1 on a random 3-regular graph, fixed beta
+    u3, v3 = W.random_regular3(n, W.BASE_SEED + 5)
+    J3 = W.couplings_pm1(u3.size, W.BASE_SEED + 6)
+    p = S.Problem(S.GRAPH, S.MULTISPIN, R, 1.0, 1.0, n=n, u=u3, v=v3, J_edge=J3,
+                  J_is_integer=True, lambda_=lam)
+    c = S.shaken_init(p, W.BASE_SEED + 13, stream)
+    S.shaken_step(c, 2)
+    S.shaken_sync(c)
+    dt = _timed(torch, stream, lambda: S.shaken_step(c, k))
+    S.shaken_free(c)
+    out["reg3_pm1_step"] = {"updates_per_s": 2.0 * n * R * k / dt, "steps": k}
     return out
 
 
@@ -376,6 +448,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--only-batched", action="store_true",
                     help="time the batched workload only (profiling runs)")
+    ap.add_argument("--skip-graphs", action="store_true", help="skip the sparse-graph section")
+    ap.add_argument("--graph-anneal-steps", type=int, default=5000)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

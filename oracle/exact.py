@@ -210,3 +210,55 @@ def triangular_gibbs_lambda0(S, L, J, q, beta):
         logw += K1 * S[:, x] * (S[:, dn] + S[:, lf]) + K2 * S[:, dn] * S[:, lf]
     w = np.exp(logw - logw.max())
     return w / w.sum()
+
+
+# ----------------------------------------------------------------------------- large lattices
+def onsager_energy_per_site(beta: float, J: float = 1.0) -> float:
+    """Energy per site of the square-lattice Ising model (Onsager):
+    u = -J coth(2K) [1 + (2/pi) (2 tanh^2(2K) - 1) K(k)],  k = 2 sinh(2K) / cosh^2(2K),
+    K the complete elliptic integral of the first kind (argument m = k^2)."""
+    from scipy.special import ellipk
+    K = beta * J
+    k = 2.0 * np.sinh(2 * K) / np.cosh(2 * K) ** 2
+    return -J / np.tanh(2 * K) * (1.0 + (2.0 / np.pi) * (2.0 * np.tanh(2 * K) ** 2 - 1.0)
+                                  * ellipk(k * k))
+
+
+def triangular_heat_bath(L: int, J: float, q: float, beta: float, sweeps: int, burn: int,
+                         seed: int, start_plus: bool = False):
+    """Single-spin heat bath on the anisotropic triangular Ising model that the
+    lambda = 0 shaken measure equals (couplings K1 on (x, x_down) and (x, x_left),
+    K2 on (x_down, x_left); see ``triangular_gibbs_lambda0``).  Sites are updated
+    by colour class c = (i + 2 j) mod 3 (a proper colouring of that lattice when
+    3 | L), so each class update is an exact Gibbs step.  Returns per-sweep
+    samples of the square-lattice energy per site -(J/N) sum_x s_x (s_down + s_left)
+    and of the magnetisation per site."""
+    assert L % 3 == 0
+    K, Q = beta * J, beta * q
+    K1 = 0.25 * np.log(np.cosh(2 * K + Q) / np.cosh(2 * K - Q))
+    K2 = 0.25 * np.log(np.cosh(2 * K + Q) * np.cosh(2 * K - Q) / np.cosh(Q) ** 2)
+    g = np.random.default_rng(seed)
+    s = np.ones((L, L)) if start_plus else np.where(g.random((L, L)) < 0.5, -1.0, 1.0)
+    i, j = np.meshgrid(np.arange(L), np.arange(L), indexing="ij")
+    colour = (i + 2 * j) % 3
+    masks = [colour == c for c in range(3)]
+    E, M = [], []
+    for sw in range(burn + sweeps):
+        for c in range(3):
+            # local field: K1 bonds to the four square neighbours, K2 bonds along (1,-1)
+            f = K1 * (np.roll(s, 1, 0) + np.roll(s, -1, 0) + np.roll(s, 1, 1) + np.roll(s, -1, 1)) \
+                + K2 * (np.roll(np.roll(s, 1, 0), -1, 1) + np.roll(np.roll(s, -1, 0), 1, 1))
+            p = 1.0 / (1.0 + np.exp(-2.0 * f))
+            new = np.where(g.random((L, L)) < p, 1.0, -1.0)
+            s = np.where(masks[c], new, s)
+        if sw >= burn:
+            E.append(-J * np.mean(s * (np.roll(s, 1, 0) + np.roll(s, 1, 1))))
+            M.append(np.mean(s))
+    return np.array(E), np.array(M)
+
+
+def batch_means_se(x: np.ndarray, nb: int = 20) -> float:
+    """Standard error of the mean of a correlated series by batch means."""
+    x = np.asarray(x)
+    b = x[: len(x) // nb * nb].reshape(nb, -1).mean(axis=1)
+    return float(b.std(ddof=1) / np.sqrt(nb))

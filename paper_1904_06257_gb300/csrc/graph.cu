@@ -16,49 +16,122 @@
 //
 // Decision, integer couplings (exact): tau_k = +1 iff u_k < T(h_k, beta_k)
 // with T = floor(2^32 / (1 + e^{-2 beta h})) in fp64 and h = (s + q sigma) +
-// lambda_x.  The fp32 probability p~ decides directly whenever u_k / 2^32 lies
-// outside p~ +- eps, eps = 2^-20 (2 + beta B) + 2^-23 (B = |s| + |q| + |lambda| + 1)
-// bounds |p~ - p| (fp32 rounding of h, beta, the exp argument, __expf and the
-// reciprocal) with a factor >= 4 to spare; otherwise T is computed in fp64.
-// Real couplings (fp32 sums): tau_k = +1 iff u_k / 2^32 < p~ (statistical parity).
+// lambda_x.  An fp32 evaluation of u (1 + e^{-2 beta h}) / 2^32 decides directly
+// when it is farther than its error bound from 1 (see decide_int); otherwise T is
+// computed in fp64.
+// Real couplings (fp32 sums): tau_k = +1 iff u_k (1 + e~) / 2^32 < 1 (statistical parity).
 #include <cstdint>
 
 #include "shaken_internal.cuh"
 
 namespace shk {
 
-__device__ __forceinline__ float prob_f32(float h, float beta) {
-  const float e = __expf(-2.0f * beta * h);
-  return __frcp_rn(1.0f + e);
+// 2^x (PTX ex2.approx: relative error below 2^-22 over the range used here).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
-// Exact decision for integer couplings (see header).
+// Exact decision for integer couplings (see the header): +1 iff u < T(h, beta).
+// With e~ = 2^(kb h~), kb = -2 beta log2(e), the condition u < 2^32 / (1 + e) is
+// tested as t1 = (u + 1) 2^-32 (1 + e~) < 1 - eps (certainly +1) or
+// t0 = u 2^-32 (1 + e~) > 1 + eps (certainly -1); eps = 2^-18 + 2^-18 beta B with
+// B >= |s| + |q| + |lambda| + 1 is at least three times the fp32 error of t
+// (rounding of h~, kb h~, ex2, the two products); in between, T is computed in fp64.
 __device__ __forceinline__ bool decide_int(uint32_t u, int s, int sigma, float qf, double q,
-                                           float lam, float betaf, double beta, bool exact_always) {
+                                           float lam, float kb, float eps, double beta,
+                                           bool exact_always) {
   const float hf = __fadd_rn(__fadd_rn((float)s, sigma > 0 ? qf : -qf), lam);
-  const float pf = prob_f32(hf, betaf);
-  const float B = fabsf((float)s) + fabsf(qf) + fabsf(lam) + 1.0f;
-  const float eps = 9.5367431640625e-07f * (2.0f + betaf * B) + 1.1920928955078125e-07f;
+  const float onep = 1.0f + ex2_approx(kb * hf);
   const float uf = __uint2float_rn(u) * 2.3283064365386963e-10f;
   if (!exact_always) {
-    if (uf + eps < pf) return true;
-    if (uf - eps > pf) return false;
+    if ((uf + 2.3283064365386963e-10f) * onep < 1.0f - eps) return true;
+    if (uf * onep > 1.0f + eps) return false;
   }
   const double h = field_h(1.0, s, q, sigma, (double)lam);
   return (unsigned long long)u < threshold_T(h, beta);
 }
 
+struct GraphShared {
+  float kb[32];   // -2 beta_k log2(e) per lane (anneal: the step's beta on every lane)
+  float epc[32];  // 2^-18 beta_k per lane
+  double beta[32];
+  float acc[kTile / 32][32][32];  // [warp][replica lane k][thread lane]: tracking sums
+  float red[kTile / 32][32];
+};
+
+// One thread owns one (vertex, group) word.  Each block walks a contiguous range
+// of tiles (one job per tile).  With tracking on, half 0 also accumulates per
+// replica sum_x sigma_x (s_x + 2 lambda_x), i.e. -H(sigma_t) (Eq. (ham1)), reduced
+// when the block leaves a job.
 template <bool INTEGER>
 __global__ void __launch_bounds__(kTile) graph_half_kernel(const GraphJob* __restrict__ jobs,
                                                            const Tile* __restrict__ tiles,
                                                            int n_tiles, uint32_t half,
                                                            int exact_always) {
-  for (int ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
+  __shared__ GraphShared sh;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tb = (int)(((long long)blockIdx.x * n_tiles) / gridDim.x);
+  const int te = (int)(((long long)(blockIdx.x + 1) * n_tiles) / gridDim.x);
+  int cur_job = -1;
+  bool fuse = false, skip = false;
+  uint32_t t = 0;
+  double* fuse_dst = nullptr;
+  float(*acc)[32] = sh.acc[warp];  // acc[k][lane]: this thread's sum for replica lane k
+#pragma unroll
+  for (int k = 0; k < 32; ++k) acc[k][lane] = 0.0f;
+
+  auto flush = [&]() {
+    // block totals per replica lane -> step sums of the job's 32 replicas
+    __syncthreads();
+    {
+      const int k = threadIdx.x & 31, w = threadIdx.x >> 5;  // row (w, k) of the accumulators
+      float v = 0.0f;
+#pragma unroll 8
+      for (int l = 0; l < 32; ++l) v += sh.acc[w][k][(l + k) & 31];
+      sh.red[w][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      float tot = 0.0f;
+#pragma unroll
+      for (int w = 0; w < kTile / 32; ++w) tot += sh.red[w][threadIdx.x];
+      if (tot != 0.0f) atomicAdd(fuse_dst + (size_t)threadIdx.x * kNumSums + kSumE, (double)tot);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[k][lane] = 0.0f;
+  };
+
+  for (int ti = tb; ti < te; ++ti) {
     const Tile tl = tiles[ti];
     const GraphJob& J = jobs[tl.job];
-    const CtxDev* cd = J.cd;
-    const uint32_t t = cd->step;
-    if (t >= cd->t_end) continue;
+    if ((int)tl.job != cur_job) {
+      if (fuse) flush();
+      __syncthreads();  // shared per-job constants are about to change
+      const CtxDev* cd = J.cd;
+      t = cd->step;
+      skip = t >= cd->t_end;
+      fuse = !skip && half == 0u && cd->tracking && !cd->record;
+      fuse_dst = J.sums;
+      if (threadIdx.x < 32) {
+        double beta;
+        if (J.beta_sched != nullptr && cd->anneal_len != 0u) {
+          uint32_t k = t - cd->anneal_t0;
+          if (k >= cd->anneal_len) k = cd->anneal_len - 1u;
+          beta = J.beta_sched[k];
+        } else {
+          beta = J.beta_lane[threadIdx.x];
+        }
+        sh.beta[threadIdx.x] = beta;
+        sh.kb[threadIdx.x] = (float)(-2.0 * beta * 1.4426950408889634);
+        sh.epc[threadIdx.x] = (float)beta * 3.814697265625e-06f;
+      }
+      __syncthreads();
+      cur_job = (int)tl.job;
+    }
+    if (skip) continue;
     const uint32_t x = tl.w0 + threadIdx.x;
     if (x >= J.n) continue;
     const uint32_t* src = half == 0u ? J.A : J.B;
@@ -72,13 +145,6 @@ __global__ void __launch_bounds__(kTile) graph_half_kernel(const GraphJob* __res
     const uint32_t F = J.frozen != nullptr ? J.frozen[x] : 0u;
     const float lam = J.lambda != nullptr ? J.lambda[x] : J.lambda_c;
     const float qf = (float)J.q;
-    bool anneal = J.beta_sched != nullptr && cd->anneal_len != 0u;
-    double beta_a = 0.0;
-    if (anneal) {
-      uint32_t k = t - cd->anneal_t0;
-      if (k >= cd->anneal_len) k = cd->anneal_len - 1u;
-      beta_a = J.beta_sched[k];
-    }
     const PhKey K = ph_key(J.key0, J.key1);
     uint32_t res = F;
     if (INTEGER) {
@@ -96,6 +162,7 @@ __global__ void __launch_bounds__(kTile) graph_half_kernel(const GraphJob* __res
           }
         }
       }
+      const float B = (float)d + fabsf(qf) + fabsf(lam) + 1.0f;
       uint4 w = make_uint4(0, 0, 0, 0);
 #pragma unroll
       for (int k = 0; k < 32; ++k) {
@@ -115,10 +182,14 @@ __global__ void __launch_bounds__(kTile) graph_half_kernel(const GraphJob* __res
         }
         const int s = 2 * cnt - d;
         const int sigma = ((S >> k) & 1u) ? 1 : -1;
-        const double beta = anneal ? beta_a : J.beta_lane[k];
-        const bool plus = decide_int(u, s, sigma, qf, J.q, lam, (float)beta, beta,
+        const float eps = 3.814697265625e-06f + sh.epc[k] * B;
+        const bool plus = decide_int(u, s, sigma, qf, J.q, lam, sh.kb[k], eps, sh.beta[k],
                                      exact_always != 0);
         res |= (uint32_t)plus << k;
+        if (fuse) {
+          const float a = (float)s + 2.0f * lam;
+          acc[k][lane] += sigma > 0 ? a : -a;
+        }
       }
     } else {
       float h[32];
@@ -136,15 +207,20 @@ __global__ void __launch_bounds__(kTile) graph_half_kernel(const GraphJob* __res
       for (int k = 0; k < 32; ++k) {
         if ((k & 3) == 0) w = ph_call(K, x, J.b, t, half + 2u * (uint32_t)(k >> 2));
         const uint32_t u = (k & 3) == 0 ? w.x : (k & 3) == 1 ? w.y : (k & 3) == 2 ? w.z : w.w;
-        const float hk = __fadd_rn(__fadd_rn(h[k], ((S >> k) & 1u) ? qf : -qf), lam);
-        const double beta = anneal ? beta_a : J.beta_lane[k];
-        const float pf = prob_f32(hk, (float)beta);
+        const bool up = (S >> k) & 1u;
+        const float hk = __fadd_rn(__fadd_rn(h[k], up ? qf : -qf), lam);
+        const float onep = 1.0f + ex2_approx(sh.kb[k] * hk);
         const float uf = __uint2float_rn(u) * 2.3283064365386963e-10f;
-        res |= (uint32_t)(uf < pf) << k;
+        res |= (uint32_t)(uf * onep < 1.0f) << k;
+        if (fuse) {
+          const float a = h[k] + 2.0f * lam;
+          acc[k][lane] += up ? a : -a;
+        }
       }
     }
     dst[x] = res;
   }
+  if (fuse) flush();
 }
 
 // Fields h_x (float) of the next half step as the update kernel computes them.
@@ -300,8 +376,19 @@ static int grid_for(int n_tiles, int per_sm) {
 
 cudaError_t launch_graph_half(bool integer, const GraphJob* jobs, const Tile* tiles, int n_tiles,
                               uint32_t half, int exact_always, int blocks_per_sm, cudaStream_t st) {
+  (void)blocks_per_sm;
   if (n_tiles <= 0) return cudaSuccess;
-  const int grid = grid_for(n_tiles, blocks_per_sm);
+  static int occ[2] = {0, 0};
+  const int i = integer ? 1 : 0;
+  if (occ[i] == 0) {
+    int o = 1;
+    if (integer)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, graph_half_kernel<true>, kTile, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, graph_half_kernel<false>, kTile, 0);
+    occ[i] = o > 0 ? o : 1;
+  }
+  const int grid = grid_for(n_tiles, occ[i]);
   if (integer)
     graph_half_kernel<true><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, half, exact_always);
   else

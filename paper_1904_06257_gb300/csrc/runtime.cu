@@ -363,8 +363,11 @@ static shaken_status plan_step_launch(Plan& P, cudaStream_t st, uint64_t* nl,
   bool obs_needed = false;
   int ex = 0;
   for (shaken_ctx* c : P.members) {
-    if (c->hcd.tracking && (c->kind == SHAKEN_GRAPH || c->enc == SHAKEN_MULTISPIN))
+    // multispin lattices track with the observables kernel; graphs fuse tracking
+    // into half 0 unless a per-step series (which also needs M) is recorded
+    if (c->hcd.tracking && c->kind == SHAKEN_LATTICE && c->enc == SHAKEN_MULTISPIN)
       obs_needed = true;
+    if (c->hcd.tracking && c->kind == SHAKEN_GRAPH && c->hcd.record) obs_needed = true;
     ex |= c->exact_always;
   }
   if (obs_needed) {

@@ -47,6 +47,17 @@ def frozen_frame(L: int) -> np.ndarray:
     return f.reshape(-1)
 
 
+def _unique_sorted(keys: np.ndarray) -> np.ndarray:
+    """Sorted distinct values (sort + neighbour comparison)."""
+    k = np.sort(keys, kind="stable")
+    if k.size == 0:
+        return k
+    keep = np.empty(k.size, dtype=bool)
+    keep[0] = True
+    np.not_equal(k[1:], k[:-1], out=keep[1:])
+    return k[keep]
+
+
 def random_regular3(n: int, seed: int, max_tries: int = 1000):
     """Random simple 3-regular graph on n (even) vertices: configuration model,
     rejecting pairings with loops or multi-edges."""
@@ -61,7 +72,7 @@ def random_regular3(n: int, seed: int, max_tries: int = 1000):
             continue
         a, b = np.minimum(u, v), np.maximum(u, v)
         key = a * n + b
-        if np.unique(key).size != key.size:
+        if _unique_sorted(key).size != key.size:
             continue
         return a.astype(np.int32), b.astype(np.int32)
     # large n: repair by re-pairing only the bad stubs (rare) -- keeps it simple and exact
@@ -82,7 +93,7 @@ def erdos_renyi(n: int, mean_degree: float, seed: int):
         v = g.integers(0, n, size=u.size, dtype=np.int64)
         ok = u != v
         a, b = np.minimum(u[ok], v[ok]), np.maximum(u[ok], v[ok])
-        keys = np.unique(np.concatenate([keys, a * n + b]))
+        keys = _unique_sorted(np.concatenate([keys, a * n + b]))
     keys = g.permutation(keys)[:m]
     keys.sort()
     return (keys // n).astype(np.int32), (keys % n).astype(np.int32)

@@ -150,3 +150,27 @@ def test_real_graph_statistics_match_oracle(S):
         ga, oa = g.mean(axis=0), o.mean(axis=0)
         se = np.sqrt(ga.var(ddof=1) / ga.size + oa.var(ddof=1) / oa.size)
         assert abs(ga.mean() - oa.mean()) < 4 * se + 1e-12
+
+
+def test_fused_tracking_best_energy(S):
+    # the best energy tracked inside half 0 equals the minimum over steps of the
+    # oracle's H(sigma_t) along the same (bit-exact) trajectory
+    n, R = 500, 32
+    u, v, J, lam = er_instance(n, 6.0, 91)
+    sched = W.linear_schedule(0.2, 2.5, 15)
+    seed = 4711
+    ctx = S.shaken_init(graph_problem(S, n, u, v, J, R, 0.5, q=1.0, lam=lam), seed)
+    S.shaken_anneal(ctx, sched)
+    obs = S.shaken_observables(ctx, R)
+    S.shaken_free(ctx)
+    tail, head = core.orient(u, v, 0)
+    Jd, ld = J.astype(np.float64), lam.astype(np.float64)
+    cur = core.graph_init(n, R, seed, 0)
+    best = np.full(R, np.inf)
+    for k, b in enumerate(sched):
+        H = np.array([o["H"] for o in core.graph_observables(cur, cur, tail, head, Jd, ld, 1.0)])
+        best = np.minimum(best, H)
+        cur, _ = core.graph_run(cur, tail, head, Jd, True, ld, 1.0, b, seed, k, 1)
+    H = np.array([o["H"] for o in core.graph_observables(cur, cur, tail, head, Jd, ld, 1.0)])
+    best = np.minimum(best, H)
+    assert np.allclose(obs["best_energy"], best, rtol=1e-6, atol=1e-4)

@@ -1,0 +1,53 @@
+"""Stationary observables of the CUDA lattice chain against independent
+references (lambda = 0, J = 1):
+* at finite q the shaken measure is exactly the Gibbs measure of an anisotropic
+  triangular Ising model; a plain single-spin heat bath on that model
+  (oracle/exact.py, numpy) must give the same energy and |m| within 4 standard
+  errors;
+* as q grows the energy approaches Onsager's closed form (Thm 3.1: the measure
+  tends to Gibbs when e^{-2 beta q} is small), monotonically in q."""
+import numpy as np
+import pytest
+
+from oracle import exact
+from tests.gpu_util import lattice_problem, lib, require_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    require_cuda()
+    return lib()
+
+
+def gpu_series(S, L, q, beta, burn, steps, seed, R=32, init=0):
+    ctx = S.shaken_init(lattice_problem(S, S.MULTISPIN, L, R, beta, 1.0, q, 0.0, init=init), seed)
+    S.shaken_step(ctx, burn)
+    mag, en = S.shaken_step_record(ctx, steps, R)
+    S.shaken_free(ctx)
+    return en / (L * L), mag
+
+
+@pytest.mark.parametrize("q,beta", [(1.0, 0.40), (1.0, 0.55), (0.5, 0.7), (2.0, 0.45)])
+def test_energy_matches_triangular_heat_bath(S, q, beta):
+    L = 96
+    e_gpu, m_gpu = gpu_series(S, L, q, beta, burn=400, steps=1600, seed=11)
+    # replicas are independent: time-average per replica, then mean and SE over replicas
+    per_rep = e_gpu.mean(axis=0)
+    g_mean, g_se = per_rep.mean(), per_rep.std(ddof=1) / np.sqrt(per_rep.size)
+    e_ref, m_ref = exact.triangular_heat_bath(L, 1.0, q, beta, sweeps=3000, burn=300, seed=5)
+    r_mean, r_se = e_ref.mean(), exact.batch_means_se(e_ref)
+    assert abs(g_mean - r_mean) < 4 * np.hypot(g_se, r_se), (g_mean, r_mean, g_se, r_se)
+
+
+def test_energy_approaches_onsager_as_q_grows(S):
+    L, beta = 128, 0.30
+    u = exact.onsager_energy_per_site(beta)
+    dev = []
+    for q in (0.5, 1.0, 2.0, 4.0, 8.0):
+        e, _ = gpu_series(S, L, q, beta, burn=1500, steps=500, seed=21)
+        dev.append(abs(e.mean() - u))
+    # e^{-2 beta q} = 0.74 ... 0.008: the deviation from Onsager shrinks with q
+    assert all(a > b for a, b in zip(dev, dev[1:])), dev
+    assert dev[-1] < 0.1 * dev[0], dev
