@@ -169,13 +169,11 @@ template <bool COLL>
 __device__ __forceinline__ void decide_head(LaneWord& L, const LatTable& tab, const PhKey& K,
                                             uint32_t a, uint32_t b, uint32_t t, uint32_t half,
                                             uint32_t& calls) {
-  if (L.U != 0u) {
-    const uint4 w0 = ph_call(K, a, b, t, half);
-    const uint4 w1 = ph_call(K, a, b, t, half + 2u);
-    calls += 2;
-    apply_call<COLL>(L, w0, tab, 0u);
-    apply_call<COLL>(L, w1, tab, 1u);
-  }
+  const uint4 w0 = ph_call(K, a, b, t, half);
+  const uint4 w1 = ph_call(K, a, b, t, half + 2u);
+  calls += 2;
+  apply_call<COLL>(L, w0, tab, 0u);
+  apply_call<COLL>(L, w1, tab, 1u);
 }
 
 // Calls 2..7 while some lane is undecided.
@@ -322,6 +320,65 @@ __device__ __forceinline__ void store_word(const LatJob& J, void* dstbuf, uint32
   }
 }
 
+// Decisions of one tile: planes 31..24 of each of the thread's WPT lane words,
+// words with undecided lanes parked in the warp's queue, then the queue
+// finished 32 words at a time.  FULL: every word of the tile exists.
+template <int ENC, int WPT, bool COLL, bool FULL>
+__device__ __forceinline__ void tile_decide(const LatJob& J, const TileShared& sh,
+                                            Pending* __restrict__ q, const PhKey& K, uint32_t w0,
+                                            uint32_t t, uint32_t half, const uint32_t (&S)[WPT],
+                                            const uint32_t (&V)[WPT], const uint32_t (&H)[WPT],
+                                            const uint32_t (&F)[WPT], void* dstbuf,
+                                            double (&acc)[3], uint32_t& calls) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  uint32_t qn = 0;  // warp-uniform queue length
+#pragma unroll
+  for (int k = 0; k < WPT; ++k) {
+    const uint32_t w = w0 + threadIdx.x + k * kTile;
+    const bool act = FULL || w < J.nwords;
+    LaneWord Lw = classify<COLL>(S[k], V[k], H[k], F[k], sh.tab);
+    if (!FULL && !act) Lw.U = 0u;
+    decide_head<COLL>(Lw, sh.tab, K, w, J.b, t, half, calls);
+    const bool pend = act && Lw.U != 0u;
+    const uint32_t pm = __ballot_sync(0xffffffffu, pend);
+    if (pend) {
+      Pending& e = q[qn + __popc(pm & lt_mask)];
+      e.w = w;
+      e.S = Lw.S;
+      e.V = Lw.V;
+      e.X = Lw.X;
+      e.U = Lw.U;
+      e.res = Lw.res;
+    } else if (act) {
+      store_word<ENC>(J, dstbuf, w, Lw.res);
+    }
+    qn += __popc(pm);
+    if (sh.fuse && act) {
+      // sums of sigma_t over the lane word: M, E (in-edges down and left), cut
+      const int dv = __popc(S[k] ^ V[k]), dh = __popc(S[k] ^ H[k]);
+      acc[0] += (double)(2 * __popc(S[k]) - 32);
+      acc[1] += (double)(64 - 2 * dv - 2 * dh);
+      acc[2] += (double)(dv + dh);
+    }
+  }
+  __syncwarp();
+  for (uint32_t base = 0; base < qn; base += 32u) {
+    if (base + lane < qn) {
+      const Pending e = q[base + lane];
+      LaneWord Lw;
+      Lw.S = e.S;
+      Lw.V = e.V;
+      Lw.X = e.X;
+      Lw.U = e.U;
+      Lw.res = e.res;
+      decide_tail<COLL>(Lw, sh.tab, K, e.w, J.b, t, half, calls);
+      store_word<ENC>(J, dstbuf, e.w, Lw.res);
+    }
+  }
+  __syncwarp();
+}
+
 // Each block walks a contiguous range of tiles (kLatTile lane words each; a
 // tile never spans two jobs).  Per tile every thread loads the words of its
 // kWordsPerThread lane words (all loads in flight together) and runs planes
@@ -393,62 +450,22 @@ __global__ void __launch_bounds__(kTile, 3) lattice_half_kernel(const LatJob* __
     }
     const PhKey K = ph_key(J.key0, J.key1);
     double acc[3] = {0.0, 0.0, 0.0};
-    uint32_t qn = 0;  // warp-uniform queue length
-    const bool coll = sh.tab.collapsed != 0u;
-#pragma unroll
-    for (int k = 0; k < WPT; ++k) {
-      const uint32_t w = tl.w0 + threadIdx.x + k * kTile;
-      const bool act = w < J.nwords;
-      LaneWord Lw;
-      if (coll) {
-        Lw = classify<true>(S[k], V[k], H[k], F[k], sh.tab);
-        if (!act) Lw.U = 0u;
-        decide_head<true>(Lw, sh.tab, K, w, J.b, t, half, calls);
-      } else {
-        Lw = classify<false>(S[k], V[k], H[k], F[k], sh.tab);
-        if (!act) Lw.U = 0u;
-        decide_head<false>(Lw, sh.tab, K, w, J.b, t, half, calls);
-      }
-      const bool pend = act && Lw.U != 0u;
-      const uint32_t pm = __ballot_sync(0xffffffffu, pend);
-      if (pend) {
-        Pending& e = queue[warp][qn + __popc(pm & lt_mask)];
-        e.w = w;
-        e.S = Lw.S;
-        e.V = Lw.V;
-        e.X = Lw.X;
-        e.U = Lw.U;
-        e.res = Lw.res;
-      } else if (act) {
-        store_word<ENC>(J, dstbuf, w, Lw.res);
-      }
-      qn += __popc(pm);
-      if (sh.fuse && act) {
-        // sums of sigma_t over the lane word: M, E (in-edges down and left), cut
-        const int dv = __popc(S[k] ^ V[k]), dh = __popc(S[k] ^ H[k]);
-        acc[0] += (double)(2 * __popc(S[k]) - 32);
-        acc[1] += (double)(64 - 2 * dv - 2 * dh);
-        acc[2] += (double)(dv + dh);
-      }
+    const bool full_tile = tl.w0 + kTile * WPT <= J.nwords;
+    if (sh.tab.collapsed) {
+      if (full_tile)
+        tile_decide<ENC, WPT, true, true>(J, sh, queue[warp], K, tl.w0, t, half, S, V, H, F,
+                                          dstbuf, acc, calls);
+      else
+        tile_decide<ENC, WPT, true, false>(J, sh, queue[warp], K, tl.w0, t, half, S, V, H, F,
+                                           dstbuf, acc, calls);
+    } else {
+      if (full_tile)
+        tile_decide<ENC, WPT, false, true>(J, sh, queue[warp], K, tl.w0, t, half, S, V, H, F,
+                                           dstbuf, acc, calls);
+      else
+        tile_decide<ENC, WPT, false, false>(J, sh, queue[warp], K, tl.w0, t, half, S, V, H, F,
+                                            dstbuf, acc, calls);
     }
-    __syncwarp();
-    for (uint32_t base = 0; base < qn; base += 32u) {
-      if (base + lane < qn) {
-        const Pending e = queue[warp][base + lane];
-        LaneWord Lw;
-        Lw.S = e.S;
-        Lw.V = e.V;
-        Lw.X = e.X;
-        Lw.U = e.U;
-        Lw.res = e.res;
-        if (coll)
-          decide_tail<true>(Lw, sh.tab, K, e.w, J.b, t, half, calls);
-        else
-          decide_tail<false>(Lw, sh.tab, K, e.w, J.b, t, half, calls);
-        store_word<ENC>(J, dstbuf, e.w, Lw.res);
-      }
-    }
-    __syncwarp();
     if (sh.fuse) {
       double v2[2] = {acc[0], acc[1]};
       block_sum_atomic<2>(v2, J.sums + kSumM, red);
