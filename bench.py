@@ -281,6 +281,21 @@ def run_ours(args, rank, world, local_rank):
     plain_rate = 2.0 * Lp * Lp * 64 / (pe0.elapsed_time(pe1) * 1e-3)
     S.shaken_free(cp)
 
+    # ---- small lattice: L = 64 int8, one replica, beta = 0.40, 10^4 steps with m and H per step
+    Ls1 = 64
+    p1 = S.Problem(S.LATTICE, S.INT8, 1, 0.40, Q, L=Ls1, J=J, lambda_const=LAM)
+    c1 = S.shaken_init(p1, W.BASE_SEED, stream)
+    S.shaken_step_record(c1, 100, 1)
+    t0 = time.perf_counter()
+    m1, e1 = S.shaken_step_record(c1, 10000, 1)
+    dt1 = time.perf_counter() - t0
+    S.shaken_free(c1)
+    small = {"L": Ls1, "steps": 10000, "seconds": dt1,
+             "updates_per_s": 2.0 * Ls1 * Ls1 * 10000 / dt1,
+             "us_per_step": dt1 / 10000 * 1e6,
+             "m_mean": float(m1[5000:].mean()), "e_per_site_mean": float(e1[5000:].mean() / Ls1**2),
+             "what": "shaken_step_record wall time: 10^4 steps with per-step m and H to host"}
+
     # ---- arbitrary sparse graphs: n = 1e6, 256 replicas, lambda_x ~ N(0, 0.1^2), q = 1
     graphs = {} if args.skip_graphs else run_graphs(S, stream, torch, args)
 
@@ -329,6 +344,7 @@ def run_ours(args, rank, world, local_rank):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks,
             "graphs": graphs,
+            "small_lattice": small,
             "batched_vs_plain": {
                 "batched_updates_per_s": value / world,
                 "batched_graph_replay_updates_per_s": graph_rate,

@@ -630,6 +630,140 @@ __global__ void __launch_bounds__(kTile) lattice_obs_multispin_kernel(
   }
 }
 
+// --------------------------------------------------------------------------- resident runs
+// Small lattices: one block owns one job (an int8/packed replica or a multispin
+// group) for a whole run of n steps.  The state lives in shared memory as bit
+// lane words (the packed layout for INT8/PACKED, the multispin layout
+// otherwise) between a barrier per half step; the draws, thresholds and
+// decisions are the ones of lattice_half_kernel, so the trajectory is the same.
+// With tracking (INT8/PACKED only) the block also evaluates H(sigma_t) each step
+// and updates the best energy and the per-step series itself.
+template <int ENC>
+__device__ __forceinline__ uint32_t resident_load(const LatJob& J, uint32_t w) {
+  if (ENC == kEncInt8) {
+    uint32_t i, c;
+    word_rc(J, w, i, c);
+    const uint4* p = reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(J.A) +
+                                                    (size_t)i * J.L + 32u * c);
+    return bits16(p[0]) | (bits16(p[1]) << 16);
+  }
+  return static_cast<const uint32_t*>(J.A)[w];
+}
+
+template <int ENC>
+__device__ __forceinline__ void resident_store(const LatJob& J, void* buf, uint32_t w,
+                                               uint32_t bits) {
+  if (ENC == kEncInt8) {
+    uint32_t i, c;
+    word_rc(J, w, i, c);
+    uint4* p = reinterpret_cast<uint4*>(static_cast<uint8_t*>(buf) + (size_t)i * J.L + 32u * c);
+    p[0] = bytes16(bits);
+    p[1] = bytes16(bits >> 16);
+  } else {
+    static_cast<uint32_t*>(buf)[w] = bits;
+  }
+}
+
+template <int ENC>
+__global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* __restrict__ jobs,
+                                                                 uint32_t t0, uint32_t n_steps) {
+  constexpr int SENC = ENC == kEncMultispin ? kEncMultispin : kEncPacked;  // smem layout
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ LatTable stab;
+  __shared__ double red[kTile / 32][3];
+  const LatJob J = jobs[blockIdx.x];  // by value: the fields stay in registers
+  const uint32_t nw = J.nwords;
+  uint32_t* sA = smem;
+  uint32_t* sB = smem + nw;
+  const CtxDev* cd = J.cd;
+  const uint32_t anneal_t0 = cd->anneal_t0, anneal_len = cd->anneal_len;
+  const bool track = ENC != kEncMultispin && cd->tracking && J.sums != nullptr;
+  const bool record = track && cd->record;
+  for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) sA[w] = resident_load<ENC>(J, w);
+  const PhKey K = ph_key(J.key0, J.key1);
+  const LatTable* staged = nullptr;
+  uint32_t calls = 0;
+  for (uint32_t st = 0; st < n_steps; ++st) {
+    const uint32_t t = t0 + st;
+    const LatTable* src = J.table;
+    if (J.anneal_tables != nullptr && anneal_len != 0u) {
+      uint32_t k = t - anneal_t0;
+      if (k >= anneal_len) k = anneal_len - 1u;
+      src = J.anneal_tables + k;
+    }
+    if (src != staged) {
+      __syncthreads();
+      const uint32_t* g = reinterpret_cast<const uint32_t*>(src);
+      uint32_t* d = reinterpret_cast<uint32_t*>(&stab);
+      for (int k = threadIdx.x; k < (int)(sizeof(LatTable) / 4); k += blockDim.x) d[k] = g[k];
+      staged = src;
+    }
+    __syncthreads();  // sA complete (previous half step or the load), table staged
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (uint32_t half = 0; half < 2; ++half) {
+      const uint32_t* in = half == 0u ? sA : sB;
+      uint32_t* out = half == 0u ? sB : sA;
+      for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) {
+        uint32_t S, V, H;
+        load_lane_words<SENC>(J, in, w, half, S, V, H);
+        const uint32_t F = J.frozen != nullptr ? J.frozen[w] : 0u;
+        LaneWord Lw;
+        if (stab.collapsed) {
+          Lw = classify<true>(S, V, H, F, stab);
+          decide_head<true>(Lw, stab, K, w, J.b, t, half, calls);
+          decide_tail<true>(Lw, stab, K, w, J.b, t, half, calls);
+        } else {
+          Lw = classify<false>(S, V, H, F, stab);
+          decide_head<false>(Lw, stab, K, w, J.b, t, half, calls);
+          decide_tail<false>(Lw, stab, K, w, J.b, t, half, calls);
+        }
+        out[w] = Lw.res;
+        if (track && half == 0u) {
+          const int dv = __popc(S ^ V), dh = __popc(S ^ H);
+          acc[0] += (double)(2 * __popc(S) - 32);
+          acc[1] += (double)(64 - 2 * dv - 2 * dh);
+          acc[2] += (double)(dv + dh);
+        }
+      }
+      __syncthreads();
+    }
+    if (track) {
+      // block totals of sigma_t's sums -> best energy and series (Eq. (HGibbs))
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+      if ((threadIdx.x & 31) == 0)
+        for (int q = 0; q < 3; ++q) red[threadIdx.x >> 5][q] = acc[q];
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double M = 0.0, E = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+          M += red[w][0];
+          E += red[w][1];
+        }
+        const double Hs = -(cd->Jc * E) - 2.0 * cd->lamc * M;
+        const uint32_t r = J.rep0;
+        if (Hs < cd->best[r]) {
+          cd->best[r] = Hs;
+          cd->best_step[r] = (long long)t;
+        }
+        if (record && t - cd->series_t0 < cd->series_cap) {
+          const size_t k = (size_t)(t - cd->series_t0) * cd->R + r;
+          if (cd->series_m) cd->series_m[k] = M * cd->inv_n;
+          if (cd->series_H) cd->series_H[k] = Hs;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) {
+    resident_store<ENC>(J, J.A, w, sA[w]);
+    resident_store<ENC>(J, J.B, w, sB[w]);
+  }
+  (void)calls;
+}
+
 // --------------------------------------------------------------------------- launchers
 static int grid_for(int n_tiles, int per_sm) {
   int dev = 0, sms = 152;
@@ -725,4 +859,34 @@ cudaError_t launch_lattice_obs(int enc, int wpt, const LatJob* jobs, const Tile*
   return cudaGetLastError();
 }
 
+}  // namespace shk
+
+namespace shk {
+// Run n steps of every job in `jobs` (one block each) inside one launch.
+cudaError_t launch_lattice_resident(int enc, const LatJob* jobs, int n_jobs, uint32_t nwords,
+                                    uint32_t t0, uint32_t n_steps, cudaStream_t st) {
+  if (n_jobs <= 0 || n_steps == 0) return cudaSuccess;
+  const size_t bytes = (size_t)2 * nwords * sizeof(uint32_t);
+  int threads = (int)(nwords < (uint32_t)kTile ? nwords : (uint32_t)kTile);
+  threads = (threads + 31) / 32 * 32;
+  cudaError_t e = cudaSuccess;
+  if (enc == kEncInt8) {
+    e = cudaFuncSetAttribute(lattice_resident_kernel<kEncInt8>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+      lattice_resident_kernel<kEncInt8><<<n_jobs, threads, bytes, st>>>(jobs, t0, n_steps);
+  } else if (enc == kEncPacked) {
+    e = cudaFuncSetAttribute(lattice_resident_kernel<kEncPacked>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+      lattice_resident_kernel<kEncPacked><<<n_jobs, threads, bytes, st>>>(jobs, t0, n_steps);
+  } else {
+    e = cudaFuncSetAttribute(lattice_resident_kernel<kEncMultispin>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+      lattice_resident_kernel<kEncMultispin><<<n_jobs, threads, bytes, st>>>(jobs, t0, n_steps);
+  }
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
 }  // namespace shk

@@ -46,6 +46,8 @@ cudaError_t launch_graph_obs(const GraphJob*, const Tile*, int, int, int, cudaSt
 cudaError_t launch_graph_fields(const GraphJob*, const Tile*, int, uint32_t, float*,
                                 cudaStream_t);
 cudaError_t launch_epilogue(CtxDev* const*, int, cudaStream_t);
+cudaError_t launch_lattice_resident(int, const LatJob*, int, uint32_t, uint32_t, uint32_t,
+                                    cudaStream_t);
 cudaError_t launch_philox(uint64_t, const uint32_t*, uint32_t*, int64_t, cudaStream_t);
 cudaError_t launch_threshold(const double*, const double*, uint64_t*, int64_t, cudaStream_t);
 }  // namespace shk
@@ -804,16 +806,51 @@ static shaken_status check_steps(shaken_ctx* c, uint64_t n) {
   return SHAKEN_OK;
 }
 
-shaken_status shaken_step(shaken_ctx* ctx, uint64_t n_steps) {
-  if (!ctx) return fail(SHAKEN_E_INVAL, "ctx is NULL");
-  if (ctx->owner) return fail(SHAKEN_E_STATE, "context belongs to a batch");
-  TRY(check_steps(ctx, n_steps));
+// Small lattices run whole chunks of steps inside one launch, one block per
+// replica (or multispin group), the state in shared memory.
+static bool resident_eligible(const shaken_ctx* c, uint64_t n_steps) {
+  if (c->kind != SHAKEN_LATTICE || c->owner || n_steps < 4) return false;
+  const uint64_t words = c->enc == SHAKEN_MULTISPIN ? (uint64_t)c->L * c->L
+                                                    : (uint64_t)c->L * c->L / 32;
+  if (words > 4096) return false;
+  if (c->enc == SHAKEN_MULTISPIN && (c->hcd.tracking || c->hcd.record)) return false;
+  return true;
+}
+
+static shaken_status run_resident(shaken_ctx* c, uint64_t n_steps) {
+  cudaStream_t st = c->stream;
+  if (c->solo.dirty) TRY(build_plan(c->solo, st));
+  const Family& F = *c->solo.fams[0];
+  const int n_jobs = c->enc == SHAKEN_MULTISPIN ? c->R / 32 : c->R;
+  const uint32_t words = c->enc == SHAKEN_MULTISPIN ? (uint32_t)(c->L * c->L)
+                                                    : (uint32_t)(c->L * c->L / 32);
+  uint64_t done = 0;
+  while (done < n_steps) {
+    const uint64_t chunk = std::min<uint64_t>(n_steps - done, 1u << 16);
+    CU(shk::launch_lattice_resident(F.enc, F.jobs.as<LatJob>(), n_jobs, words,
+                                    (uint32_t)(c->host_step + done), (uint32_t)chunk, st));
+    c->launches++;
+    done += chunk;
+  }
+  c->host_step += n_steps;
+  return push_cd(c);  // the device step counter follows the host's
+}
+
+static shaken_status solo_run(shaken_ctx* ctx, uint64_t n_steps) {
+  if (resident_eligible(ctx, n_steps)) return run_resident(ctx, n_steps);
   uint64_t nl = 0;
   shaken_status s = plan_run(ctx->solo, ctx->stream, n_steps, n_steps >= 64, &nl);
   ctx->launches += nl;
   if (s != SHAKEN_OK) return s;
   ctx->host_step += n_steps;
   return SHAKEN_OK;
+}
+
+shaken_status shaken_step(shaken_ctx* ctx, uint64_t n_steps) {
+  if (!ctx) return fail(SHAKEN_E_INVAL, "ctx is NULL");
+  if (ctx->owner) return fail(SHAKEN_E_STATE, "context belongs to a batch");
+  TRY(check_steps(ctx, n_steps));
+  return solo_run(ctx, n_steps);
 }
 
 shaken_status shaken_set_tracking(shaken_ctx* ctx, int enable) {
@@ -864,11 +901,7 @@ shaken_status shaken_anneal(shaken_ctx* ctx, const double* beta_schedule, uint64
   if (n_steps == 0) return SHAKEN_OK;
   TRY(check_steps(ctx, n_steps));
   TRY(begin_anneal(ctx, beta_schedule, n_steps));
-  uint64_t nl = 0;
-  shaken_status s = plan_run(ctx->solo, ctx->stream, n_steps, n_steps >= 64, &nl);
-  ctx->launches += nl;
-  if (s != SHAKEN_OK) return s;
-  ctx->host_step += n_steps;
+  TRY(solo_run(ctx, n_steps));
   return end_anneal(ctx);
 }
 
@@ -888,11 +921,7 @@ shaken_status shaken_step_record(shaken_ctx* ctx, uint64_t n_steps, double* mag,
   ctx->hcd.tracking = 1u;
   ctx->solo.invalidate();
   TRY(push_cd(ctx));
-  uint64_t nl = 0;
-  shaken_status s = plan_run(ctx->solo, ctx->stream, n_steps, n_steps >= 64, &nl);
-  ctx->launches += nl;
-  if (s != SHAKEN_OK) return s;
-  ctx->host_step += n_steps;
+  TRY(solo_run(ctx, n_steps));
   if (mag) CU(cudaMemcpyAsync(mag, ctx->series_m.p, bytes, cudaMemcpyDeviceToHost, ctx->stream));
   if (energy)
     CU(cudaMemcpyAsync(energy, ctx->series_H.p, bytes, cudaMemcpyDeviceToHost, ctx->stream));

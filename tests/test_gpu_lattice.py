@@ -179,3 +179,23 @@ def test_frozen_sites_stay_plus(S):
     s = S.shaken_get_spins(ctx, 1, L * L)[0]
     assert np.all(s[fz > 0] == 1)
     S.shaken_free(ctx)
+
+
+@pytest.mark.parametrize("enc", ["INT8", "PACKED", "MULTISPIN"])
+def test_tiled_and_resident_paths_agree_with_oracle(S, enc):
+    """Small lattices run chunks of >= 4 steps in one resident launch; chunks of
+    fewer steps use the per-half-step tiled kernels.  Both must follow the oracle."""
+    e = getattr(S, enc)
+    L, R = (64, 32) if enc == "MULTISPIN" else (96, 2)
+    beta = W.beta_grid(R, 0.35, 0.5, 5)
+    J, q, lam, seed = 1.0, 0.8, 0.02, 99
+    ctx = S.shaken_init(lattice_problem(S, e, L, R, beta, J, q, lam), seed)
+    mode = mode_of(S, e)
+    o = core.lattice_init(L, R, seed, mode, 0)
+    t = 0
+    for n in (2, 5, 3, 1, 6):  # tiled, resident, tiled, tiled, resident
+        S.shaken_step(ctx, n)
+        o, _ = core.lattice_run(o, J, q, lam, beta, seed, t, n, mode)
+        t += n
+        assert np.array_equal(S.shaken_get_spins(ctx, R, L * L).reshape(R, L, L), o), n
+    S.shaken_free(ctx)
