@@ -299,6 +299,9 @@ def run_ours(args, rank, world, local_rank):
     # ---- arbitrary sparse graphs: n = 1e6, 256 replicas, lambda_x ~ N(0, 0.1^2), q = 1
     graphs = {} if args.skip_graphs else run_graphs(S, stream, torch, args)
 
+    # ---- serving: Poisson stream of anneal jobs, continuous batching
+    serving = None if args.skip_serving else run_serving(S, stream, args)
+
     # ---- roofline of the dominant kernel (multispin half step)
     rb_calls, _ = S.shaken_microbench(0)
     rb_lop3, _ = S.shaken_microbench(1)
@@ -345,6 +348,7 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clocks,
             "graphs": graphs,
             "small_lattice": small,
+            "serving": serving,
             "batched_vs_plain": {
                 "batched_updates_per_s": value / world,
                 "batched_graph_replay_updates_per_s": graph_rate,
@@ -426,6 +430,60 @@ def run_graphs(S, stream, torch, args):
     return out
 
 
+# ------------------------------------------------------------------------ serving
+def run_serving(S, stream, args):
+    """Continuous batching of annealing jobs through the server.  Arrivals are a
+    Poisson stream; each job anneals (beta 0.1 -> 3.0) a +-1 Erdos-Renyi graph with
+    n log-uniform in [1e3, 1e6] and mean degree uniform in [3, 16] -- drawn from a
+    pool of pre-generated graphs of that distribution -- with replicas log-uniform
+    over multiples of 32 in [32, 1024] and steps uniform in [1000, 20000] times
+    step_scale.  Returns p50/p99 latency (completion - arrival) and throughput."""
+    g = W.rng(W.BASE_SEED + 77)
+    pool = []
+    for k in range(args.serve_pool):
+        n = int(round(np.exp(g.uniform(np.log(1e3), np.log(1e6)))))
+        n += n % 2
+        deg = float(g.uniform(3.0, 16.0))
+        u, v = W.erdos_renyi(n, deg, W.BASE_SEED + 1000 + k)
+        J = W.couplings_pm1(u.size, W.BASE_SEED + 2000 + k)
+        pool.append((n, u, v, J))
+    jobs = W.serving_stream(args.serve_rate, args.serve_horizon, W.BASE_SEED + 3)
+    srv = S.shaken_server_create(int(args.serve_budget_gb * 2**30), 64, stream)
+    t0 = time.perf_counter()
+    ids, meta = [], []
+    for k, jb in enumerate(jobs):
+        n, u, v, J = pool[k % len(pool)]
+        steps = max(1, int(round(jb["steps"] * args.serve_step_scale)))
+        R = jb["replicas"]
+        p = S.Problem(S.GRAPH, S.MULTISPIN, R, 0.1, 1.0, n=n, u=u, v=v, J_edge=J,
+                      J_is_integer=True)
+        delay = jb["arrival"] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        ids.append(S.shaken_server_submit(srv, p, jb["seed"], W.linear_schedule(0.1, 3.0, steps)))
+        meta.append((jb["arrival"], n, R, steps))
+    S.shaken_server_drain(srv, args.serve_timeout)
+    wall = time.perf_counter() - t0
+    upd, launches, done = S.shaken_server_stats(srv)
+    lat, waits = [], []
+    for jid, (arr, n, R, steps) in zip(ids, meta):
+        _, ta, td = S.shaken_server_result(srv, jid, R)
+        lat.append(td - arr)
+        waits.append(ta - arr)
+    S.shaken_server_free(srv)
+    lat = np.array(lat)
+    work = sum(2.0 * n * R * st for _, n, R, st in meta)
+    return {"jobs": len(ids), "completed": int(done), "wall_s": wall,
+            "arrival_rate_per_s": args.serve_rate, "horizon_s": args.serve_horizon,
+            "step_scale": args.serve_step_scale, "graph_pool": len(pool),
+            "offered_updates_per_s": work / args.serve_horizon,
+            "served_updates_per_s": upd / wall,
+            "latency_p50_s": float(np.percentile(lat, 50)),
+            "latency_p99_s": float(np.percentile(lat, 99)),
+            "admission_wait_p50_s": float(np.percentile(waits, 50)),
+            "launches": int(launches)}
+
+
 # ------------------------------------------------------------------------ reference arm
 def run_reference(args, rank, world):
     if rank != 0:
@@ -466,6 +524,14 @@ def main():
                     help="time the batched workload only (profiling runs)")
     ap.add_argument("--skip-graphs", action="store_true", help="skip the sparse-graph section")
     ap.add_argument("--graph-anneal-steps", type=int, default=5000)
+    ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=4.0, help="Poisson arrivals per second")
+    ap.add_argument("--serve-horizon", type=float, default=10.0, help="seconds of arrivals")
+    ap.add_argument("--serve-step-scale", type=float, default=0.05,
+                    help="steps per job = U[1000, 20000] x this factor")
+    ap.add_argument("--serve-pool", type=int, default=12, help="pre-generated graphs")
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
+    ap.add_argument("--serve-timeout", type=float, default=120.0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

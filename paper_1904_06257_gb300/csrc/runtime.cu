@@ -599,7 +599,19 @@ static shaken_status validate(const shaken_problem* p) {
   return SHAKEN_OK;
 }
 
-static shaken_status build_graph(shaken_ctx* c, const shaken_problem* p, cudaStream_t st) {
+// Host-side preparation of a context (no CUDA call): orientation and CSR of a
+// graph, frozen lane masks, initial spins.  Kept separate from the device
+// set-up so that the server can prepare jobs on the submitting thread.
+struct HostPrep {
+  std::vector<int32_t> iptr, optr;
+  std::vector<uint32_t> icol, ocol;
+  std::vector<float> iJ, oJ;
+  std::vector<uint32_t> frozen_lanes;
+  std::vector<int8_t> init_spins;
+  int init_kind = 0;
+};
+
+static void build_graph_host(shaken_ctx* c, const shaken_problem* p, HostPrep& hp) {
   const int64_t n = p->n, m = p->m;
   std::vector<int32_t> tail(m), head(m);
   for (int64_t e = 0; e < m; ++e) {
@@ -619,31 +631,30 @@ static shaken_status build_graph(shaken_ctx* c, const shaken_problem* p, cudaStr
     for (int64_t x = 0; x < n; ++x) ptr[x + 1] += ptr[x];
     std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
     col.assign(m, 0);
-    Jv.assign(m, 0.0f);
+    if (!c->integer) Jv.assign(m, 0.0f);
     for (int64_t e = 0; e < m; ++e) {
       const int32_t pos = fill[key[e]]++;
       uint32_t cv = (uint32_t)other[e];
       if (c->integer && p->J_edge[e] < 0.0f) cv |= 0x80000000u;
       col[pos] = cv;
-      Jv[pos] = p->J_edge[e];
+      if (!c->integer) Jv[pos] = p->J_edge[e];
     }
   };
-  std::vector<int32_t> iptr, optr;
-  std::vector<uint32_t> icol, ocol;
-  std::vector<float> iJ, oJ;
-  csr(head, tail, iptr, icol, iJ);
-  csr(tail, head, optr, ocol, oJ);
+  csr(head, tail, hp.iptr, hp.icol, hp.iJ);
+  csr(tail, head, hp.optr, hp.ocol, hp.oJ);
   c->sumJ = 0.0;
   for (int64_t e = 0; e < m; ++e) c->sumJ += (double)p->J_edge[e];
-  TRY(upload(c->in_ptr, iptr.data(), iptr.size() * 4, st));
-  TRY(upload(c->out_ptr, optr.data(), optr.size() * 4, st));
-  TRY(upload(c->in_col, icol.data(), icol.size() * 4, st));
-  TRY(upload(c->out_col, ocol.data(), ocol.size() * 4, st));
+}
+
+static shaken_status upload_graph(shaken_ctx* c, const HostPrep& hp, cudaStream_t st) {
+  TRY(upload(c->in_ptr, hp.iptr.data(), hp.iptr.size() * 4, st));
+  TRY(upload(c->out_ptr, hp.optr.data(), hp.optr.size() * 4, st));
+  TRY(upload(c->in_col, hp.icol.data(), hp.icol.size() * 4, st));
+  TRY(upload(c->out_col, hp.ocol.data(), hp.ocol.size() * 4, st));
   if (!c->integer) {
-    TRY(upload(c->in_J, iJ.data(), iJ.size() * 4, st));
-    TRY(upload(c->out_J, oJ.data(), oJ.size() * 4, st));
+    TRY(upload(c->in_J, hp.iJ.data(), hp.iJ.size() * 4, st));
+    TRY(upload(c->out_J, hp.oJ.data(), hp.oJ.size() * 4, st));
   }
-  CU(cudaStreamSynchronize(st));  // host vectors die here
   return SHAKEN_OK;
 }
 
@@ -683,10 +694,12 @@ static shaken_status reset_best(shaken_ctx* c) {
 // ============================================================================ C ABI: contexts
 extern "C" {
 
-shaken_status shaken_init(shaken_ctx** out, const shaken_problem* p, uint64_t seed,
-                          void* cuda_stream) {
-  if (!out) return fail(SHAKEN_E_INVAL, "out is NULL");
-  *out = nullptr;
+}  // extern "C"
+
+// Validates the problem and fills the context's host fields and the host-side
+// preparation (no CUDA call).
+static shaken_status prepare_ctx(const shaken_problem* p, uint64_t seed, void* cuda_stream,
+                                 std::unique_ptr<shaken_ctx>& out, HostPrep& hp) {
   TRY(validate(p));
   std::unique_ptr<shaken_ctx> c(new shaken_ctx());
   c->kind = p->kind;
@@ -722,9 +735,15 @@ shaken_status shaken_init(shaken_ctx** out, const shaken_problem* p, uint64_t se
         for (int64_t x = 0; x < N; ++x)
           if (c->frozen[x] && p->init_spins[(size_t)r * N + x] != 1)
             return fail(SHAKEN_E_INVAL, "frozen sites must be +1 in init_spins");
+    if (c->kind == SHAKEN_LATTICE && c->enc != SHAKEN_MULTISPIN) {
+      hp.frozen_lanes.assign(N / 32, 0u);
+      for (int64_t x = 0; x < N; ++x)
+        if (c->frozen[x]) hp.frozen_lanes[x >> 5] |= 1u << (x & 31);
+    } else {
+      hp.frozen_lanes.assign(N, 0u);
+      for (int64_t x = 0; x < N; ++x) hp.frozen_lanes[x] = c->frozen[x] ? 0xffffffffu : 0u;
+    }
   }
-  cudaStream_t st = c->stream;
-  // spin buffers
   if (c->kind == SHAKEN_LATTICE) {
     if (c->enc == SHAKEN_INT8)
       c->spin_bytes = (size_t)c->R * N;
@@ -734,36 +753,31 @@ shaken_status shaken_init(shaken_ctx** out, const shaken_problem* p, uint64_t se
       c->spin_bytes = (size_t)(c->R / 32) * N * 4;
   } else {
     c->spin_bytes = (size_t)(c->R / 32) * N * 4;
+    build_graph_host(c.get(), p, hp);
   }
+  hp.init_kind = p->init;
+  if (p->init == SHAKEN_INIT_GIVEN) hp.init_spins.assign(p->init_spins, p->init_spins + (size_t)c->R * N);
+  out = std::move(c);
+  return SHAKEN_OK;
+}
+
+// Device set-up of a prepared context: allocations, uploads, tables, initial spins.
+static shaken_status setup_ctx(shaken_ctx* c, const HostPrep& hp) {
+  cudaStream_t st = ctx_stream(c);
+  const int64_t N = c->sites();
   TRY(c->A.alloc(c->spin_bytes));
   TRY(c->B.alloc(c->spin_bytes));
-  // frozen lane masks
-  if (!c->frozen.empty()) {
-    std::vector<uint32_t> fl;
-    if (c->kind == SHAKEN_LATTICE && c->enc != SHAKEN_MULTISPIN) {
-      fl.assign(N / 32, 0u);
-      for (int64_t x = 0; x < N; ++x)
-        if (c->frozen[x]) fl[x >> 5] |= 1u << (x & 31);
-    } else {
-      fl.assign(N, 0u);
-      for (int64_t x = 0; x < N; ++x) fl[x] = c->frozen[x] ? 0xffffffffu : 0u;
-    }
-    TRY(upload(c->frozen_lanes, fl.data(), fl.size() * 4, st));
-    CU(cudaStreamSynchronize(st));
-  }
-  // graph structure, lambda, betas
+  if (!hp.frozen_lanes.empty())
+    TRY(upload(c->frozen_lanes, hp.frozen_lanes.data(), hp.frozen_lanes.size() * 4, st));
   if (c->kind == SHAKEN_GRAPH) {
-    TRY(build_graph(c.get(), p, st));
+    TRY(upload_graph(c, hp, st));
     if (c->has_lambda) TRY(upload(c->lam_dev, c->lambda.data(), c->lambda.size() * 4, st));
     TRY(upload(c->beta_lanes, c->beta.data(), c->beta.size() * 8, st));
-    CU(cudaStreamSynchronize(st));
   } else {
-    const std::vector<double> lanes = lattice_table_lanes(c.get());
-    TRY(build_tables_for_betas(c.get(), lanes, c->tables, c->beta_lanes, lattice_ntab(c.get()),
-                               st));
-    CU(cudaStreamSynchronize(st));
+    const std::vector<double> lanes = lattice_table_lanes(c);
+    TRY(build_tables_for_betas(c, lanes, c->tables, c->beta_lanes, lattice_ntab(c), st));
   }
-  // sums, best, ctx record
+  CU(cudaStreamSynchronize(st));  // host sources of the uploads may go away after this
   const size_t sums_bytes = (size_t)c->R * kNumSums * sizeof(double);
   TRY(c->step_sums.alloc(sums_bytes));
   TRY(c->obs_sums.alloc(sums_bytes));
@@ -783,12 +797,25 @@ shaken_status shaken_init(shaken_ctx** out, const shaken_problem* p, uint64_t se
   h.step_sums = c->step_sums.as<double>();
   h.best = c->best.as<double>();
   h.best_step = c->best_step.as<long long>();
-  TRY(push_cd(c.get()));
-  TRY(reset_best(c.get()));
-  c->solo.members = {c.get()};
+  TRY(push_cd(c));
+  TRY(reset_best(c));
+  c->solo.members = {c};
   c->solo.dirty = true;
-  TRY(ctx_init_spins(c.get(), p->init, p->init_spins));
+  TRY(ctx_init_spins(c, hp.init_kind, hp.init_spins.empty() ? nullptr : hp.init_spins.data()));
   CU(cudaStreamSynchronize(st));
+  return SHAKEN_OK;
+}
+
+extern "C" {
+
+shaken_status shaken_init(shaken_ctx** out, const shaken_problem* p, uint64_t seed,
+                          void* cuda_stream) {
+  if (!out) return fail(SHAKEN_E_INVAL, "out is NULL");
+  *out = nullptr;
+  std::unique_ptr<shaken_ctx> c;
+  HostPrep hp;
+  TRY(prepare_ctx(p, seed, cuda_stream, c, hp));
+  TRY(setup_ctx(c.get(), hp));
   *out = c.release();
   return SHAKEN_OK;
 }
@@ -1290,12 +1317,9 @@ const char* shaken_version(void) { return "libshaken 0.1 (sm_103a)"; }
 // context once its step reaches t_end), and retires finished jobs.
 struct ServerJob {
   int64_t id = 0;
-  shaken_problem p{};
-  std::vector<int32_t> u, v;
-  std::vector<float> J, lambda;
-  std::vector<uint8_t> frozen;
-  std::vector<double> beta, sched;
-  std::vector<int8_t> init;
+  std::unique_ptr<shaken_ctx> prepared;  // host-prepared context (device set-up in the worker)
+  HostPrep hp;
+  std::vector<double> sched;
   uint64_t seed = 0, n_steps = 0;
   size_t bytes = 0;
   int state = 0;  // 0 queued, 1 running, 2 done, 3 failed
@@ -1348,8 +1372,10 @@ static void server_loop(shaken_server* s) {
       if (s->used + j->bytes > s->budget && !s->running.empty()) break;
       s->queue.pop_front();
       lk.unlock();
-      shaken_ctx* c = nullptr;
-      shaken_status st = shaken_init(&c, &j->p, j->seed, s->stream);
+      shaken_ctx* c = j->prepared.release();
+      c->stream = s->stream;
+      shaken_status st = setup_ctx(c, j->hp);
+      j->hp = HostPrep();  // host copies are on the device now
       if (st == SHAKEN_OK) {
         c->owner = &s->batch;
         st = begin_anneal(c, j->sched.data(), j->n_steps);
@@ -1446,33 +1472,13 @@ shaken_status shaken_server_submit(shaken_server* s, const shaken_problem* p, ui
                                    int64_t* job_id) {
   if (!s || !p || !beta_schedule || !job_id || n_steps == 0)
     return fail(SHAKEN_E_INVAL, "bad argument");
-  TRY(validate(p));
   if (n_steps >= 0xFFFFFFFEull) return fail(SHAKEN_E_INVAL, "too many steps");
+  for (uint64_t k = 0; k < n_steps; ++k)
+    if (!std::isfinite(beta_schedule[k]) || beta_schedule[k] < 0.0)
+      return fail(SHAKEN_E_INVAL, "beta_schedule must be finite and >= 0");
   auto j = std::make_unique<ServerJob>();
-  j->p = *p;
-  const int64_t N = p->kind == SHAKEN_LATTICE ? p->L * p->L : p->n;
-  if (p->m > 0 && p->kind == SHAKEN_GRAPH) {
-    j->u.assign(p->u, p->u + p->m);
-    j->v.assign(p->v, p->v + p->m);
-    j->J.assign(p->J_edge, p->J_edge + p->m);
-    j->p.u = j->u.data();
-    j->p.v = j->v.data();
-    j->p.J_edge = j->J.data();
-  }
-  if (p->lambda) {
-    j->lambda.assign(p->lambda, p->lambda + N);
-    j->p.lambda = j->lambda.data();
-  }
-  if (p->frozen_mask) {
-    j->frozen.assign(p->frozen_mask, p->frozen_mask + N);
-    j->p.frozen_mask = j->frozen.data();
-  }
-  j->beta.assign(p->beta, p->beta + p->replicas);
-  j->p.beta = j->beta.data();
-  if (p->init == SHAKEN_INIT_GIVEN) {
-    j->init.assign(p->init_spins, p->init_spins + (size_t)p->replicas * N);
-    j->p.init_spins = j->init.data();
-  }
+  // validation, orientation and CSR on the submitting thread
+  TRY(prepare_ctx(p, seed, s->stream, j->prepared, j->hp));
   j->sched.assign(beta_schedule, beta_schedule + n_steps);
   j->seed = seed;
   j->n_steps = n_steps;
