@@ -265,21 +265,24 @@ def run_ours(args, rank, world, local_rank):
            "what": "per job of K steps: raw state of all 128 groups H2D from pinned memory, "
                    "K batched steps (CUDA graph), states and observables D2H; wall clock"}
 
-    # ---- plain single-lattice kernel: L = 4096 int8, one replica
+    # ---- plain single-lattice kernel: L = 4096, one replica, int8 and bit-packed
     Lp = 4096
-    pp = S.Problem(S.LATTICE, S.INT8, 1, 0.4407, Q, L=Lp, J=J, lambda_const=LAM)
-    cp = S.shaken_init(pp, W.BASE_SEED + 7, stream)
-    S.shaken_step(cp, 3)
-    S.shaken_sync(cp)
-    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        pe0.record(stream)
-    S.shaken_step(cp, 64)
-    with torch.cuda.stream(stream):
-        pe1.record(stream)
-    stream.synchronize()
-    plain_rate = 2.0 * Lp * Lp * 64 / (pe0.elapsed_time(pe1) * 1e-3)
-    S.shaken_free(cp)
+    plain = {}
+    for name, enc in (("int8", S.INT8), ("packed", S.PACKED)):
+        pp = S.Problem(S.LATTICE, enc, 1, 0.4407, Q, L=Lp, J=J, lambda_const=LAM)
+        cp = S.shaken_init(pp, W.BASE_SEED + 7, stream)
+        S.shaken_step(cp, 3)
+        S.shaken_sync(cp)
+        pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            pe0.record(stream)
+        S.shaken_step(cp, 128)
+        with torch.cuda.stream(stream):
+            pe1.record(stream)
+        stream.synchronize()
+        plain[name] = 2.0 * Lp * Lp * 128 / (pe0.elapsed_time(pe1) * 1e-3)
+        S.shaken_free(cp)
+    plain_rate = plain["int8"]
 
     # ---- small lattice: L = 64 int8, one replica, beta = 0.40, 10^4 steps with m and H per step
     Ls1 = 64
@@ -354,7 +357,8 @@ def run_ours(args, rank, world, local_rank):
                 "batched_updates_per_s": value / world,
                 "batched_graph_replay_updates_per_s": graph_rate,
                 "unbatched_same_groups_updates_per_s": unbatched_rate,
-                "plain_int8_L4096_updates_per_s": plain_rate},
+                "plain_int8_L4096_updates_per_s": plain_rate,
+                "plain_packed_L4096_updates_per_s": plain["packed"]},
         }
     for c in ctxs:
         S.shaken_batch_remove(batch, c)
