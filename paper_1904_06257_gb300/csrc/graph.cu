@@ -39,6 +39,14 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // t0 = u 2^-32 (1 + e~) > 1 + eps (certainly -1); eps = 2^-18 + 2^-18 beta B with
 // B >= |s| + |q| + |lambda| + 1 is at least three times the fp32 error of t
 // (rounding of h~, kb h~, ex2, the two products); in between, T is computed in fp64.
+// The fp64 threshold test, out of line: it is reached with probability about
+// 2^-17 (1 + beta B) per update, so it should not bloat the hot loop.
+__device__ __noinline__ bool decide_exact(uint32_t u, int s, int sigma, double q, float lam,
+                                          double beta) {
+  const double h = field_h(1.0, s, q, sigma, (double)lam);
+  return (unsigned long long)u < threshold_T(h, beta);
+}
+
 __device__ __forceinline__ bool decide_int(uint32_t u, int s, int sigma, float qf, double q,
                                            float lam, float kb, float eps, double beta,
                                            bool exact_always) {
@@ -49,8 +57,7 @@ __device__ __forceinline__ bool decide_int(uint32_t u, int s, int sigma, float q
     if ((uf + 2.3283064365386963e-10f) * onep < 1.0f - eps) return true;
     if (uf * onep > 1.0f + eps) return false;
   }
-  const double h = field_h(1.0, s, q, sigma, (double)lam);
-  return (unsigned long long)u < threshold_T(h, beta);
+  return decide_exact(u, s, sigma, q, lam, beta);
 }
 
 struct GraphShared {
@@ -163,32 +170,35 @@ __global__ void __launch_bounds__(kTile) graph_half_kernel(const GraphJob* __res
         }
       }
       const float B = (float)d + fabsf(qf) + fabsf(lam) + 1.0f;
-      uint4 w = make_uint4(0, 0, 0, 0);
+#pragma unroll 1
+      for (int c = 0; c < 8; ++c) {  // one Philox call per 4 lanes
+        const uint4 w = ph_call(K, x, J.b, t, half + 2u * (uint32_t)c);
+        const uint32_t uw[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        if ((k & 3) == 0) w = ph_call(K, x, J.b, t, half + 2u * (uint32_t)(k >> 2));
-        const uint32_t u = (k & 3) == 0 ? w.x : (k & 3) == 1 ? w.y : (k & 3) == 2 ? w.z : w.w;
-        int cnt;
-        if (d <= 63) {
-          cnt = 0;
+        for (int i = 0; i < 4; ++i) {
+          const int k = 4 * c + i;
+          int cnt;
+          if (d <= 63) {
+            cnt = 0;
 #pragma unroll
-          for (int b = 0; b < 6; ++b) cnt |= (int)((P[b] >> k) & 1u) << b;
-        } else {
-          cnt = 0;
-          for (int e = p0; e < p1; ++e) {
-            const uint32_t cv = col[e];
-            cnt += (int)(((src[cv & 0x7fffffffu] ^ (0u - (cv >> 31))) >> k) & 1u);
+            for (int b = 0; b < 6; ++b) cnt |= (int)((P[b] >> k) & 1u) << b;
+          } else {
+            cnt = 0;
+            for (int e = p0; e < p1; ++e) {
+              const uint32_t cv = col[e];
+              cnt += (int)(((src[cv & 0x7fffffffu] ^ (0u - (cv >> 31))) >> k) & 1u);
+            }
           }
-        }
-        const int s = 2 * cnt - d;
-        const int sigma = ((S >> k) & 1u) ? 1 : -1;
-        const float eps = 3.814697265625e-06f + sh.epc[k] * B;
-        const bool plus = decide_int(u, s, sigma, qf, J.q, lam, sh.kb[k], eps, sh.beta[k],
-                                     exact_always != 0);
-        res |= (uint32_t)plus << k;
-        if (fuse) {
-          const float a = (float)s + 2.0f * lam;
-          acc[k][lane] += sigma > 0 ? a : -a;
+          const int s = 2 * cnt - d;
+          const int sigma = ((S >> k) & 1u) ? 1 : -1;
+          const float eps = 3.814697265625e-06f + sh.epc[k] * B;
+          const bool plus = decide_int(uw[i], s, sigma, qf, J.q, lam, sh.kb[k], eps, sh.beta[k],
+                                       exact_always != 0);
+          res |= (uint32_t)plus << k;
+          if (fuse) {
+            const float a = (float)s + 2.0f * lam;
+            acc[k][lane] += sigma > 0 ? a : -a;
+          }
         }
       }
     } else {
