@@ -142,6 +142,14 @@ shaken_status shaken_step(shaken_ctx* ctx, uint64_t n_steps);
  * per-replica beta reverts to the one given at init. */
 shaken_status shaken_anneal(shaken_ctx* ctx, const double* beta_schedule, uint64_t n_steps);
 
+/* Order of the two half steps within a step: 0 (default) P^{1->2} then P^{2->1}
+ * (on the lattice P^dl then P^ur, Sec. 3); 1 the reversed chain P^{sh'} = P^ur then
+ * P^dl (Sec. 3, end), i.e. out-neighbour fields first.  The draw of an update is
+ * keyed by its type (dl / 1->2 = half 0, ur / 2->1 = half 1), not by its position.
+ * observables' pair energy stays H(sigma, sigma') of Eq. (ham21) with sigma' the
+ * configuration after the first half step of the last step. */
+shaken_status shaken_set_order(shaken_ctx* ctx, int reversed);
+
 /* Turn per-step best-energy tracking on (1) or off (0) for shaken_step.
  * Tracking evaluates H(sigma_t) of every full-step configuration; on INT8 and
  * PACKED lattices it is fused into the first half step. */

@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kTile) graph_half_kernel(const GraphJob* __res
   const int te = (int)(((long long)(blockIdx.x + 1) * n_tiles) / gridDim.x);
   int cur_job = -1;
   bool fuse = false, skip = false;
-  uint32_t t = 0;
+  uint32_t t = 0, typ = 0;
   double* fuse_dst = nullptr;
   float(*acc)[32] = sh.acc[warp];  // acc[k][lane]: this thread's sum for replica lane k
 #pragma unroll
@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(kTile) graph_half_kernel(const GraphJob* __res
       __syncthreads();  // shared per-job constants are about to change
       const CtxDev* cd = J.cd;
       t = cd->step;
+      typ = half ^ cd->order;
       skip = t >= cd->t_end;
       fuse = !skip && half == 0u && cd->tracking && !cd->record;
       fuse_dst = J.sums;
@@ -141,11 +142,12 @@ __global__ void __launch_bounds__(kTile) graph_half_kernel(const GraphJob* __res
     if (skip) continue;
     const uint32_t x = tl.w0 + threadIdx.x;
     if (x >= J.n) continue;
+    // `half` is the position in the step (buffers); typ the update type (neighbours, draws)
     const uint32_t* src = half == 0u ? J.A : J.B;
     uint32_t* dst = half == 0u ? J.B : J.A;
-    const int32_t* ptr = half == 0u ? J.in_ptr : J.out_ptr;
-    const uint32_t* col = half == 0u ? J.in_col : J.out_col;
-    const float* Jr = half == 0u ? J.in_J : J.out_J;
+    const int32_t* ptr = typ == 0u ? J.in_ptr : J.out_ptr;
+    const uint32_t* col = typ == 0u ? J.in_col : J.out_col;
+    const float* Jr = typ == 0u ? J.in_J : J.out_J;
     const int32_t p0 = ptr[x], p1 = ptr[x + 1];
     const int d = p1 - p0;
     const uint32_t S = src[x];
@@ -172,7 +174,7 @@ __global__ void __launch_bounds__(kTile) graph_half_kernel(const GraphJob* __res
       const float B = (float)d + fabsf(qf) + fabsf(lam) + 1.0f;
 #pragma unroll 1
       for (int c = 0; c < 8; ++c) {  // one Philox call per 4 lanes
-        const uint4 w = ph_call(K, x, J.b, t, half + 2u * (uint32_t)c);
+        const uint4 w = ph_call(K, x, J.b, t, typ + 2u * (uint32_t)c);
         const uint32_t uw[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -215,7 +217,7 @@ __global__ void __launch_bounds__(kTile) graph_half_kernel(const GraphJob* __res
       uint4 w = make_uint4(0, 0, 0, 0);
 #pragma unroll
       for (int k = 0; k < 32; ++k) {
-        if ((k & 3) == 0) w = ph_call(K, x, J.b, t, half + 2u * (uint32_t)(k >> 2));
+        if ((k & 3) == 0) w = ph_call(K, x, J.b, t, typ + 2u * (uint32_t)(k >> 2));
         const uint32_t u = (k & 3) == 0 ? w.x : (k & 3) == 1 ? w.y : (k & 3) == 2 ? w.z : w.w;
         const bool up = (S >> k) & 1u;
         const float hk = __fadd_rn(__fadd_rn(h[k], up ? qf : -qf), lam);

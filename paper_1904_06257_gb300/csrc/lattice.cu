@@ -296,6 +296,7 @@ struct TileShared {
   uint32_t t;
   uint32_t skip;
   uint32_t fuse;
+  uint32_t typ;
   const LatTable* tab_src;
 };
 
@@ -415,6 +416,7 @@ __global__ void __launch_bounds__(kTile, 3) lattice_half_kernel(const LatJob* __
         sh.t = t;
         sh.skip = t >= cd->t_end;
         sh.fuse = (ENC != kEncMultispin) && half == 0u && sh.job.sums != nullptr && cd->tracking;
+        sh.typ = half ^ cd->order;  // update type: 0 = dl / 1->2, 1 = ur / 2->1
         const LatTable* src = sh.job.table;
         if (sh.job.anneal_tables != nullptr && cd->anneal_len != 0u) {
           uint32_t k = t - cd->anneal_t0;
@@ -435,7 +437,8 @@ __global__ void __launch_bounds__(kTile, 3) lattice_half_kernel(const LatJob* __
     if (sh.skip) continue;
     const LatJob& J = sh.job;
     const uint32_t t = sh.t;
-    const void* src = half == 0u ? J.A : J.B;
+    const uint32_t typ = sh.typ;
+    const void* src = half == 0u ? J.A : J.B;  // `half` is the position in the step
     void* dstbuf = half == 0u ? J.B : J.A;
     uint32_t S[WPT], V[WPT], H[WPT], F[WPT];
 #pragma unroll
@@ -444,7 +447,7 @@ __global__ void __launch_bounds__(kTile, 3) lattice_half_kernel(const LatJob* __
       S[k] = V[k] = H[k] = 0u;
       F[k] = 0u;
       if (w < J.nwords) {
-        load_lane_words<ENC>(J, src, w, half, S[k], V[k], H[k]);
+        load_lane_words<ENC>(J, src, w, typ, S[k], V[k], H[k]);
         if (J.frozen != nullptr) F[k] = J.frozen[w];
       }
     }
@@ -453,17 +456,17 @@ __global__ void __launch_bounds__(kTile, 3) lattice_half_kernel(const LatJob* __
     const bool full_tile = tl.w0 + kTile * WPT <= J.nwords;
     if (sh.tab.collapsed) {
       if (full_tile)
-        tile_decide<ENC, WPT, true, true>(J, sh, queue[warp], K, tl.w0, t, half, S, V, H, F,
+        tile_decide<ENC, WPT, true, true>(J, sh, queue[warp], K, tl.w0, t, typ, S, V, H, F,
                                           dstbuf, acc, calls);
       else
-        tile_decide<ENC, WPT, true, false>(J, sh, queue[warp], K, tl.w0, t, half, S, V, H, F,
+        tile_decide<ENC, WPT, true, false>(J, sh, queue[warp], K, tl.w0, t, typ, S, V, H, F,
                                            dstbuf, acc, calls);
     } else {
       if (full_tile)
-        tile_decide<ENC, WPT, false, true>(J, sh, queue[warp], K, tl.w0, t, half, S, V, H, F,
+        tile_decide<ENC, WPT, false, true>(J, sh, queue[warp], K, tl.w0, t, typ, S, V, H, F,
                                            dstbuf, acc, calls);
       else
-        tile_decide<ENC, WPT, false, false>(J, sh, queue[warp], K, tl.w0, t, half, S, V, H, F,
+        tile_decide<ENC, WPT, false, false>(J, sh, queue[warp], K, tl.w0, t, typ, S, V, H, F,
                                             dstbuf, acc, calls);
     }
     if (sh.fuse) {
@@ -678,6 +681,7 @@ __global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* _
   const CtxDev* cd = J.cd;
   const uint32_t anneal_t0 = cd->anneal_t0, anneal_len = cd->anneal_len;
   const bool track = ENC != kEncMultispin && cd->tracking && J.sums != nullptr;
+  const uint32_t order = cd->order;
   const bool record = track && cd->record;
   for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) sA[w] = resident_load<ENC>(J, w);
   const PhKey K = ph_key(J.key0, J.key1);
@@ -700,9 +704,10 @@ __global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* _
     }
     __syncthreads();  // sA complete (previous half step or the load), table staged
     double acc[3] = {0.0, 0.0, 0.0};
-    for (uint32_t half = 0; half < 2; ++half) {
-      const uint32_t* in = half == 0u ? sA : sB;
-      uint32_t* out = half == 0u ? sB : sA;
+    for (uint32_t pos = 0; pos < 2; ++pos) {
+      const uint32_t half = pos ^ order;  // update type of this position
+      const uint32_t* in = pos == 0u ? sA : sB;
+      uint32_t* out = pos == 0u ? sB : sA;
       for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) {
         uint32_t S, V, H;
         load_lane_words<SENC>(J, in, w, half, S, V, H);
@@ -718,7 +723,7 @@ __global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* _
           decide_tail<false>(Lw, stab, K, w, J.b, t, half, calls);
         }
         out[w] = Lw.res;
-        if (track && half == 0u) {
+        if (track && pos == 0u) {
           const int dv = __popc(S ^ V), dh = __popc(S ^ H);
           acc[0] += (double)(2 * __popc(S) - 32);
           acc[1] += (double)(64 - 2 * dv - 2 * dh);

@@ -880,6 +880,15 @@ shaken_status shaken_step(shaken_ctx* ctx, uint64_t n_steps) {
   return solo_run(ctx, n_steps);
 }
 
+shaken_status shaken_set_order(shaken_ctx* ctx, int reversed) {
+  if (!ctx) return fail(SHAKEN_E_INVAL, "ctx is NULL");
+  if (reversed != 0 && reversed != 1) return fail(SHAKEN_E_INVAL, "order must be 0 or 1");
+  ctx->hcd.order = (uint32_t)reversed;
+  ctx->solo.invalidate();
+  if (ctx->owner) ctx->owner->plan.invalidate();
+  return push_cd(ctx);
+}
+
 shaken_status shaken_set_tracking(shaken_ctx* ctx, int enable) {
   if (!ctx) return fail(SHAKEN_E_INVAL, "ctx is NULL");
   ctx->tracking = enable != 0;

@@ -140,6 +140,8 @@ struct CtxDev {
   uint32_t series_cap;
   uint32_t R;
   uint32_t kind;        // 0 lattice, 1 graph
+  uint32_t order;       // 0: P^{1->2} then P^{2->1} (dl then ur); 1: reversed (Sec. 3, P^{sh'})
+  uint32_t pad0;
   double Jc;            // energy: H = -Jc E - 2 lamc M - 2 LS
   double lamc;
   double inv_n;

@@ -70,6 +70,7 @@ def _load():
         "shaken_step": [vp, u64],
         "shaken_anneal": [vp, vp, u64],
         "shaken_set_tracking": [vp, ctypes.c_int],
+        "shaken_set_order": [vp, ctypes.c_int],
         "shaken_step_record": [vp, u64, vp, vp],
         "shaken_observables": [vp, vp],
         "shaken_get_spins": [vp, vp],
@@ -201,6 +202,10 @@ def shaken_step(ctx, n_steps: int):
 def shaken_anneal(ctx, beta_schedule):
     b = np.ascontiguousarray(beta_schedule, dtype=np.float64)
     _check(_lib.shaken_anneal(ctx, _ptr(b), b.size))
+
+
+def shaken_set_order(ctx, reversed_: bool):
+    _check(_lib.shaken_set_order(ctx, int(bool(reversed_))))
 
 
 def shaken_set_tracking(ctx, enable: bool):

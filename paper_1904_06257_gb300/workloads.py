@@ -133,6 +133,29 @@ def lattice_as_graph(L: int):
     return u, v
 
 
+def triangular_lattice_as_graph(L: int):
+    """Edges of the L x L triangular lattice (square lattice plus the (1,-1)
+    diagonal, periodic), each oriented from x to its three "right" neighbours
+    (i, j+1), (i+1, j), (i+1, j-1); the "left" neighbours are then the
+    in-neighbours.  x = (i, j) -> i*L + j."""
+    i, j = np.divmod(np.arange(L * L), L)
+    x = i * L + j
+    nb = [i * L + (j + 1) % L, ((i + 1) % L) * L + j, ((i + 1) % L) * L + (j - 1) % L]
+    u = np.concatenate([x, x, x]).astype(np.int32)
+    v = np.concatenate(nb).astype(np.int32)
+    return u, v
+
+
+def split_both_ways(u, v, J, frac=0.5):
+    """Generalised decomposition J = J^o + J^oT: every edge {u, v} becomes the two
+    oriented edges (u -> v) with weight frac J and (v -> u) with (1 - frac) J
+    (frac = 1/2 is the symmetric PCA)."""
+    uu = np.concatenate([u, v]).astype(np.int32)
+    vv = np.concatenate([v, u]).astype(np.int32)
+    JJ = np.concatenate([frac * np.asarray(J), (1 - frac) * np.asarray(J)]).astype(np.float32)
+    return uu, vv, JJ
+
+
 def serving_stream(rate_per_s: float, horizon_s: float, seed: int, n_lo=1_000, n_hi=1_000_000,
                    deg_lo=3.0, deg_hi=16.0, rep_lo=32, rep_hi=1024, steps_lo=1000,
                    steps_hi=20000, max_jobs=None):

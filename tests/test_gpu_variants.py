@@ -1,0 +1,118 @@
+"""Variants of the shaken dynamics on the GPU path:
+* the reversed order P^{sh'} = P^ur then P^dl (Sec. 3), bit-exact against the
+  oracle applying the two half steps in that order;
+* the generalised dynamics of Sec. 5 (J = J^o + J^oT, both orientations weighted;
+  J^o = J/2 is the symmetric PCA), fed as an oriented edge list: the GPU chain's
+  law against the exact transition matrix (chi-square);
+* the triangular lattice of Sec. 4 (three right / three left neighbours) through
+  the graph path, bit-exact against the oracle."""
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle import core, exact
+from paper_1904_06257_gb300 import workloads as W
+from tests.gpu_util import graph_problem, lattice_problem, lib, require_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    require_cuda()
+    return lib()
+
+
+@pytest.mark.parametrize("enc,L,R,steps", [("INT8", 64, 2, 5), ("PACKED", 96, 1, 2),
+                                           ("MULTISPIN", 32, 32, 6), ("MULTISPIN", 96, 32, 3)])
+def test_reversed_order_lattice(S, enc, L, R, steps):
+    e = getattr(S, enc)
+    mode = core.MODE_MULTISPIN if enc == "MULTISPIN" else core.MODE_SINGLE
+    J, q, lam, seed = 1.0, 0.7, 0.05, 123
+    beta = W.beta_grid(R, 0.3, 0.6, 5)
+    ctx = S.shaken_init(lattice_problem(S, e, L, R, beta, J, q, lam), seed)
+    S.shaken_set_order(ctx, True)
+    S.shaken_step(ctx, steps)
+    got = S.shaken_get_spins(ctx, R, L * L).reshape(R, L, L)
+    S.shaken_free(ctx)
+    o = core.lattice_init(L, R, seed, mode, 0)
+    for t in range(steps):
+        sp = core.lattice_half(o, J, q, lam, beta, seed, t, 1, mode)  # ur first
+        o = core.lattice_half(sp, J, q, lam, beta, seed, t, 0, mode)
+    assert np.array_equal(got, o)
+
+
+def test_reversed_order_graph(S):
+    n, R = 500, 32
+    u, v = W.erdos_renyi(n, 6.0, 3)
+    J = W.couplings_pm1(u.size, 4)
+    lam = W.fields_normal(n, 0.1, 5)
+    seed = 77
+    ctx = S.shaken_init(graph_problem(S, n, u, v, J, R, 0.9, q=1.0, lam=lam), seed)
+    S.shaken_set_order(ctx, True)
+    S.shaken_step(ctx, 4)
+    got = S.shaken_get_spins(ctx, R, n)
+    S.shaken_free(ctx)
+    tail, head = core.orient(u, v, 0)
+    o = core.graph_init(n, R, seed, 0)
+    for t in range(4):
+        sp = core.graph_half(o, tail, head, J.astype(np.float64), True, lam.astype(np.float64),
+                             1.0, 0.9, seed, t, 1)
+        o = core.graph_half(sp, tail, head, J.astype(np.float64), True, lam.astype(np.float64),
+                            1.0, 0.9, seed, t, 0)
+    assert np.array_equal(got, o)
+
+
+def _chi2_pvalue(counts, probs, nrep):
+    exp_ = probs * nrep
+    big = exp_ >= 5
+    obs = np.append(counts[big], counts[~big].sum())
+    ex = np.append(exp_[big], exp_[~big].sum())
+    if ex[-1] == 0:
+        obs, ex = obs[:-1], ex[:-1]
+    return stats.chisquare(obs, ex * obs.sum() / ex.sum()).pvalue
+
+
+@pytest.mark.parametrize("frac", [0.5, 0.25])
+def test_generalised_split_follows_exact_law(S, frac):
+    n, R = 6, 32 * 256
+    u = np.array([0, 1, 2, 3, 4, 5, 0, 2], dtype=np.int32)
+    v = np.array([1, 2, 3, 4, 5, 0, 3, 5], dtype=np.int32)
+    g = np.random.default_rng(2)
+    J = g.standard_normal(8).astype(np.float32)
+    lam = (0.3 * g.standard_normal(n)).astype(np.float32)
+    uu, vv, JJ = W.split_both_ways(u, v, J, frac)
+    q, beta = 0.8, 0.7
+    s0 = np.array([1, -1, 1, 1, -1, -1], dtype=np.int8)
+    Sx = exact.states(n)
+    Jo = exact.oriented_matrix(n, uu, vv, JJ.astype(np.float64))
+    P = exact.shaken_matrix(Sx, Jo, lam.astype(np.float64), q, beta)
+    mu0 = np.zeros(Sx.shape[0])
+    mu0[exact.state_index(s0)] = 1.0
+    for t in (1, 2):
+        init = np.broadcast_to(s0, (R, n)).copy()
+        ctx = S.shaken_init(graph_problem(S, n, uu, vv, JJ, R, beta, q=q, lam=lam, integer=False,
+                                          orientation=S.ORIENT_GIVEN, init=S.INIT_GIVEN,
+                                          init_spins=init), 1000 + t)
+        S.shaken_step(ctx, t)
+        st = S.shaken_get_spins(ctx, R, n)
+        S.shaken_free(ctx)
+        counts = np.bincount(exact.state_index(st), minlength=Sx.shape[0]).astype(float)
+        assert _chi2_pvalue(counts, exact.evolve(mu0, P, t), R) > 1e-4
+
+
+def test_triangular_lattice_bit_exact(S):
+    L, R = 12, 64
+    u, v = W.triangular_lattice_as_graph(L)
+    J = np.ones(u.size, dtype=np.float32)
+    seed = 5
+    ctx = S.shaken_init(graph_problem(S, L * L, u, v, J, R, W.beta_grid(R, 0.1, 0.6, 16), q=0.6,
+                                      lam_c=0.0, orientation=S.ORIENT_GIVEN), seed)
+    S.shaken_step(ctx, 5)
+    got = S.shaken_get_spins(ctx, R, L * L)
+    S.shaken_free(ctx)
+    tail, head = core.orient(u, v, 2)
+    o = core.graph_init(L * L, R, seed, 0)
+    o, _ = core.graph_run(o, tail, head, J.astype(np.float64), True, 0.0, 0.6,
+                          W.beta_grid(R, 0.1, 0.6, 16), seed, 0, 5)
+    assert np.array_equal(got, o)

@@ -174,3 +174,36 @@ def test_reversed_order_same_measure():
     pi2 /= pi2.sum()
     F = pi2[:, None] * P2
     assert np.abs(F - F.T).max() < 1e-14
+
+
+def test_generalised_split_is_reversible():
+    # Sec. 5: J = J^o + J^oT with both orientations weighted; Thm 2.1 extends
+    n = 5
+    u = np.array([0, 1, 2, 3, 0, 1])
+    v = np.array([1, 2, 3, 4, 4, 3])
+    g = np.random.default_rng(4)
+    J = g.standard_normal(6)
+    lam = 0.2 * g.standard_normal(n)
+    tails = np.concatenate([u, v])
+    heads = np.concatenate([v, u])
+    Jsplit = np.concatenate([0.3 * J, 0.7 * J])
+    S = exact.states(n)
+    Jo = exact.oriented_matrix(n, tails, heads, Jsplit)
+    P = exact.shaken_matrix(S, Jo, lam, 0.9, 0.8)
+    pi = exact.stationary(S, tails, heads, Jsplit, lam, 0.9, 0.8)
+    assert np.abs(pi @ P - pi).max() < 1e-14
+    F = pi[:, None] * P
+    assert np.abs(F - F.T).max() < 1e-15
+    # H(sigma, sigma) = H(sigma) - q|V| with H over the undirected couplings
+    Hs = exact.hamiltonian(S, u, v, J, lam)
+    Hp = exact.pair_hamiltonian(S, S, tails, heads, Jsplit, lam, 0.9)
+    assert np.abs(Hp - (Hs - 0.9 * n)).max() < 1e-12
+
+
+def test_triangular_critical_curve_reduces_to_square_at_q_equal_J():
+    # Thm 4.1: 1 + tanh^3 J tanh q = 3 tanh J tanh q + 3 tanh^2 J; at q = J the
+    # root is the square-lattice (Onsager) point tanh J = sqrt(2) - 1
+    from scipy.optimize import brentq
+    f = lambda x: 1 + np.tanh(x) ** 4 - 3 * np.tanh(x) ** 2 - 3 * np.tanh(x) ** 2
+    Jc = brentq(f, 0.1, 1.0)
+    assert abs(np.tanh(Jc) - (np.sqrt(2) - 1)) < 1e-12
