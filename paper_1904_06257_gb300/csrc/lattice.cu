@@ -802,8 +802,8 @@ static cudaError_t launch_half_t(const LatJob* jobs, const Tile* tiles, int n_ti
 
 int lattice_resident_blocks() {
   int o = 1, dev = 0, sms = 152;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lattice_half_kernel<kEncMultispin, 4>, kTile,
-                                                0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lattice_half_kernel<kEncMultispin, kWordsPerThread>,
+                                                kTile, 0);
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   return (o > 0 ? o : 1) * sms;
@@ -813,11 +813,13 @@ cudaError_t launch_lattice_half(int enc, int wpt, const LatJob* jobs, const Tile
                                 int n_tiles, uint32_t half, unsigned long long* rng_calls,
                                 cudaStream_t st) {
   if (n_tiles <= 0) return cudaSuccess;
-  if (wpt == 4) {
-    if (enc == kEncInt8) return launch_half_t<kEncInt8, 4>(jobs, tiles, n_tiles, half, rng_calls, st);
+  if (wpt == kWordsPerThread) {
+    if (enc == kEncInt8)
+      return launch_half_t<kEncInt8, kWordsPerThread>(jobs, tiles, n_tiles, half, rng_calls, st);
     if (enc == kEncPacked)
-      return launch_half_t<kEncPacked, 4>(jobs, tiles, n_tiles, half, rng_calls, st);
-    return launch_half_t<kEncMultispin, 4>(jobs, tiles, n_tiles, half, rng_calls, st);
+      return launch_half_t<kEncPacked, kWordsPerThread>(jobs, tiles, n_tiles, half, rng_calls, st);
+    return launch_half_t<kEncMultispin, kWordsPerThread>(jobs, tiles, n_tiles, half, rng_calls,
+                                                         st);
   }
   if (enc == kEncInt8) return launch_half_t<kEncInt8, 1>(jobs, tiles, n_tiles, half, rng_calls, st);
   if (enc == kEncPacked)
