@@ -239,8 +239,13 @@ shaken_status shaken_batch_set_rng_counter(shaken_batch* b, uint64_t* device_cou
 
 /* Device microbenchmarks on the current GPU (all SMs, register-only work):
  * kind 0 = Philox-4x32-10 calls per second, 1 = 32-bit LOP3 per second,
- * 2 = 32-bit IMAD per second.  *rate receives the rate, *ms (optional) the
- * timed duration. */
+ * 2 = 32-bit IMAD per second, 3 = LOP3 and IMAD interleaved (operations per
+ * second, both kinds counted), 4 = 32 x 32 -> 64-bit multiply-adds per second,
+ * 5 = 32 x 32 -> 64-bit products per second, 6 = products and LOP3
+ * interleaved (operations per second, both kinds counted), 7 = Philox-4x32-10
+ * calls per second with each product as separate high and low multiplies.
+ * *rate receives the rate, *ms (optional) the timed duration.  Unknown kind:
+ * SHAKEN_E_INVAL. */
 shaken_status shaken_microbench(int kind, double* rate, double* ms);
 void shaken_batch_free(shaken_batch* b);
 

@@ -96,26 +96,43 @@ struct LaneWord {
   uint32_t S, V, X, U, res;  // U = lanes still undecided
 };
 
-// Threshold bit of plane j for every lane: first select by sigma within each
-// n-class, then by n: 5 three-input selects.
-__device__ __forceinline__ uint32_t plane_bits(const LaneWord& L, const uint32_t* tm) {
-  const uint4 lo = *reinterpret_cast<const uint4*>(tm);      // classes 0..3
-  const uint2 hi = *reinterpret_cast<const uint2*>(tm + 4);  // classes 4, 5
-  const uint32_t b0 = (L.S & lo.y) | (~L.S & lo.x);  // n = 0
-  const uint32_t b1 = (L.S & lo.w) | (~L.S & lo.z);  // n = 1
-  const uint32_t b2 = (L.S & hi.y) | (~L.S & hi.x);  // n = 2
-  const uint32_t m = (L.V & b2) | (~L.V & b0);       // V == H
-  return (L.X & b1) | (~L.X & m);
+// One plane of a threshold table, read from shared memory once and applied to
+// every lane word of the thread.
+struct PlaneRow {
+  uint4 lo;  // classes 0..3 (collapsed: c = 0..3)
+  uint2 hi;  // classes 4, 5 (unused when collapsed)
+};
+
+template <bool COLL>
+__device__ __forceinline__ PlaneRow plane_row(const LatTable& tab, int j) {
+  PlaneRow r;
+  if (COLL) {
+    r.lo = *reinterpret_cast<const uint4*>(&tab.tmc[j][0]);
+    r.hi = make_uint2(0u, 0u);
+  } else {
+    r.lo = *reinterpret_cast<const uint4*>(&tab.tm[j][0]);
+    r.hi = *reinterpret_cast<const uint2*>(&tab.tm[j][4]);
+  }
+  return r;
 }
 
+// Threshold bit of plane j for every lane: first select by sigma within each
+// n-class, then by n: 5 three-input selects.
 // Collapsed tables (thresholds by c = n + s): with c0 = parity and c1 =
-// majority of (V, H, S), c = c0 + 2 c1 and the plane bit is 3 selects.
-// Here L.V holds c1 and L.X holds c0.
-__device__ __forceinline__ uint32_t plane_bits_c(const LaneWord& L, const uint32_t* tmc) {
-  const uint4 t = *reinterpret_cast<const uint4*>(tmc);
-  const uint32_t lo = (L.X & t.y) | (~L.X & t.x);  // c1 = 0
-  const uint32_t hi = (L.X & t.w) | (~L.X & t.z);  // c1 = 1
-  return (L.V & hi) | (~L.V & lo);
+// majority of (V, H, S), c = c0 + 2 c1 and the plane bit is 3 selects; there
+// L.V holds c1 and L.X holds c0.
+template <bool COLL>
+__device__ __forceinline__ uint32_t plane_bits(const LaneWord& L, const PlaneRow& r) {
+  if (COLL) {
+    const uint32_t lo = (L.X & r.lo.y) | (~L.X & r.lo.x);  // c1 = 0
+    const uint32_t hi = (L.X & r.lo.w) | (~L.X & r.lo.z);  // c1 = 1
+    return (L.V & hi) | (~L.V & lo);
+  }
+  const uint32_t b0 = (L.S & r.lo.y) | (~L.S & r.lo.x);  // n = 0
+  const uint32_t b1 = (L.S & r.lo.w) | (~L.S & r.lo.z);  // n = 1
+  const uint32_t b2 = (L.S & r.hi.y) | (~L.S & r.hi.x);  // n = 2
+  const uint32_t m = (L.V & b2) | (~L.V & b0);           // V == H
+  return (L.X & b1) | (~L.X & m);
 }
 
 // MSB-first comparison of u_k with T_k over the four planes of one Philox call.
@@ -125,8 +142,7 @@ __device__ __forceinline__ void apply_call(LaneWord& L, const uint4 w, const Lat
   const uint32_t Wj[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const uint32_t P = COLL ? plane_bits_c(L, &tab.tmc[4 * call + i][0])
-                            : plane_bits(L, &tab.tm[4 * call + i][0]);
+    const uint32_t P = plane_bits<COLL>(L, plane_row<COLL>(tab, 4 * call + i));
     const uint32_t diff = (Wj[i] ^ P) & L.U;  // first plane where u and T differ
     L.res |= diff & P;                        // T has the 1 there: u < T
     L.U &= ~diff;
@@ -174,6 +190,62 @@ __device__ __forceinline__ void decide_head(LaneWord& L, const LatTable& tab, co
   calls += 2;
   apply_call<COLL>(L, w0, tab, 0u);
   apply_call<COLL>(L, w1, tab, 1u);
+}
+
+// Planes 31..24 (calls 0 and 1) of the thread's WPT lane words, plane-major:
+// every table row is read once for all the words, and the WPT Philox calls of
+// a group are independent of one another.  The top eight bits of u_k and T_k
+// are compared as an eight-bit subtraction, least significant plane first:
+// the borrow lt <- maj(~w, P, lt) ends as [u_top < T_top] and eq as
+// [u_top == T_top].  Lanes with equal top bits stay undecided for planes 23..0
+// (decide_tail); the others are decided exactly as by the first differing plane.
+// Four planes of one call (planes 4c+3 .. 4c, least significant first) for
+// the WPT words: one step of the borrow chain per plane.
+template <bool COLL, int WPT>
+__device__ __forceinline__ void head_planes(const LaneWord (&Lw)[WPT], const LatTable& tab,
+                                            int call, const uint4 (&W)[WPT], uint32_t (&lt)[WPT],
+                                            uint32_t (&eq)[WPT]) {
+#pragma unroll
+  for (int i = 3; i >= 0; --i) {
+    const PlaneRow r = plane_row<COLL>(tab, 4 * call + i);
+#pragma unroll
+    for (int k = 0; k < WPT; ++k) {
+      const uint32_t w = i == 0 ? W[k].x : i == 1 ? W[k].y : i == 2 ? W[k].z : W[k].w;
+      const uint32_t P = plane_bits<COLL>(Lw[k], r);
+      lt[k] = (~w & P) | (~w & lt[k]) | (P & lt[k]);
+      eq[k] &= ~(w ^ P);
+    }
+  }
+}
+
+template <int WPT>
+__device__ __forceinline__ void head_finish(LaneWord (&Lw)[WPT], const uint32_t (&lt)[WPT],
+                                            const uint32_t (&eq)[WPT]) {
+#pragma unroll
+  for (int k = 0; k < WPT; ++k) {
+    Lw[k].res |= Lw[k].U & ~eq[k] & lt[k];
+    Lw[k].U &= eq[k];
+  }
+}
+
+template <bool COLL, int WPT>
+__device__ __forceinline__ void decide_head_words(LaneWord (&Lw)[WPT], const LatTable& tab,
+                                                  const PhKey& K, const uint32_t (&a)[WPT],
+                                                  uint32_t b, uint32_t t, uint32_t half) {
+  uint32_t lt[WPT], eq[WPT];
+#pragma unroll
+  for (int k = 0; k < WPT; ++k) {
+    lt[k] = 0u;
+    eq[k] = 0xffffffffu;
+  }
+#pragma unroll
+  for (int call = 1; call >= 0; --call) {
+    uint4 W[WPT];
+#pragma unroll
+    for (int k = 0; k < WPT; ++k) W[k] = ph_call(K, a[k], b, t, half + 2u * (uint32_t)call);
+    head_planes<COLL, WPT>(Lw, tab, call, W, lt, eq);
+  }
+  head_finish<WPT>(Lw, lt, eq);
 }
 
 // Calls 2..7 while some lane is undecided.
@@ -248,7 +320,15 @@ __device__ __forceinline__ void word_rc(const LatJob& J, uint32_t w, uint32_t& i
 // Loads the three lane words a decision needs from buffer src: S (own), V (the
 // vertical in-neighbour row: i-1 for half 0, i+1 for half 1) and H (the
 // horizontal in-neighbour: j-1 for half 0, j+1 for half 1).
-template <int ENC>
+// NC: buf is a global buffer not written during the launch (read through the
+// non-coherent cache); otherwise a plain load (shared memory).
+template <bool NC, typename T>
+__device__ __forceinline__ T ld_ro(const T* p) {
+  if (NC) return __ldg(p);
+  return *p;
+}
+
+template <int ENC, bool NC = true>
 __device__ __forceinline__ void load_lane_words(const LatJob& J, const void* buf, uint32_t w,
                                                 uint32_t half, uint32_t& S, uint32_t& V,
                                                 uint32_t& H) {
@@ -260,30 +340,31 @@ __device__ __forceinline__ void load_lane_words(const LatJob& J, const void* buf
     const uint8_t* A = static_cast<const uint8_t*>(buf);
     const uint4* own = reinterpret_cast<const uint4*>(A + (size_t)i * L + 32u * c);
     const uint4* ver = reinterpret_cast<const uint4*>(A + (size_t)iv * L + 32u * c);
-    const uint4 o0 = own[0], o1 = own[1], v0 = ver[0], v1 = ver[1];
+    const uint4 o0 = ld_ro<NC>(own), o1 = ld_ro<NC>(own + 1), v0 = ld_ro<NC>(ver),
+                v1 = ld_ro<NC>(ver + 1);
     const uint32_t jn = half == 0u ? (c == 0u ? L - 1u : 32u * c - 1u)
                                    : (32u * c + 32u == L ? 0u : 32u * c + 32u);
-    const uint32_t nb = (A[(size_t)i * L + jn] >> 7) ^ 1u;  // 1 if +1
+    const uint32_t nb = (ld_ro<NC>(A + (size_t)i * L + jn) >> 7) ^ 1u;  // 1 if +1
     S = bits16(o0) | (bits16(o1) << 16);
     V = bits16(v0) | (bits16(v1) << 16);
     H = half == 0u ? ((S << 1) | nb) : ((S >> 1) | (nb << 31));
   } else if (ENC == kEncPacked) {
     const uint32_t* A = static_cast<const uint32_t*>(buf);
-    S = A[(size_t)i * wpr + c];
-    V = A[(size_t)iv * wpr + c];
+    S = ld_ro<NC>(A + (size_t)i * wpr + c);
+    V = ld_ro<NC>(A + (size_t)iv * wpr + c);
     if (half == 0u) {
       const uint32_t cl = c == 0u ? wpr - 1u : c - 1u;
-      H = (S << 1) | (A[(size_t)i * wpr + cl] >> 31);
+      H = (S << 1) | (ld_ro<NC>(A + (size_t)i * wpr + cl) >> 31);
     } else {
       const uint32_t cr = c + 1u == wpr ? 0u : c + 1u;
-      H = (S >> 1) | (A[(size_t)i * wpr + cr] << 31);
+      H = (S >> 1) | (ld_ro<NC>(A + (size_t)i * wpr + cr) << 31);
     }
   } else {
     const uint32_t* A = static_cast<const uint32_t*>(buf);
     const uint32_t jn = half == 0u ? (c == 0u ? L - 1u : c - 1u) : (c + 1u == L ? 0u : c + 1u);
-    S = A[w];
-    V = A[(size_t)iv * L + c];
-    H = A[(size_t)i * L + jn];
+    S = ld_ro<NC>(A + w);
+    V = ld_ro<NC>(A + (size_t)iv * L + c);
+    H = ld_ro<NC>(A + (size_t)i * L + jn);
   }
 }
 
@@ -321,32 +402,30 @@ __device__ __forceinline__ void store_word(const LatJob& J, void* dstbuf, uint32
   }
 }
 
-// Decisions of one tile: planes 31..24 of each of the thread's WPT lane words,
-// words with undecided lanes parked in the warp's queue, then the queue
-// finished 32 words at a time.  FULL: every word of the tile exists.
+// After the head: words with undecided lanes go to the warp's queue, the others
+// are stored; then the queue is finished 32 words at a time (planes 23..0).
+// With sh.fuse the sums of sigma_t over the words are accumulated as well.
 template <int ENC, int WPT, bool COLL, bool FULL>
-__device__ __forceinline__ void tile_decide(const LatJob& J, const TileShared& sh,
-                                            Pending* __restrict__ q, const PhKey& K, uint32_t w0,
-                                            uint32_t t, uint32_t half, const uint32_t (&S)[WPT],
-                                            const uint32_t (&V)[WPT], const uint32_t (&H)[WPT],
-                                            const uint32_t (&F)[WPT], void* dstbuf,
-                                            double (&acc)[3], uint32_t& calls) {
+__device__ __forceinline__ void tile_commit(const LatJob& J, const TileShared& sh,
+                                            Pending* __restrict__ q,
+                                            const uint32_t (&a)[WPT], uint32_t t, uint32_t half,
+                                            const uint32_t (&S)[WPT], const uint32_t (&V)[WPT],
+                                            const uint32_t (&H)[WPT], const LaneWord (&Lws)[WPT],
+                                            void* dstbuf, double (&acc)[3], uint32_t& calls) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt_mask = (1u << lane) - 1u;
   uint32_t qn = 0;  // warp-uniform queue length
 #pragma unroll
   for (int k = 0; k < WPT; ++k) {
-    const uint32_t w = w0 + threadIdx.x + k * kTile;
+    const uint32_t w = a[k];
     const bool act = FULL || w < J.nwords;
-    LaneWord Lw = classify<COLL>(S[k], V[k], H[k], F[k], sh.tab);
-    if (!FULL && !act) Lw.U = 0u;
-    decide_head<COLL>(Lw, sh.tab, K, w, J.b, t, half, calls);
+    const LaneWord& Lw = Lws[k];
     const bool pend = act && Lw.U != 0u;
     const uint32_t pm = __ballot_sync(0xffffffffu, pend);
     if (pend) {
       Pending& e = q[qn + __popc(pm & lt_mask)];
       e.w = w;
-      e.S = Lw.S;
+      e.S = COLL ? 0u : Lw.S;  // the collapsed planes do not use sigma
       e.V = Lw.V;
       e.X = Lw.X;
       e.U = Lw.U;
@@ -355,7 +434,7 @@ __device__ __forceinline__ void tile_decide(const LatJob& J, const TileShared& s
       store_word<ENC>(J, dstbuf, w, Lw.res);
     }
     qn += __popc(pm);
-    if (sh.fuse && act) {
+    if (ENC != kEncMultispin && sh.fuse && act) {
       // sums of sigma_t over the lane word: M, E (in-edges down and left), cut
       const int dv = __popc(S[k] ^ V[k]), dh = __popc(S[k] ^ H[k]);
       acc[0] += (double)(2 * __popc(S[k]) - 32);
@@ -364,6 +443,8 @@ __device__ __forceinline__ void tile_decide(const LatJob& J, const TileShared& s
     }
   }
   __syncwarp();
+  if (qn == 0u) return;
+  const PhKey K = ph_key(J.key0, J.key1);
   for (uint32_t base = 0; base < qn; base += 32u) {
     if (base + lane < qn) {
       const Pending e = q[base + lane];
@@ -380,6 +461,29 @@ __device__ __forceinline__ void tile_decide(const LatJob& J, const TileShared& s
   __syncwarp();
 }
 
+// Decisions of one tile: planes 31..24 of each of the thread's WPT lane words,
+// words with undecided lanes parked in the warp's queue, then the queue
+// finished 32 words at a time.  FULL: every word of the tile exists.
+template <int ENC, int WPT, bool COLL, bool FULL>
+__device__ __forceinline__ void tile_decide(const LatJob& J, const TileShared& sh,
+                                            Pending* __restrict__ q, const PhKey& K, uint32_t w0,
+                                            uint32_t t, uint32_t half, const uint32_t (&S)[WPT],
+                                            const uint32_t (&V)[WPT], const uint32_t (&H)[WPT],
+                                            const uint32_t (&F)[WPT], void* dstbuf,
+                                            double (&acc)[3], uint32_t& calls) {
+  LaneWord Lws[WPT];
+  uint32_t a[WPT];
+#pragma unroll
+  for (int k = 0; k < WPT; ++k) {
+    a[k] = w0 + threadIdx.x + k * kTile;
+    Lws[k] = classify<COLL>(S[k], V[k], H[k], F[k], sh.tab);
+    if (!FULL && a[k] >= J.nwords) Lws[k].U = 0u;
+  }
+  decide_head_words<COLL, WPT>(Lws, sh.tab, K, a, J.b, t, half);
+  calls += 2u * WPT;
+  tile_commit<ENC, WPT, COLL, FULL>(J, sh, q, a, t, half, S, V, H, Lws, dstbuf, acc, calls);
+}
+
 // Each block walks a contiguous range of tiles (kLatTile lane words each; a
 // tile never spans two jobs).  Per tile every thread loads the words of its
 // kWordsPerThread lane words (all loads in flight together) and runs planes
@@ -387,7 +491,7 @@ __device__ __forceinline__ void tile_decide(const LatJob& J, const TileShared& s
 // queue and finished afterwards 32 at a time, so the warp pays the rare later
 // planes once per 32 such words instead of once per word position.
 template <int ENC, int WPT>
-__global__ void __launch_bounds__(kTile, 3) lattice_half_kernel(const LatJob* __restrict__ jobs,
+__global__ void __launch_bounds__(kTile, kLatMinBlocks) lattice_half_kernel(const LatJob* __restrict__ jobs,
                                                                 const Tile* __restrict__ tiles,
                                                                 int n_tiles, uint32_t half,
                                                                 unsigned long long* rng_calls) {
@@ -448,7 +552,7 @@ __global__ void __launch_bounds__(kTile, 3) lattice_half_kernel(const LatJob* __
       F[k] = 0u;
       if (w < J.nwords) {
         load_lane_words<ENC>(J, src, w, typ, S[k], V[k], H[k]);
-        if (J.frozen != nullptr) F[k] = J.frozen[w];
+        if (J.frozen != nullptr) F[k] = __ldg(J.frozen + w);
       }
     }
     const PhKey K = ph_key(J.key0, J.key1);
@@ -710,7 +814,7 @@ __global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* _
       uint32_t* out = pos == 0u ? sB : sA;
       for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) {
         uint32_t S, V, H;
-        load_lane_words<SENC>(J, in, w, half, S, V, H);
+        load_lane_words<SENC, false>(J, in, w, half, S, V, H);
         const uint32_t F = J.frozen != nullptr ? J.frozen[w] : 0u;
         LaneWord Lw;
         if (stab.collapsed) {

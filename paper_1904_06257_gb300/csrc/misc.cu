@@ -102,7 +102,8 @@ __global__ void __launch_bounds__(256) mb_lop3_kernel(uint32_t iters, uint32_t* 
   const uint32_t m = blockIdx.x | 0x01010101u, n = threadIdx.x ^ 0x5a5a5a5au;
   for (uint32_t i = 0; i < iters; ++i) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) a[k] = (a[k] ^ m) & (a[k] | n);
+    for (int k = 0; k < 8; ++k)  // one three-input logic instruction: (a ^ m) & (a | n)
+      asm volatile("lop3.b32 %0, %1, %2, %3, 0x38;" : "=r"(a[k]) : "r"(a[k]), "r"(m), "r"(n));
   }
   uint32_t acc = 0;
 #pragma unroll
@@ -126,7 +127,129 @@ __global__ void __launch_bounds__(256) mb_imad_kernel(uint32_t iters, uint32_t* 
   if (acc == 0x5eedu) sink[0] = acc;
 }
 
+// 4 chains of LOP3 interleaved with 4 chains of IMAD: if the logic and the
+// multiply-add pipes overlapped, this would run at the sum of the two rates.
+__global__ void __launch_bounds__(256) mb_mix_kernel(uint32_t iters, uint32_t* sink) {
+  uint32_t a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = threadIdx.x * (k + 3) + blockIdx.x;
+  const uint32_t m = blockIdx.x | 0x01010101u, n = threadIdx.x ^ 0x5a5a5a5au;
+  for (uint32_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      asm volatile("lop3.b32 %0, %1, %2, %3, 0x38;" : "=r"(a[k]) : "r"(a[k]), "r"(m), "r"(n));
+      a[k + 4] = a[k + 4] * m + n;
+    }
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc ^= a[k];
+  if (acc == 0x5eedu) sink[0] = acc;
+}
+
+// 8 chains of 32 x 32 -> 64-bit multiply-adds (the Philox multiply).
+__global__ void __launch_bounds__(256) mb_imad_wide_kernel(uint32_t iters, uint32_t* sink) {
+  unsigned long long p[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) p[k] = threadIdx.x * (k + 3) + blockIdx.x;
+  const uint32_t m = blockIdx.x * 2u + 0xD2511F53u;
+  for (uint32_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t a = (uint32_t)(p[k] >> 32);
+      asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(p[k]) : "r"(a), "r"(m));
+    }
+  }
+  unsigned long long acc = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc ^= p[k];
+  if (acc == 0x5eedull) sink[0] = (uint32_t)acc;
+}
+
+// 8 chains of 32 x 32 -> 64-bit products without an addend (the form of the
+// Philox multiply): both halves of each product feed the next one.
+__global__ void __launch_bounds__(256) mb_mul_wide_kernel(uint32_t iters, uint32_t* sink) {
+  uint32_t a[8], b[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    a[k] = threadIdx.x * (k + 3) + blockIdx.x;
+    b[k] = 0xD2511F53u + k;
+  }
+  for (uint32_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      unsigned long long p;
+      asm volatile("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a[k]), "r"(b[k]));
+      a[k] = (uint32_t)p;
+      b[k] = (uint32_t)(p >> 32);
+    }
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc ^= a[k] ^ b[k];
+  if (acc == 0x5eedu) sink[0] = acc;
+}
+
+// 4 chains of 64-bit products interleaved with 4 chains of LOP3.
+__global__ void __launch_bounds__(256) mb_mix_wide_kernel(uint32_t iters, uint32_t* sink) {
+  uint32_t a[4], b[4], c[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    a[k] = threadIdx.x * (k + 3) + blockIdx.x;
+    b[k] = 0xD2511F53u + k;
+    c[k] = threadIdx.x ^ (k * 0x01234567u);
+  }
+  const uint32_t m = blockIdx.x | 0x01010101u, n = threadIdx.x ^ 0x5a5a5a5au;
+  for (uint32_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      unsigned long long p;
+      asm volatile("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a[k]), "r"(b[k]));
+      a[k] = (uint32_t)p;
+      b[k] = (uint32_t)(p >> 32);
+      asm volatile("lop3.b32 %0, %1, %2, %3, 0x38;" : "=r"(c[k]) : "r"(c[k]), "r"(m), "r"(n));
+    }
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) acc ^= a[k] ^ b[k] ^ c[k];
+  if (acc == 0x5eedu) sink[0] = acc;
+}
+
+// Philox-4x32-10 with each 32 x 32 -> 64-bit product split into a high and a
+// low 32-bit multiply (same values as ph_call), chained like mb_philox_kernel.
+__device__ __forceinline__ uint4 ph_call_split(const PhKey& K, uint32_t c0, uint32_t c1,
+                                               uint32_t c2, uint32_t c3) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t h0, l0, h1, l1;
+    asm volatile("mul.hi.u32 %0, %1, %2;" : "=r"(h0) : "r"(c0), "n"(kPhM0));
+    asm volatile("mul.lo.u32 %0, %1, %2;" : "=r"(l0) : "r"(c0), "n"(kPhM0));
+    asm volatile("mul.hi.u32 %0, %1, %2;" : "=r"(h1) : "r"(c2), "n"(kPhM1));
+    asm volatile("mul.lo.u32 %0, %1, %2;" : "=r"(l1) : "r"(c2), "n"(kPhM1));
+    const uint32_t n0 = h1 ^ c1 ^ K.k0[r];
+    const uint32_t n2 = h0 ^ c3 ^ K.k1[r];
+    c1 = l1;
+    c3 = l0;
+    c0 = n0;
+    c2 = n2;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+__global__ void __launch_bounds__(256) mb_philox_split_kernel(uint32_t iters, uint32_t* sink) {
+  const PhKey K = ph_key(0x1234u + threadIdx.x, 0x9876u ^ blockIdx.x);
+  uint4 c = make_uint4(threadIdx.x, blockIdx.x, 7u, 9u);
+  uint32_t acc = 0u;
+  for (uint32_t i = 0; i < iters; ++i) {
+    c = ph_call_split(K, c.x, c.y, c.z + i, c.w);
+    acc ^= c.x ^ c.y ^ c.z ^ c.w;
+  }
+  if (acc == 0x5eedu) sink[0] = acc;
+}
+
 cudaError_t run_microbench(int kind, double* rate, double* ms_out) {
+  if (kind < 0 || kind > 7) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -137,14 +260,24 @@ cudaError_t run_microbench(int kind, double* rate, double* ms_out) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const uint32_t iters = kind == 0 ? 4096u : 65536u;
+  const uint32_t iters = (kind == 0 || kind == 7) ? 4096u : 65536u;
   auto launch = [&]() {
     if (kind == 0)
       mb_philox_kernel<<<grid, block>>>(iters, sink);
     else if (kind == 1)
       mb_lop3_kernel<<<grid, block>>>(iters, sink);
-    else
+    else if (kind == 2)
       mb_imad_kernel<<<grid, block>>>(iters, sink);
+    else if (kind == 3)
+      mb_mix_kernel<<<grid, block>>>(iters, sink);
+    else if (kind == 4)
+      mb_imad_wide_kernel<<<grid, block>>>(iters, sink);
+    else if (kind == 5)
+      mb_mul_wide_kernel<<<grid, block>>>(iters, sink);
+    else if (kind == 6)
+      mb_mix_wide_kernel<<<grid, block>>>(iters, sink);
+    else
+      mb_philox_split_kernel<<<grid, block>>>(iters, sink);
   };
   launch();  // warm-up
   cudaEventRecord(e0);
@@ -154,7 +287,7 @@ cudaError_t run_microbench(int kind, double* rate, double* ms_out) {
   float ms = 0.0f;
   if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
   if (e == cudaSuccess) e = cudaGetLastError();
-  const double work = 5.0 * grid * block * (double)iters * (kind == 0 ? 1.0 : 8.0);
+  const double work = 5.0 * grid * block * (double)iters * ((kind == 0 || kind == 7) ? 1.0 : 8.0);
   *rate = ms > 0.0f ? work / (ms * 1e-3) : 0.0;
   if (ms_out) *ms_out = ms;
   cudaEventDestroy(e0);

@@ -1274,6 +1274,7 @@ shaken_status shaken_batch_set_rng_counter(shaken_batch* b, uint64_t* device_cou
 
 shaken_status shaken_microbench(int kind, double* rate, double* ms) {
   if (!rate) return fail(SHAKEN_E_INVAL, "rate is NULL");
+  if (kind < 0 || kind > 7) return fail(SHAKEN_E_INVAL, "unknown microbenchmark kind");
   CU(shk::run_microbench(kind, rate, ms));
   return SHAKEN_OK;
 }

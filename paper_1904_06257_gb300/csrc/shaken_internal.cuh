@@ -32,6 +32,7 @@ constexpr uint32_t kInitStep = 0xFFFFFFFFu;  // step index of the initial draw
 constexpr int kTile = 256;  // threads per block; graph tiles hold kTile vertices
 constexpr int kWordsPerThread = 4;                   // lattice lane words per thread and tile
 constexpr int kLatTile = kTile * kWordsPerThread;    // lattice lane words per tile
+constexpr int kLatMinBlocks = 3;                     // resident blocks per SM of the half-step kernel
 
 // ---------------------------------------------------------------- Philox-4x32-10
 struct PhKey {
