@@ -237,6 +237,29 @@ shaken_status shaken_batch_launch_count(shaken_batch* b, uint64_t* count);
  * are decided).  NULL switches counting off. */
 shaken_status shaken_batch_set_rng_counter(shaken_batch* b, uint64_t* device_counter);
 
+/* Autotuner of the lattice launch shape.  For every lattice encoding family of
+ * a plan (a batch, or a context stepped on its own) the half-step kernel runs
+ * with tiles of 256 lane words (one per thread) or 1024 (four per thread).
+ * With autotuning on (the default) a family of at least one resident wave of
+ * 1024-word tiles is timed once with both shapes -- trial launches of the
+ * first half step that rewrite sigma' with the values the real step writes,
+ * so no trajectory changes -- and the faster shape is cached per (encoding,
+ * bit length of the lane-word count, bit length of the job count).  Off: a
+ * fixed rule (four words per thread once the family fills eight waves).
+ * Trajectories are bit-identical under every shape.
+ * lattice_wpt returns the words per thread the plan uses for an encoding
+ * (SHAKEN_INT8 / SHAKEN_PACKED / SHAKEN_MULTISPIN), 0 if the plan has no such
+ * family; it builds the plan (and may run the trials) if needed.  A context
+ * that belongs to a batch: SHAKEN_E_STATE.  autotune_stats: number of tuning
+ * searches run and of cached results in this process; autotune_clear empties
+ * the cache. */
+shaken_status shaken_batch_set_autotune(shaken_batch* b, int on);
+shaken_status shaken_set_autotune(shaken_ctx* ctx, int on);
+shaken_status shaken_batch_lattice_wpt(shaken_batch* b, int encoding, int* words_per_thread);
+shaken_status shaken_lattice_wpt(shaken_ctx* ctx, int* words_per_thread);
+shaken_status shaken_autotune_stats(uint64_t* trials, uint64_t* cached);
+shaken_status shaken_autotune_clear(void);
+
 /* Device microbenchmarks on the current GPU (all SMs, register-only work):
  * kind 0 = Philox-4x32-10 calls per second, 1 = 32-bit LOP3 per second,
  * 2 = 32-bit IMAD per second, 3 = LOP3 and IMAD interleaved (operations per

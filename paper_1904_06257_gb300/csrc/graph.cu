@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kTile) graph_half_kernel(const GraphJob* __res
       t = cd->step;
       typ = half ^ cd->order;
       skip = t >= cd->t_end;
-      fuse = !skip && half == 0u && cd->tracking && !cd->record;
+      fuse = !skip && half == 0u && cd->tracking && !cd->record && J.sums != nullptr;
       fuse_dst = J.sums;
       if (threadIdx.x < 32) {
         double beta;

@@ -143,6 +143,7 @@ struct Plan {
   int graph_steps = 0;
   uint64_t graph_launches = 0;
   bool dirty = true;
+  bool autotune = true;  // pick the lattice tile shape by timing trial launches
   int blocks_per_sm = 8;
   bool timing = false;
   unsigned long long* rng_counter = nullptr;  // device counter of Philox calls (lattice), or null
@@ -240,6 +241,124 @@ static void add_tiles(std::vector<Tile>& tiles, uint32_t job, uint64_t count, ui
   for (uint64_t w = 0; w < count; w += size) tiles.push_back(Tile{job, (uint32_t)w});
 }
 
+static void lattice_tiles(const std::vector<LatJob>& jobs, uint32_t size,
+                          std::vector<Tile>& out) {
+  out.clear();
+  for (size_t j = 0; j < jobs.size(); ++j) add_tiles(out, (uint32_t)j, jobs[j].nwords, size);
+}
+
+// ============================================================================ autotuner
+// Launch shape of the lattice half-step kernel per encoding family: tiles of
+// kTile lane words (one per thread) or kLatTile (kWordsPerThread per thread).
+// The choice is made by timing: each candidate runs the position-0 half step of
+// the family on a copy of its job table without step sums (no fused tracking)
+// and without the Philox counter.  Such a launch only writes sigma', with the
+// values the real position-0 half step of the same step writes (the draws are
+// counter-based), so the trials leave no trace in any trajectory.  Results are
+// cached per (encoding, bit length of the lane-word count, bit length of the
+// job count).  Families smaller than one resident wave of kLatTile tiles take
+// one lane word per thread without trials.
+namespace {
+struct TuneKey {
+  int enc, lw, lj;
+  bool operator<(const TuneKey& o) const {
+    if (enc != o.enc) return enc < o.enc;
+    if (lw != o.lw) return lw < o.lw;
+    return lj < o.lj;
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+std::atomic<uint64_t> g_tune_trials{0};
+
+int bit_length(uint64_t x) {
+  int b = 0;
+  while (x) {
+    ++b;
+    x >>= 1;
+  }
+  return b;
+}
+
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+}  // namespace
+
+// Mean device time (ms) of one position-0 half-step launch with tiles of kTile * wpt
+// lane words: 3 timed launches after one warm-up.
+static shaken_status trial_lattice(int enc, int wpt, const DevMem& jobs_dev,
+                                   const std::vector<LatJob>& jobs, cudaStream_t st, float* ms) {
+  std::vector<Tile> tiles;
+  lattice_tiles(jobs, (uint32_t)(kTile * wpt), tiles);
+  DevMem td;
+  TRY(upload(td, tiles.data(), tiles.size() * sizeof(Tile), st));
+  EventPair ev;
+  CU(cudaEventCreate(&ev.a));
+  CU(cudaEventCreate(&ev.b));
+  const int nt = (int)tiles.size();
+  CU(shk::launch_lattice_half(enc, wpt, jobs_dev.as<LatJob>(), td.as<Tile>(), nt, 0u, nullptr, st));
+  CU(cudaEventRecord(ev.a, st));
+  for (int r = 0; r < 3; ++r)
+    CU(shk::launch_lattice_half(enc, wpt, jobs_dev.as<LatJob>(), td.as<Tile>(), nt, 0u, nullptr,
+                                st));
+  CU(cudaEventRecord(ev.b, st));
+  CU(cudaEventSynchronize(ev.b));
+  float t = 0.0f;
+  CU(cudaEventElapsedTime(&t, ev.a, ev.b));
+  *ms = t / 3.0f;
+  return SHAKEN_OK;
+}
+
+static shaken_status choose_lattice_wpt(const Plan& P, int enc, const std::vector<LatJob>& jobs,
+                                        cudaStream_t st, int* wpt) {
+  uint64_t words = 0;
+  for (const LatJob& J : jobs) words += J.nwords;
+  const uint64_t wave = (uint64_t)shk::lattice_resident_blocks();
+  const uint64_t big_tiles = words / (uint64_t)shk::kLatTile;
+  if (big_tiles < wave) {  // not one wave of large tiles: one lane word per thread
+    *wpt = 1;
+    return SHAKEN_OK;
+  }
+  if (!P.autotune) {  // fixed rule: large tiles once the family fills 8 waves
+    *wpt = big_tiles >= 8 * wave ? shk::kWordsPerThread : 1;
+    return SHAKEN_OK;
+  }
+  const TuneKey key{enc, bit_length(words), bit_length(jobs.size())};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      *wpt = it->second;
+      return SHAKEN_OK;
+    }
+  }
+  std::vector<LatJob> trial(jobs);
+  for (LatJob& J : trial) J.sums = nullptr;
+  DevMem jd;
+  TRY(upload(jd, trial.data(), trial.size() * sizeof(LatJob), st));
+  const int cands[2] = {1, shk::kWordsPerThread};
+  float best = 0.0f;
+  int pick = 1;
+  for (int i = 0; i < 2; ++i) {
+    float ms = 0.0f;
+    TRY(trial_lattice(enc, cands[i], jd, trial, st, &ms));
+    if (i == 0 || ms < best) {
+      best = ms;
+      pick = cands[i];
+    }
+  }
+  g_tune_trials.fetch_add(1);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = pick;
+  *wpt = pick;
+  return SHAKEN_OK;
+}
+
 static shaken_status build_plan(Plan& P, cudaStream_t st) {
   P.fams.clear();
   P.drop_graph();
@@ -247,21 +366,6 @@ static shaken_status build_plan(Plan& P, cudaStream_t st) {
   std::vector<std::vector<GraphJob>> gjobs(2);  // 0 integer, 1 real
   std::vector<std::vector<Tile>> tiles(5);
   std::vector<CtxDev*> cds;
-  // lattice tile size per encoding family: 4 lane words per thread when the
-  // family has enough tiles to keep one resident wave busy, else 1
-  int lat_wpt[3] = {1, 1, 1};
-  {
-    uint64_t words[3] = {0, 0, 0};
-    for (shaken_ctx* c : P.members) {
-      if (c->kind != SHAKEN_LATTICE) continue;
-      const bool multi = c->enc == SHAKEN_MULTISPIN;
-      const uint64_t per_job = multi ? (uint64_t)c->L * c->L : (uint64_t)c->L * c->L / 32;
-      words[c->enc] += per_job * (uint64_t)(multi ? c->R / 32 : c->R);
-    }
-    const uint64_t wave = (uint64_t)shk::lattice_resident_blocks();
-    for (int e = 0; e < 3; ++e)
-      lat_wpt[e] = words[e] / (uint64_t)shk::kLatTile >= 8 * wave ? shk::kWordsPerThread : 1;
-  }
   for (shaken_ctx* c : P.members) {
     CtxDev* cdp = c->cd.as<CtxDev>();
     cds.push_back(cdp);
@@ -295,7 +399,6 @@ static shaken_status build_plan(Plan& P, cudaStream_t st) {
         J.wpr_shift = 0xffffffffu;
         for (uint32_t sh = 0; sh < 32; ++sh)
           if ((1u << sh) == wpr) J.wpr_shift = sh;
-        add_tiles(tiles[e], (uint32_t)ljobs[e].size(), nwords, (uint32_t)(kTile * lat_wpt[e]));
         ljobs[e].push_back(J);
       }
     } else {
@@ -330,6 +433,12 @@ static shaken_status build_plan(Plan& P, cudaStream_t st) {
         gjobs[fi].push_back(J);
       }
     }
+  }
+  int lat_wpt[3] = {1, 1, 1};
+  for (int e = 0; e < 3; ++e) {
+    if (ljobs[e].empty()) continue;
+    TRY(choose_lattice_wpt(P, e, ljobs[e], st, &lat_wpt[e]));
+    lattice_tiles(ljobs[e], (uint32_t)(kTile * lat_wpt[e]), tiles[e]);
   }
   for (int e = 0; e < 3; ++e) {
     if (ljobs[e].empty()) continue;
@@ -1243,6 +1352,55 @@ void shaken_batch_free(shaken_batch* b) {
   cudaStreamSynchronize(b->stream);
   for (shaken_ctx* c : b->plan.members) c->owner = nullptr;
   delete b;
+}
+
+shaken_status shaken_batch_set_autotune(shaken_batch* b, int on) {
+  if (!b) return fail(SHAKEN_E_INVAL, "NULL batch");
+  b->plan.autotune = on != 0;
+  b->plan.invalidate();
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_set_autotune(shaken_ctx* ctx, int on) {
+  if (!ctx) return fail(SHAKEN_E_INVAL, "NULL context");
+  ctx->solo.autotune = on != 0;
+  ctx->solo.invalidate();
+  return SHAKEN_OK;
+}
+
+static shaken_status plan_lattice_wpt(Plan& P, cudaStream_t st, int enc, int* wpt) {
+  if (!wpt || enc < 0 || enc > 2) return fail(SHAKEN_E_INVAL, "bad encoding or NULL output");
+  if (P.dirty) TRY(build_plan(P, st));
+  *wpt = 0;
+  for (auto& F : P.fams)
+    if (F->kind == 0 && F->enc == enc) *wpt = F->wpt;
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_batch_lattice_wpt(shaken_batch* b, int encoding, int* words_per_thread) {
+  if (!b) return fail(SHAKEN_E_INVAL, "NULL batch");
+  return plan_lattice_wpt(b->plan, b->stream, encoding, words_per_thread);
+}
+
+shaken_status shaken_lattice_wpt(shaken_ctx* ctx, int* words_per_thread) {
+  if (!ctx) return fail(SHAKEN_E_INVAL, "NULL context");
+  if (ctx->kind != SHAKEN_LATTICE) return fail(SHAKEN_E_INVAL, "not a lattice context");
+  if (ctx->owner) return fail(SHAKEN_E_STATE, "context belongs to a batch");
+  return plan_lattice_wpt(ctx->solo, ctx->stream, ctx->enc, words_per_thread);
+}
+
+shaken_status shaken_autotune_stats(uint64_t* trials, uint64_t* cached) {
+  if (!trials || !cached) return fail(SHAKEN_E_INVAL, "NULL argument");
+  *trials = g_tune_trials.load();
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  *cached = (uint64_t)g_tune.size();
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_autotune_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
+  return SHAKEN_OK;
 }
 
 shaken_status shaken_batch_set_timing(shaken_batch* b, int on) {

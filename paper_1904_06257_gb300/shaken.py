@@ -91,6 +91,12 @@ def _load():
         "shaken_batch_set_timing": [vp, ctypes.c_int],
         "shaken_batch_kernel_time": [vp, ctypes.POINTER(d), ctypes.POINTER(u64)],
         "shaken_batch_set_rng_counter": [vp, vp],
+        "shaken_batch_set_autotune": [vp, ctypes.c_int],
+        "shaken_set_autotune": [vp, ctypes.c_int],
+        "shaken_batch_lattice_wpt": [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+        "shaken_lattice_wpt": [vp, ctypes.POINTER(ctypes.c_int)],
+        "shaken_autotune_stats": [ctypes.POINTER(u64), ctypes.POINTER(u64)],
+        "shaken_autotune_clear": [],
         "shaken_microbench": [ctypes.c_int, ctypes.POINTER(d), ctypes.POINTER(d)],
         "shaken_state_bytes": [vp, ctypes.POINTER(sz)],
         "shaken_set_state_raw": [vp, vp, sz],
@@ -302,6 +308,36 @@ def shaken_batch_launch_count(batch) -> int:
     c = ctypes.c_uint64()
     _check(_lib.shaken_batch_launch_count(batch, ctypes.byref(c)))
     return c.value
+
+
+def shaken_batch_set_autotune(batch, on: bool):
+    _check(_lib.shaken_batch_set_autotune(batch, int(bool(on))))
+
+
+def shaken_set_autotune(ctx, on: bool):
+    _check(_lib.shaken_set_autotune(ctx, int(bool(on))))
+
+
+def shaken_batch_lattice_wpt(batch, encoding: int) -> int:
+    v = ctypes.c_int()
+    _check(_lib.shaken_batch_lattice_wpt(batch, int(encoding), ctypes.byref(v)))
+    return v.value
+
+
+def shaken_lattice_wpt(ctx) -> int:
+    v = ctypes.c_int()
+    _check(_lib.shaken_lattice_wpt(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def shaken_autotune_stats():
+    t, c = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_lib.shaken_autotune_stats(ctypes.byref(t), ctypes.byref(c)))
+    return t.value, c.value
+
+
+def shaken_autotune_clear():
+    _check(_lib.shaken_autotune_clear())
 
 
 def shaken_batch_set_timing(batch, on: bool):
