@@ -148,6 +148,10 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
+    if args.only_graphs:
+        if rank == 0:
+            print(json.dumps(run_graphs(S, stream, torch, args)), flush=True)
+        return None
     Ls, betas, seeds = workload(rank)
     ups = updates_per_step(Ls)
 
@@ -603,6 +607,8 @@ def main():
     ap.add_argument("--only-batched", action="store_true",
                     help="time the batched workload only (profiling runs)")
     ap.add_argument("--skip-graphs", action="store_true", help="skip the sparse-graph section")
+    ap.add_argument("--only-graphs", action="store_true",
+                    help="run the sparse-graph section only (profiling runs)")
     ap.add_argument("--graph-anneal-steps", type=int, default=5000)
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=4.0, help="Poisson arrivals per second")

@@ -60,20 +60,109 @@ __device__ __forceinline__ bool decide_int(uint32_t u, int s, int sigma, float q
   return decide_exact(u, s, sigma, q, lam, beta);
 }
 
+// Number of neighbours y with J_xy s_y = +1 on lane k (slow path, one lane).
+__device__ __noinline__ int lane_count(const uint32_t* __restrict__ src,
+                                       const uint32_t* __restrict__ col, int p0, int p1, int k) {
+  int cnt = 0;
+  for (int e = p0; e < p1; ++e) {
+    const uint32_t cv = col[e];
+    cnt += (int)(((src[cv & 0x7fffffffu] ^ (0u - (cv >> 31))) >> k) & 1u);
+  }
+  return cnt;
+}
+
+// u_k of lane k of word (x, b) (slow path, one lane).
+__device__ __noinline__ uint32_t lane_draw(uint32_t key0, uint32_t key1, uint32_t x, uint32_t b,
+                                           uint32_t t, uint32_t typ, int k) {
+  const uint4 w = ph_call(ph_key(key0, key1), x, b, t, typ + 2u * (uint32_t)(k >> 2));
+  const int i = k & 3;
+  return i == 0 ? w.x : i == 1 ? w.y : i == 2 ? w.z : w.w;
+}
+
+struct GraphShared;
+
+// Fast decisions of the 32 lanes of a word (integer couplings, byte counters C):
+// lane k = 8 c2 + m takes byte c2 of C[m] as its count and u_k from call k >> 2.
+// With e~ = 2^(kb h~) the lane is +1 if (u + 1)(1 + e~) < 2^32 (1 - eps) and -1 if
+// u (1 + e~) > 2^32 (1 + eps); otherwise its bit is set in `und` for the fp64 test.
+// eps = 2^-18 + 2^-18 beta B, B = d + |q| + |lambda| + 1, is at least five times the
+// fp32 error of the compared products (h~: three roundings of magnitude <= B;
+// kb h~; ex2.approx, relative error 2^-22; 1 + e~; u to float; the product).
+template <bool UNI>
+__device__ __forceinline__ void int_lanes(const uint32_t (&C)[8], uint32_t S, const PhKey& K,
+                                          uint32_t x, uint32_t b, uint32_t t, uint32_t typ,
+                                          float bp, float bm, float a0, float B,
+                                          const GraphShared& sh, bool fuse, float (*acc)[32],
+                                          int lane, uint32_t& res, uint32_t& und);
+
 struct GraphShared {
   float kb[32];   // -2 beta_k log2(e) per lane (anneal: the step's beta on every lane)
   float epc[32];  // 2^-18 beta_k per lane
   double beta[32];
+  int uni;        // every lane has the same beta
   float acc[kTile / 32][32][32];  // [warp][replica lane k][thread lane]: tracking sums
   float red[kTile / 32][32];
 };
+
+template <bool UNI>
+__device__ __forceinline__ void int_lanes(const uint32_t (&C)[8], uint32_t S, const PhKey& K,
+                                          uint32_t x, uint32_t b, uint32_t t, uint32_t typ,
+                                          float bp, float bm, float a0, float B,
+                                          const GraphShared& sh, bool fuse, float (*acc)[32],
+                                          int lane, uint32_t& res, uint32_t& und) {
+  const float two32 = 4294967296.0f;
+  float kb0 = 0.0f, lo0 = 0.0f, hi0 = 0.0f;
+  if (UNI) {
+    kb0 = sh.kb[0];
+    const float eps = 3.814697265625e-06f + sh.epc[0] * B;
+    lo0 = two32 * (1.0f - eps);
+    hi0 = two32 * (1.0f + eps);
+  }
+#pragma unroll 1
+  for (uint32_t c2 = 0; c2 < 4u; ++c2) {
+    const uint4 w0 = ph_call(K, x, b, t, typ + 4u * c2);       // call 2 c2
+    const uint4 w1 = ph_call(K, x, b, t, typ + 4u * c2 + 2u);  // call 2 c2 + 1
+    const uint32_t uw[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+    const uint32_t selb = 0x7540u + c2;  // byte c2 of C[m] under the exponent byte 0x4B
+    const uint32_t s8 = S >> (8u * c2);  // sigma bits of lanes 8 c2 .. 8 c2 + 7
+    uint32_t r8 = 0u, u8 = 0u;           // their decisions and undecided flags
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int k = 8 * (int)c2 + m;
+      // count as a float: 2^23 + cnt exactly, minus 2^23
+      const float cf = __fsub_rn(__int_as_float((int)__byte_perm(C[m], 0x4B000000u, selb)),
+                                 8388608.0f);
+      const bool up = (s8 >> m) & 1u;
+      const float hf = __fmaf_rn(2.0f, cf, up ? bp : bm);
+      float kb = kb0, lo = lo0, hi = hi0;
+      if (!UNI) {
+        kb = sh.kb[k];
+        const float eps = 3.814697265625e-06f + sh.epc[k] * B;
+        lo = two32 * (1.0f - eps);
+        hi = two32 * (1.0f + eps);
+      }
+      const float onep = 1.0f + ex2_approx(kb * hf);
+      const float uf = __uint2float_rn(uw[m]);
+      const bool plus = __fmaf_rn(uf, onep, onep) < lo;
+      const bool minus = uf * onep > hi;
+      r8 |= (uint32_t)plus << m;
+      u8 |= (uint32_t)(!plus && !minus) << m;
+      if (fuse) {
+        const float a = __fmaf_rn(2.0f, cf, a0);
+        acc[k][lane] += up ? a : -a;
+      }
+    }
+    res |= r8 << (8u * c2);
+    und |= u8 << (8u * c2);
+  }
+}
 
 // One thread owns one (vertex, group) word.  Each block walks a contiguous range
 // of tiles (one job per tile).  With tracking on, half 0 also accumulates per
 // replica sum_x sigma_x (s_x + 2 lambda_x), i.e. -H(sigma_t) (Eq. (ham1)), reduced
 // when the block leaves a job.
 template <bool INTEGER>
-__global__ void __launch_bounds__(kTile) graph_half_kernel(const GraphJob* __restrict__ jobs,
+__global__ void __launch_bounds__(kTile, 3) graph_half_kernel(const GraphJob* __restrict__ jobs,
                                                            const Tile* __restrict__ tiles,
                                                            int n_tiles, uint32_t half,
                                                            int exact_always) {
@@ -135,6 +224,9 @@ __global__ void __launch_bounds__(kTile) graph_half_kernel(const GraphJob* __res
         sh.beta[threadIdx.x] = beta;
         sh.kb[threadIdx.x] = (float)(-2.0 * beta * 1.4426950408889634);
         sh.epc[threadIdx.x] = (float)beta * 3.814697265625e-06f;
+        const double b0 = __shfl_sync(0xffffffffu, beta, 0);
+        const bool same = __all_sync(0xffffffffu, beta == b0);
+        if (threadIdx.x == 0) sh.uni = same ? 1 : 0;
       }
       __syncthreads();
       cur_job = (int)tl.job;
@@ -157,50 +249,60 @@ __global__ void __launch_bounds__(kTile) graph_half_kernel(const GraphJob* __res
     const PhKey K = ph_key(J.key0, J.key1);
     uint32_t res = F;
     if (INTEGER) {
-      // bit-sliced count of +1 contributions J_xy s_y over the neighbours
-      uint32_t P[6] = {0u, 0u, 0u, 0u, 0u, 0u};
-      if (d <= 63) {
-        for (int e = p0; e < p1; ++e) {
-          const uint32_t cv = col[e];
-          uint32_t carry = src[cv & 0x7fffffffu] ^ (0u - (cv >> 31));
-#pragma unroll
-          for (int b = 0; b < 6; ++b) {
-            const uint32_t tmp = P[b] & carry;
-            P[b] ^= carry;
-            carry = tmp;
-          }
-        }
-      }
       const float B = (float)d + fabsf(qf) + fabsf(lam) + 1.0f;
+      if (d <= 255) {
+        // byte counters: byte i of C[m] = number of neighbours with J_xy s_y = +1 on
+        // lane m + 8 i (at most d <= 255, so bytes never carry into each other)
+        uint32_t C[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) C[m] = 0u;
+        for (int e = p0; e < p1; ++e) {
+          const uint32_t cv = __ldg(col + e);
+          const uint32_t w = __ldg(src + (cv & 0x7fffffffu)) ^ (0u - (cv >> 31));
+#pragma unroll
+          for (int m = 0; m < 8; ++m) C[m] += (w >> m) & 0x01010101u;
+        }
+        // h = 2 cnt + (lambda - d +- q): one rounding in the fused multiply-add
+        const float lmd = __fadd_rn(lam, -(float)d);
+        const float bp = __fadd_rn(lmd, qf), bm = __fadd_rn(lmd, -qf);
+        const float a0 = __fadd_rn(2.0f * lam, -(float)d);  // sigma (s + 2 lambda) = sigma (2 cnt + a0)
+        uint32_t und = 0u;
+        if (sh.uni)
+          int_lanes<true>(C, S, K, x, J.b, t, typ, bp, bm, a0, B, sh, fuse, acc, lane, res, und);
+        else
+          int_lanes<false>(C, S, K, x, J.b, t, typ, bp, bm, a0, B, sh, fuse, acc, lane, res, und);
+        while (und != 0u) {  // lanes inside the error bound of the fast test: fp64 threshold
+          const int k = __ffs(und) - 1;
+          und &= und - 1u;
+          const int cnt = lane_count(src, col, p0, p1, k);
+          const uint32_t u = lane_draw(J.key0, J.key1, x, J.b, t, typ, k);
+          const int sigma = ((S >> k) & 1u) ? 1 : -1;
+          res |= (uint32_t)decide_exact(u, 2 * cnt - d, sigma, J.q, lam, sh.beta[k]) << k;
+        }
+      } else {
 #pragma unroll 1
-      for (int c = 0; c < 8; ++c) {  // one Philox call per 4 lanes
-        const uint4 w = ph_call(K, x, J.b, t, typ + 2u * (uint32_t)c);
-        const uint32_t uw[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int k = 4 * c + i;
-          int cnt;
-          if (d <= 63) {
-            cnt = 0;
-#pragma unroll
-            for (int b = 0; b < 6; ++b) cnt |= (int)((P[b] >> k) & 1u) << b;
-          } else {
-            cnt = 0;
-            for (int e = p0; e < p1; ++e) {
-              const uint32_t cv = col[e];
-              cnt += (int)(((src[cv & 0x7fffffffu] ^ (0u - (cv >> 31))) >> k) & 1u);
-            }
-          }
+        for (int k = 0; k < 32; ++k) {  // very high degree: one lane at a time
+          const int cnt = lane_count(src, col, p0, p1, k);
+          const uint32_t u = lane_draw(J.key0, J.key1, x, J.b, t, typ, k);
           const int s = 2 * cnt - d;
           const int sigma = ((S >> k) & 1u) ? 1 : -1;
           const float eps = 3.814697265625e-06f + sh.epc[k] * B;
-          const bool plus = decide_int(uw[i], s, sigma, qf, J.q, lam, sh.kb[k], eps, sh.beta[k],
-                                       exact_always != 0);
-          res |= (uint32_t)plus << k;
+          res |= (uint32_t)decide_int(u, s, sigma, qf, J.q, lam, sh.kb[k], eps, sh.beta[k],
+                                      exact_always != 0) << k;
           if (fuse) {
             const float a = (float)s + 2.0f * lam;
             acc[k][lane] += sigma > 0 ? a : -a;
           }
+        }
+      }
+      if (exact_always) {  // debugging aid: every lane through the fp64 threshold
+        res = F;
+#pragma unroll 1
+        for (int k = 0; k < 32; ++k) {
+          const int cnt = lane_count(src, col, p0, p1, k);
+          const uint32_t u = lane_draw(J.key0, J.key1, x, J.b, t, typ, k);
+          const int sigma = ((S >> k) & 1u) ? 1 : -1;
+          res |= (uint32_t)decide_exact(u, 2 * cnt - d, sigma, J.q, lam, sh.beta[k]) << k;
         }
       }
     } else {

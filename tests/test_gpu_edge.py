@@ -42,13 +42,15 @@ def test_graph_without_edges(S):
     assert np.array_equal(got, ref)
 
 
-def test_star_graph_high_degree_and_isolated(S):
-    # vertex 0 joined to 100 leaves (in-degree 0 and out-degree 100 with min->max;
-    # reversed orientation gives in-degree 100 > 63); vertices 101..149 isolated
-    n, R = 150, 32
-    u = np.zeros(100, np.int32)
-    v = np.arange(1, 101, dtype=np.int32)
-    J = W.couplings_pm1(100, 3)
+@pytest.mark.parametrize("leaves", [100, 300])
+def test_star_graph_high_degree_and_isolated(S, leaves):
+    # vertex 0 joined to `leaves` leaves (in-degree 0 and out-degree `leaves` with
+    # min->max; reversed orientation gives in-degree `leaves`: above 63, and 300 is
+    # above the 255 a byte counter holds); 50 further vertices isolated
+    n, R = leaves + 50, 32
+    u = np.zeros(leaves, np.int32)
+    v = np.arange(1, leaves + 1, dtype=np.int32)
+    J = W.couplings_pm1(leaves, 3)
     lam = W.fields_normal(n, 0.2, 4)
     for orientation, (uu, vv) in ((0, (u, v)), (2, (v, u))):
         got, ref = run_graph_both(S, n, uu, vv, J, R, W.beta_grid(R, 0.1, 2.0, 8), 0.5, lam, 3,
