@@ -148,9 +148,11 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
-    if args.only_graphs:
+    if args.only_graphs or args.only_serving:
         if rank == 0:
-            print(json.dumps(run_graphs(S, stream, torch, args)), flush=True)
+            part = (run_graphs(S, stream, torch, args) if args.only_graphs
+                    else run_serving(S, stream, args))
+            print(json.dumps(part), flush=True)
         return None
     Ls, betas, seeds = workload(rank)
     ups = updates_per_step(Ls)
@@ -515,13 +517,9 @@ def run_graphs(S, stream, torch, args):
 
 
 # ------------------------------------------------------------------------ serving
-def run_serving(S, stream, args):
-    """Continuous batching of annealing jobs through the server.  Arrivals are a
-    Poisson stream; each job anneals (beta 0.1 -> 3.0) a +-1 Erdos-Renyi graph with
-    n log-uniform in [1e3, 1e6] and mean degree uniform in [3, 16] -- drawn from a
-    pool of pre-generated graphs of that distribution -- with replicas log-uniform
-    over multiples of 32 in [32, 1024] and steps uniform in [1000, 20000] times
-    step_scale.  Returns p50/p99 latency (completion - arrival) and throughput."""
+def _serving_pool(args):
+    """Pre-generated +-1 Erdos-Renyi graphs of the serving distribution (n log-uniform in
+    [1e3, 1e6], mean degree uniform in [3, 16])."""
     g = W.rng(W.BASE_SEED + 77)
     pool = []
     for k in range(args.serve_pool):
@@ -531,41 +529,102 @@ def run_serving(S, stream, args):
         u, v = W.erdos_renyi(n, deg, W.BASE_SEED + 1000 + k)
         J = W.couplings_pm1(u.size, W.BASE_SEED + 2000 + k)
         pool.append((n, u, v, J))
-    jobs = W.serving_stream(args.serve_rate, args.serve_horizon, W.BASE_SEED + 3)
+    return pool
+
+
+def _serve(S, stream, pool, jobs, args, step_scale, window_s=None):
+    """Submit `jobs` at their arrival times (job k anneals pool graph k mod |pool|, beta
+    0.1 -> 3.0), then drain -- or, with window_s, stop after window_s seconds and cancel
+    what is left.  Latency = completion - arrival of the completed jobs."""
     srv = S.shaken_server_create(int(args.serve_budget_gb * 2**30), 64, stream)
     t0 = time.perf_counter()
-    ids, meta = [], []
+    ids, meta, lags = [], [], []
     for k, jb in enumerate(jobs):
         n, u, v, J = pool[k % len(pool)]
-        steps = max(1, int(round(jb["steps"] * args.serve_step_scale)))
+        steps = max(1, int(round(jb["steps"] * step_scale)))
         R = jb["replicas"]
         p = S.Problem(S.GRAPH, S.MULTISPIN, R, 0.1, 1.0, n=n, u=u, v=v, J_edge=J,
                       J_is_integer=True)
         delay = jb["arrival"] - (time.perf_counter() - t0)
         if delay > 0:
             time.sleep(delay)
+        lags.append(max(0.0, -delay))
         ids.append(S.shaken_server_submit(srv, p, jb["seed"], W.linear_schedule(0.1, 3.0, steps)))
         meta.append((jb["arrival"], n, R, steps))
-    S.shaken_server_drain(srv, args.serve_timeout)
+    if window_s is None:
+        S.shaken_server_drain(srv, args.serve_timeout)
+    else:
+        rest = window_s - (time.perf_counter() - t0)
+        if rest > 0:
+            time.sleep(rest)
     wall = time.perf_counter() - t0
     upd, launches, done = S.shaken_server_stats(srv)
-    lat, waits = [], []
+    lat, states = [], [0, 0, 0]
     for jid, (arr, n, R, steps) in zip(ids, meta):
-        _, ta, td = S.shaken_server_result(srv, jid, R)
-        lat.append(td - arr)
-        waits.append(ta - arr)
+        st = S.shaken_server_poll(srv, jid)
+        states[min(st, 2)] += 1
+        if st == 2:
+            _, ta, td = S.shaken_server_result(srv, jid, R)
+            lat.append(td - arr)
     S.shaken_server_free(srv)
-    lat = np.array(lat)
     work = sum(2.0 * n * R * st for _, n, R, st in meta)
-    return {"jobs": len(ids), "completed": int(done), "wall_s": wall,
-            "arrival_rate_per_s": args.serve_rate, "horizon_s": args.serve_horizon,
-            "step_scale": args.serve_step_scale, "graph_pool": len(pool),
-            "offered_updates_per_s": work / args.serve_horizon,
-            "served_updates_per_s": upd / wall,
-            "latency_p50_s": float(np.percentile(lat, 50)),
-            "latency_p99_s": float(np.percentile(lat, 99)),
-            "admission_wait_p50_s": float(np.percentile(waits, 50)),
+    return {"jobs": len(ids), "completed": int(done), "queued_at_end": states[0],
+            "running_at_end": states[1], "wall_s": wall,
+            "offered_updates": work, "served_updates_per_s": upd / wall,
+            "latency_p50_s": float(np.percentile(lat, 50)) if lat else None,
+            "latency_p99_s": float(np.percentile(lat, 99)) if lat else None,
+            "submit_lag_max_s": float(max(lags) if lags else 0.0),
             "launches": int(launches)}
+
+
+def run_serving(S, stream, args):
+    """Continuous batching of annealing jobs through the server (Poisson arrivals of
+    +-1 Erdos-Renyi anneals, replicas log-uniform over multiples of 32 in [32, 1024],
+    steps uniform in [1000, 20000] x step_scale):
+    * capacity: a burst of jobs submitted at once, served updates/s over the makespan;
+    * load sweep: Poisson streams at 50 / 70 / 90 % of that capacity -> p50 / p99
+      latency (completion - arrival);
+    * the literal stream (200 jobs/s, full step counts) for a fixed window: it offers
+      ~100x the capacity, so the queue grows; completed jobs, queue depth and served
+      rate are reported and the rest is cancelled."""
+    pool = _serving_pool(args)
+    scale = args.serve_step_scale
+    out = {"step_scale": scale, "graph_pool": len(pool), "budget_gb": args.serve_budget_gb}
+    # expected work per job of the stream distribution (large sample, no GPU)
+    sample = W.serving_stream(1000.0, 10.0, W.BASE_SEED + 9)
+    mean_work = float(np.mean([2.0 * pool[k % len(pool)][0] * jb["replicas"] *
+                               max(1, int(round(jb["steps"] * scale)))
+                               for k, jb in enumerate(sample)]))
+    # capacity
+    burst = W.serving_stream(1000.0, 10.0, W.BASE_SEED + 4, max_jobs=args.serve_burst)
+    for jb in burst:
+        jb["arrival"] = 0.0
+    cap = _serve(S, stream, pool, burst, args, scale)
+    capacity = cap["offered_updates"] / cap["wall_s"]
+    out["capacity"] = {"jobs": cap["jobs"], "makespan_s": cap["wall_s"],
+                       "updates_per_s": capacity}
+    # load sweep
+    sweep = []
+    for frac in (0.5, 0.7, 0.9):
+        rate = frac * capacity / mean_work
+        jobs = W.serving_stream(rate, args.serve_horizon, W.BASE_SEED + 3)
+        r = _serve(S, stream, pool, jobs, args, scale)
+        r.update({"load": frac, "arrival_rate_per_s": rate, "horizon_s": args.serve_horizon,
+                  "offered_updates_per_s": r["offered_updates"] / args.serve_horizon})
+        sweep.append(r)
+    out["load_sweep"] = sweep
+    # literal stream
+    lit = W.serving_stream(200.0, args.serve_literal_horizon, W.BASE_SEED + 3)
+    r = _serve(S, stream, pool, lit, args, 1.0, window_s=args.serve_literal_window)
+    r.update({"arrival_rate_per_s": 200.0, "horizon_s": args.serve_literal_horizon,
+              "window_s": args.serve_literal_window,
+              "offered_updates_per_s": r["offered_updates"] / args.serve_literal_horizon})
+    out["literal_stream"] = r
+    # headline numbers: the 70 % load point
+    mid = sweep[1]
+    out.update({"latency_p50_s": mid["latency_p50_s"], "latency_p99_s": mid["latency_p99_s"],
+                "served_updates_per_s": mid["served_updates_per_s"], "at_load": 0.7})
+    return out
 
 
 # ------------------------------------------------------------------------ reference arm
@@ -609,10 +668,16 @@ def main():
     ap.add_argument("--skip-graphs", action="store_true", help="skip the sparse-graph section")
     ap.add_argument("--only-graphs", action="store_true",
                     help="run the sparse-graph section only (profiling runs)")
+    ap.add_argument("--only-serving", action="store_true", help="run the serving section only")
     ap.add_argument("--graph-anneal-steps", type=int, default=5000)
     ap.add_argument("--skip-serving", action="store_true")
-    ap.add_argument("--serve-rate", type=float, default=4.0, help="Poisson arrivals per second")
-    ap.add_argument("--serve-horizon", type=float, default=10.0, help="seconds of arrivals")
+    ap.add_argument("--serve-horizon", type=float, default=8.0,
+                    help="seconds of arrivals of each load-sweep stream")
+    ap.add_argument("--serve-burst", type=int, default=24, help="jobs of the capacity burst")
+    ap.add_argument("--serve-literal-horizon", type=float, default=1.0,
+                    help="seconds of arrivals of the literal 200 jobs/s stream")
+    ap.add_argument("--serve-literal-window", type=float, default=8.0,
+                    help="seconds the literal stream runs before the rest is cancelled")
     ap.add_argument("--serve-step-scale", type=float, default=0.05,
                     help="steps per job = U[1000, 20000] x this factor")
     ap.add_argument("--serve-pool", type=int, default=12, help="pre-generated graphs")

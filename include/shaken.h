@@ -300,6 +300,8 @@ shaken_status shaken_server_drain(shaken_server* s, double timeout_s);
 /* Aggregate counters: site updates done, kernel launches, jobs done. */
 shaken_status shaken_server_stats(shaken_server* s, double* site_updates, uint64_t* launches,
                                   int64_t* jobs_done);
+/* Stop the worker after its current chunk, cancel queued and running jobs and
+ * release their device memory. */
 void shaken_server_free(shaken_server* s);
 
 /* ------------------------------------------------------------------------ */

@@ -1570,7 +1570,7 @@ static void server_loop(shaken_server* s) {
       s->batch.plan.members.push_back(c);
       s->batch.plan.invalidate();
     }
-    if (s->stop && s->queue.empty() && s->running.empty()) break;
+    if (s->stop) break;  // freeing the server cancels queued and running jobs
     if (s->running.empty()) {
       s->cv.wait_for(lk, std::chrono::milliseconds(2));
       if (s->stop && s->queue.empty()) break;
