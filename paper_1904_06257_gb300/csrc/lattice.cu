@@ -407,7 +407,7 @@ __device__ __forceinline__ void store_word(const LatJob& J, void* dstbuf, uint32
 // With sh.fuse the sums of sigma_t over the words are accumulated as well.
 template <int ENC, int WPT, bool COLL, bool FULL>
 __device__ __forceinline__ void tile_commit(const LatJob& J, const TileShared& sh,
-                                            Pending* __restrict__ q,
+                                            Pending* __restrict__ q, const PhKey& K,
                                             const uint32_t (&a)[WPT], uint32_t t, uint32_t half,
                                             const uint32_t (&S)[WPT], const uint32_t (&V)[WPT],
                                             const uint32_t (&H)[WPT], const LaneWord (&Lws)[WPT],
@@ -443,8 +443,6 @@ __device__ __forceinline__ void tile_commit(const LatJob& J, const TileShared& s
     }
   }
   __syncwarp();
-  if (qn == 0u) return;
-  const PhKey K = ph_key(J.key0, J.key1);
   for (uint32_t base = 0; base < qn; base += 32u) {
     if (base + lane < qn) {
       const Pending e = q[base + lane];
@@ -481,7 +479,7 @@ __device__ __forceinline__ void tile_decide(const LatJob& J, const TileShared& s
   }
   decide_head_words<COLL, WPT>(Lws, sh.tab, K, a, J.b, t, half);
   calls += 2u * WPT;
-  tile_commit<ENC, WPT, COLL, FULL>(J, sh, q, a, t, half, S, V, H, Lws, dstbuf, acc, calls);
+  tile_commit<ENC, WPT, COLL, FULL>(J, sh, q, K, a, t, half, S, V, H, Lws, dstbuf, acc, calls);
 }
 
 // Each block walks a contiguous range of tiles (kLatTile lane words each; a
@@ -505,6 +503,7 @@ __global__ void __launch_bounds__(kTile, kLatMinBlocks) lattice_half_kernel(cons
   const int tb = (int)(((long long)blockIdx.x * n_tiles) / gridDim.x);
   const int te = (int)(((long long)(blockIdx.x + 1) * n_tiles) / gridDim.x);
   int cur_job = -1;
+  PhKey K = ph_key(0u, 0u);  // the job's key schedule, rebuilt on job change only
   for (int ti = tb; ti < te; ++ti) {
     const Tile tl = tiles[ti];
     if ((int)tl.job != cur_job) {
@@ -537,6 +536,7 @@ __global__ void __launch_bounds__(kTile, kLatMinBlocks) lattice_half_kernel(cons
       }
       __syncthreads();
       cur_job = (int)tl.job;
+      K = ph_key(sh.job.key0, sh.job.key1);
     }
     if (sh.skip) continue;
     const LatJob& J = sh.job;
@@ -555,7 +555,6 @@ __global__ void __launch_bounds__(kTile, kLatMinBlocks) lattice_half_kernel(cons
         if (J.frozen != nullptr) F[k] = __ldg(J.frozen + w);
       }
     }
-    const PhKey K = ph_key(J.key0, J.key1);
     double acc[3] = {0.0, 0.0, 0.0};
     const bool full_tile = tl.w0 + kTile * WPT <= J.nwords;
     if (sh.tab.collapsed) {
