@@ -230,8 +230,8 @@ __device__ __forceinline__ void head_finish(LaneWord (&Lw)[WPT], const uint32_t 
 
 template <bool COLL, int WPT>
 __device__ __forceinline__ void decide_head_words(LaneWord (&Lw)[WPT], const LatTable& tab,
-                                                  const PhKey& K, const uint32_t (&a)[WPT],
-                                                  uint32_t b, uint32_t t, uint32_t half) {
+                                                  const PhKey& K, const PhShared& P,
+                                                  const uint32_t (&a)[WPT], uint32_t half) {
   uint32_t lt[WPT], eq[WPT];
 #pragma unroll
   for (int k = 0; k < WPT; ++k) {
@@ -242,7 +242,7 @@ __device__ __forceinline__ void decide_head_words(LaneWord (&Lw)[WPT], const Lat
   for (int call = 1; call >= 0; --call) {
     uint4 W[WPT];
 #pragma unroll
-    for (int k = 0; k < WPT; ++k) W[k] = ph_call(K, a[k], b, t, half + 2u * (uint32_t)call);
+    for (int k = 0; k < WPT; ++k) W[k] = ph_call_shared(K, P, a[k], half + 2u * (uint32_t)call);
     head_planes<COLL, WPT>(Lw, tab, call, W, lt, eq);
   }
   head_finish<WPT>(Lw, lt, eq);
@@ -251,11 +251,11 @@ __device__ __forceinline__ void decide_head_words(LaneWord (&Lw)[WPT], const Lat
 // Calls 2..7 while some lane is undecided.
 template <bool COLL>
 __device__ __forceinline__ void decide_tail(LaneWord& L, const LatTable& tab, const PhKey& K,
-                                            uint32_t a, uint32_t b, uint32_t t, uint32_t half,
+                                            const PhShared& P, uint32_t a, uint32_t half,
                                             uint32_t& calls) {
 #pragma unroll 1
   for (uint32_t call = 2; call < 8 && L.U != 0u; ++call) {
-    const uint4 w = ph_call(K, a, b, t, half + 2u * call);
+    const uint4 w = ph_call_shared(K, P, a, half + 2u * call);
     ++calls;
     apply_call<COLL>(L, w, tab, call);
   }
@@ -374,6 +374,7 @@ __device__ __forceinline__ void load_lane_words(const LatJob& J, const void* buf
 struct TileShared {
   LatJob job;
   LatTable tab;
+  PhShared ph;  // Philox rounds shared by every call of the job at this step
   uint32_t t;
   uint32_t skip;
   uint32_t fuse;
@@ -452,7 +453,7 @@ __device__ __forceinline__ void tile_commit(const LatJob& J, const TileShared& s
       Lw.X = e.X;
       Lw.U = e.U;
       Lw.res = e.res;
-      decide_tail<COLL>(Lw, sh.tab, K, e.w, J.b, t, half, calls);
+      decide_tail<COLL>(Lw, sh.tab, K, sh.ph, e.w, half, calls);
       store_word<ENC>(J, dstbuf, e.w, Lw.res);
     }
   }
@@ -477,7 +478,7 @@ __device__ __forceinline__ void tile_decide(const LatJob& J, const TileShared& s
     Lws[k] = classify<COLL>(S[k], V[k], H[k], F[k], sh.tab);
     if (!FULL && a[k] >= J.nwords) Lws[k].U = 0u;
   }
-  decide_head_words<COLL, WPT>(Lws, sh.tab, K, a, J.b, t, half);
+  decide_head_words<COLL, WPT>(Lws, sh.tab, K, sh.ph, a, half);
   calls += 2u * WPT;
   tile_commit<ENC, WPT, COLL, FULL>(J, sh, q, K, a, t, half, S, V, H, Lws, dstbuf, acc, calls);
 }
@@ -520,6 +521,7 @@ __global__ void __launch_bounds__(kTile, kLatMinBlocks) lattice_half_kernel(cons
         sh.skip = t >= cd->t_end;
         sh.fuse = (ENC != kEncMultispin) && half == 0u && sh.job.sums != nullptr && cd->tracking;
         sh.typ = half ^ cd->order;  // update type: 0 = dl / 1->2, 1 = ur / 2->1
+        sh.ph = ph_shared(ph_key(sh.job.key0, sh.job.key1), sh.job.b, t);
         const LatTable* src = sh.job.table;
         if (sh.job.anneal_tables != nullptr && cd->anneal_len != 0u) {
           uint32_t k = t - cd->anneal_t0;
@@ -806,6 +808,7 @@ __global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* _
       staged = src;
     }
     __syncthreads();  // sA complete (previous half step or the load), table staged
+    const PhShared P = ph_shared(K, J.b, t);
     double acc[3] = {0.0, 0.0, 0.0};
     for (uint32_t pos = 0; pos < 2; ++pos) {
       const uint32_t half = pos ^ order;  // update type of this position
@@ -819,11 +822,11 @@ __global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* _
         if (stab.collapsed) {
           Lw = classify<true>(S, V, H, F, stab);
           decide_head<true>(Lw, stab, K, w, J.b, t, half, calls);
-          decide_tail<true>(Lw, stab, K, w, J.b, t, half, calls);
+          decide_tail<true>(Lw, stab, K, P, w, half, calls);
         } else {
           Lw = classify<false>(S, V, H, F, stab);
           decide_head<false>(Lw, stab, K, w, J.b, t, half, calls);
-          decide_tail<false>(Lw, stab, K, w, J.b, t, half, calls);
+          decide_tail<false>(Lw, stab, K, P, w, half, calls);
         }
         out[w] = Lw.res;
         if (track && pos == 0u) {

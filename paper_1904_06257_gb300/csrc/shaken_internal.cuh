@@ -66,6 +66,52 @@ __device__ __forceinline__ uint4 ph_call(const PhKey& K, uint32_t c0, uint32_t c
   return make_uint4(c0, c1, c2, c3);
 }
 
+// Calls whose counters share (b, t): round 0 multiplies only words 0 and 2 of the
+// counter, so after it word 0 = hi(M1 t) ^ b ^ k0[0] and word 1 = lo(M1 t) do not
+// depend on (a, c3), and round 1's first product M0 * word0 does not either.
+// ph_call_shared(K, P, a, c3) == ph_call(K, a, b, t, c3) with P = ph_shared(K, b, t).
+struct PhShared {
+  uint32_t u0, u1;    // counter words 0 and 1 after round 0
+  uint32_t h01, l01;  // high and low halves of M0 * u0 (round 1)
+};
+
+__device__ __forceinline__ PhShared ph_shared(const PhKey& K, uint32_t b, uint32_t t) {
+  PhShared P;
+  const unsigned long long p1 = (unsigned long long)kPhM1 * t;
+  P.u0 = (uint32_t)(p1 >> 32) ^ b ^ K.k0[0];
+  P.u1 = (uint32_t)p1;
+  const unsigned long long q = (unsigned long long)kPhM0 * P.u0;
+  P.h01 = (uint32_t)(q >> 32);
+  P.l01 = (uint32_t)q;
+  return P;
+}
+
+__device__ __forceinline__ uint4 ph_call_shared(const PhKey& K, const PhShared& P, uint32_t a,
+                                                uint32_t c3) {
+  // round 0: only M0 * a depends on the lane word
+  const unsigned long long p0 = (unsigned long long)kPhM0 * a;
+  const uint32_t c2r0 = (uint32_t)(p0 >> 32) ^ c3 ^ K.k1[0];
+  const uint32_t c3r0 = (uint32_t)p0;
+  // round 1: M0 * u0 is shared
+  const unsigned long long p1 = (unsigned long long)kPhM1 * c2r0;
+  uint32_t c0 = (uint32_t)(p1 >> 32) ^ P.u1 ^ K.k0[1];
+  uint32_t c1 = (uint32_t)p1;
+  uint32_t c2 = P.h01 ^ c3r0 ^ K.k1[1];
+  uint32_t c3v = P.l01;
+#pragma unroll
+  for (int r = 2; r < 10; ++r) {
+    const unsigned long long q0 = (unsigned long long)kPhM0 * c0;
+    const unsigned long long q1 = (unsigned long long)kPhM1 * c2;
+    const uint32_t n0 = (uint32_t)(q1 >> 32) ^ c1 ^ K.k0[r];
+    const uint32_t n2 = (uint32_t)(q0 >> 32) ^ c3v ^ K.k1[r];
+    c1 = (uint32_t)q1;
+    c3v = (uint32_t)q0;
+    c0 = n0;
+    c2 = n2;
+  }
+  return make_uint4(c0, c1, c2, c3v);
+}
+
 // ---------------------------------------------------------------- exp and threshold
 __device__ __forceinline__ double exp_sd(double x) {
   if (x <= -64.0) return 0.0;
