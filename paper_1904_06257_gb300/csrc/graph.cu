@@ -99,6 +99,7 @@ struct GraphShared {
   float kb[32];   // -2 beta_k log2(e) per lane (anneal: the step's beta on every lane)
   float epc[32];  // 2^-18 beta_k per lane
   double beta[32];
+  PhShared ph;    // Philox rounds shared by every call of the job at this step
   int uni;        // every lane has the same beta
   float acc[kTile / 32][32][32];  // [warp][replica lane k][thread lane]: tracking sums
   float red[kTile / 32][32];
@@ -120,8 +121,8 @@ __device__ __forceinline__ void int_lanes(const uint32_t (&C)[8], uint32_t S, co
   }
 #pragma unroll 1
   for (uint32_t c2 = 0; c2 < 4u; ++c2) {
-    const uint4 w0 = ph_call(K, x, b, t, typ + 4u * c2);       // call 2 c2
-    const uint4 w1 = ph_call(K, x, b, t, typ + 4u * c2 + 2u);  // call 2 c2 + 1
+    const uint4 w0 = ph_call_shared(K, sh.ph, x, typ + 4u * c2);       // call 2 c2
+    const uint4 w1 = ph_call_shared(K, sh.ph, x, typ + 4u * c2 + 2u);  // call 2 c2 + 1
     const uint32_t uw[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
     const uint32_t selb = 0x7540u + c2;  // byte c2 of C[m] under the exponent byte 0x4B
     const uint32_t s8 = S >> (8u * c2);  // sigma bits of lanes 8 c2 .. 8 c2 + 7
@@ -226,7 +227,10 @@ __global__ void __launch_bounds__(kTile, 3) graph_half_kernel(const GraphJob* __
         sh.epc[threadIdx.x] = (float)beta * 3.814697265625e-06f;
         const double b0 = __shfl_sync(0xffffffffu, beta, 0);
         const bool same = __all_sync(0xffffffffu, beta == b0);
-        if (threadIdx.x == 0) sh.uni = same ? 1 : 0;
+        if (threadIdx.x == 0) {
+          sh.uni = same ? 1 : 0;
+          sh.ph = ph_shared(ph_key(J.key0, J.key1), J.b, t);
+        }
       }
       __syncthreads();
       cur_job = (int)tl.job;
@@ -319,7 +323,7 @@ __global__ void __launch_bounds__(kTile, 3) graph_half_kernel(const GraphJob* __
       uint4 w = make_uint4(0, 0, 0, 0);
 #pragma unroll
       for (int k = 0; k < 32; ++k) {
-        if ((k & 3) == 0) w = ph_call(K, x, J.b, t, typ + 2u * (uint32_t)(k >> 2));
+        if ((k & 3) == 0) w = ph_call_shared(K, sh.ph, x, typ + 2u * (uint32_t)(k >> 2));
         const uint32_t u = (k & 3) == 0 ? w.x : (k & 3) == 1 ? w.y : (k & 3) == 2 ? w.z : w.w;
         const bool up = (S >> k) & 1u;
         const float hk = __fadd_rn(__fadd_rn(h[k], up ? qf : -qf), lam);
