@@ -382,10 +382,12 @@ struct TileShared {
   const LatTable* tab_src;
 };
 
-// A lane word still undecided after planes 31..24, parked in its warp's queue.
+// A lane word with undecided lanes, parked in its warp's queue; `call` is the
+// next Philox call it needs (2..7: planes 4 call .. 4 call + 3).
 struct Pending {
-  uint32_t w, S, V, X, U, res;
+  uint32_t w, S, V, X, U, res, call;
 };
+
 
 
 template <int ENC>
@@ -403,19 +405,74 @@ __device__ __forceinline__ void store_word(const LatJob& J, void* dstbuf, uint32
   }
 }
 
+// One round of the warp's queue: the top n = min(qn, 32) entries each make their
+// next call and compare its four planes; finished words are stored, the others
+// go back on the queue.  qn is warp-uniform.
+template <int ENC, bool COLL>
+__device__ __forceinline__ void tail_round(const LatJob& J, const TileShared& sh,
+                                           Pending* __restrict__ q, uint32_t& qn,
+                                           const PhKey& K, uint32_t typ, void* dstbuf,
+                                           uint32_t& calls) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const uint32_t n = qn < 32u ? qn : 32u;
+  const uint32_t base = qn - n;
+  const bool act = (uint32_t)lane < n;
+  Pending e{};
+  if (act) e = q[base + lane];
+  __syncwarp();
+  bool still = false;
+  if (act) {
+    LaneWord L;
+    L.S = e.S;
+    L.V = e.V;
+    L.X = e.X;
+    L.U = e.U;
+    L.res = e.res;
+    const uint4 w = ph_call_shared(K, sh.ph, e.w, typ + 2u * e.call);
+    ++calls;
+    apply_call<COLL>(L, w, sh.tab, e.call);
+    if (L.U == 0u || e.call == 7u) {
+      store_word<ENC>(J, dstbuf, e.w, L.res);  // after plane 0 of call 7: u == T, tau = -1
+    } else {
+      still = true;
+      e.U = L.U;
+      e.res = L.res;
+      e.call += 1u;
+    }
+  }
+  const uint32_t sm = __ballot_sync(0xffffffffu, still);
+  if (still) q[base + __popc(sm & lt_mask)] = e;
+  qn = base + (uint32_t)__popc(sm);
+  __syncwarp();
+}
+
+// Every queued word of the warp to the end (before the staged job changes).
+template <int ENC>
+__device__ __forceinline__ void tail_drain(const LatJob& J, const TileShared& sh,
+                                           Pending* __restrict__ q, uint32_t& qn,
+                                           const PhKey& K, uint32_t typ, void* dstbuf,
+                                           uint32_t& calls) {
+  if (sh.tab.collapsed) {
+    while (qn != 0u) tail_round<ENC, true>(J, sh, q, qn, K, typ, dstbuf, calls);
+  } else {
+    while (qn != 0u) tail_round<ENC, false>(J, sh, q, qn, K, typ, dstbuf, calls);
+  }
+}
+
 // After the head: words with undecided lanes go to the warp's queue, the others
 // are stored; then the queue is finished 32 words at a time (planes 23..0).
 // With sh.fuse the sums of sigma_t over the words are accumulated as well.
 template <int ENC, int WPT, bool COLL, bool FULL>
 __device__ __forceinline__ void tile_commit(const LatJob& J, const TileShared& sh,
-                                            Pending* __restrict__ q, const PhKey& K,
-                                            const uint32_t (&a)[WPT], uint32_t t, uint32_t half,
-                                            const uint32_t (&S)[WPT], const uint32_t (&V)[WPT],
-                                            const uint32_t (&H)[WPT], const LaneWord (&Lws)[WPT],
-                                            void* dstbuf, double (&acc)[3], uint32_t& calls) {
+                                            Pending* __restrict__ q, uint32_t& qn,
+                                            const PhKey& K, const uint32_t (&a)[WPT],
+                                            uint32_t half, const uint32_t (&S)[WPT],
+                                            const uint32_t (&V)[WPT], const uint32_t (&H)[WPT],
+                                            const LaneWord (&Lws)[WPT], void* dstbuf,
+                                            double (&acc)[3], uint32_t& calls) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  uint32_t qn = 0;  // warp-uniform queue length
 #pragma unroll
   for (int k = 0; k < WPT; ++k) {
     const uint32_t w = a[k];
@@ -431,6 +488,7 @@ __device__ __forceinline__ void tile_commit(const LatJob& J, const TileShared& s
       e.X = Lw.X;
       e.U = Lw.U;
       e.res = Lw.res;
+      e.call = 2u;
     } else if (act) {
       store_word<ENC>(J, dstbuf, w, Lw.res);
     }
@@ -444,29 +502,20 @@ __device__ __forceinline__ void tile_commit(const LatJob& J, const TileShared& s
     }
   }
   __syncwarp();
-  for (uint32_t base = 0; base < qn; base += 32u) {
-    if (base + lane < qn) {
-      const Pending e = q[base + lane];
-      LaneWord Lw;
-      Lw.S = e.S;
-      Lw.V = e.V;
-      Lw.X = e.X;
-      Lw.U = e.U;
-      Lw.res = e.res;
-      decide_tail<COLL>(Lw, sh.tab, K, sh.ph, e.w, half, calls);
-      store_word<ENC>(J, dstbuf, e.w, Lw.res);
-    }
-  }
-  __syncwarp();
+  // words of this and earlier tiles wait until a full warp of them can go on
+  while (qn >= 32u) tail_round<ENC, COLL>(J, sh, q, qn, K, half, dstbuf, calls);
 }
 
-// Decisions of one tile: planes 31..24 of each of the thread's WPT lane words,
-// words with undecided lanes parked in the warp's queue, then the queue
-// finished 32 words at a time.  FULL: every word of the tile exists.
+// Decisions of one tile: planes 31..24 of each of the thread's WPT lane words;
+// words with undecided lanes go to the warp's queue, which runs whenever it holds
+// a full warp of them (one call per word and round; words still undecided go
+// back).  The queue carries over to the block's next tile of the same job and is
+// drained when the job changes.  FULL: every word of the tile exists.
 template <int ENC, int WPT, bool COLL, bool FULL>
 __device__ __forceinline__ void tile_decide(const LatJob& J, const TileShared& sh,
-                                            Pending* __restrict__ q, const PhKey& K, uint32_t w0,
-                                            uint32_t t, uint32_t half, const uint32_t (&S)[WPT],
+                                            Pending* __restrict__ q, uint32_t& qn,
+                                            const PhKey& K, uint32_t w0,
+                                            uint32_t half, const uint32_t (&S)[WPT],
                                             const uint32_t (&V)[WPT], const uint32_t (&H)[WPT],
                                             const uint32_t (&F)[WPT], void* dstbuf,
                                             double (&acc)[3], uint32_t& calls) {
@@ -480,34 +529,37 @@ __device__ __forceinline__ void tile_decide(const LatJob& J, const TileShared& s
   }
   decide_head_words<COLL, WPT>(Lws, sh.tab, K, sh.ph, a, half);
   calls += 2u * WPT;
-  tile_commit<ENC, WPT, COLL, FULL>(J, sh, q, K, a, t, half, S, V, H, Lws, dstbuf, acc, calls);
+  tile_commit<ENC, WPT, COLL, FULL>(J, sh, q, qn, K, a, half, S, V, H, Lws, dstbuf, acc, calls);
 }
 
 // Each block walks a contiguous range of tiles (kLatTile lane words each; a
 // tile never spans two jobs).  Per tile every thread loads the words of its
 // kWordsPerThread lane words (all loads in flight together) and runs planes
 // 31..24 of each; words with lanes still undecided are parked in the warp's
-// queue and finished afterwards 32 at a time, so the warp pays the rare later
-// planes once per 32 such words instead of once per word position.
+// queue, which makes the rare later calls only in full rounds of 32 words, so
+// the warp pays for them once per 32 such words instead of once per word position.
 template <int ENC, int WPT>
 __global__ void __launch_bounds__(kTile, kLatMinBlocks) lattice_half_kernel(const LatJob* __restrict__ jobs,
                                                                 const Tile* __restrict__ tiles,
                                                                 int n_tiles, uint32_t half,
                                                                 unsigned long long* rng_calls) {
   __shared__ TileShared sh;
-  __shared__ Pending queue[kTile / 32][32 * WPT];
+  __shared__ Pending queue[kTile / 32][32 * WPT + 32];  // a tile's words + fewer than 32 left
   __shared__ double red[(kTile / 32) * 3];
   uint32_t calls = 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t lt_mask = (1u << lane) - 1u;
   // balanced contiguous split: block b walks tiles [b n / G, (b+1) n / G)
   const int tb = (int)(((long long)blockIdx.x * n_tiles) / gridDim.x);
   const int te = (int)(((long long)(blockIdx.x + 1) * n_tiles) / gridDim.x);
   int cur_job = -1;
   PhKey K = ph_key(0u, 0u);  // the job's key schedule, rebuilt on job change only
+  uint32_t qn = 0;           // warp-uniform length of this warp's queue
   for (int ti = tb; ti < te; ++ti) {
     const Tile tl = tiles[ti];
     if ((int)tl.job != cur_job) {
+      if (qn != 0u)  // finish the previous job's queued words while its state is staged
+        tail_drain<ENC>(sh.job, sh, queue[warp], qn, K, sh.typ,
+                        half == 0u ? sh.job.B : sh.job.A, calls);
       __syncthreads();  // every warp is done with the previous job's staged state
       constexpr int nw = sizeof(LatJob) / 4;
       if (threadIdx.x < nw)
@@ -542,7 +594,6 @@ __global__ void __launch_bounds__(kTile, kLatMinBlocks) lattice_half_kernel(cons
     }
     if (sh.skip) continue;
     const LatJob& J = sh.job;
-    const uint32_t t = sh.t;
     const uint32_t typ = sh.typ;
     const void* src = half == 0u ? J.A : J.B;  // `half` is the position in the step
     void* dstbuf = half == 0u ? J.B : J.A;
@@ -561,17 +612,17 @@ __global__ void __launch_bounds__(kTile, kLatMinBlocks) lattice_half_kernel(cons
     const bool full_tile = tl.w0 + kTile * WPT <= J.nwords;
     if (sh.tab.collapsed) {
       if (full_tile)
-        tile_decide<ENC, WPT, true, true>(J, sh, queue[warp], K, tl.w0, t, typ, S, V, H, F,
+        tile_decide<ENC, WPT, true, true>(J, sh, queue[warp], qn, K, tl.w0, typ, S, V, H, F,
                                           dstbuf, acc, calls);
       else
-        tile_decide<ENC, WPT, true, false>(J, sh, queue[warp], K, tl.w0, t, typ, S, V, H, F,
+        tile_decide<ENC, WPT, true, false>(J, sh, queue[warp], qn, K, tl.w0, typ, S, V, H, F,
                                            dstbuf, acc, calls);
     } else {
       if (full_tile)
-        tile_decide<ENC, WPT, false, true>(J, sh, queue[warp], K, tl.w0, t, typ, S, V, H, F,
+        tile_decide<ENC, WPT, false, true>(J, sh, queue[warp], qn, K, tl.w0, typ, S, V, H, F,
                                            dstbuf, acc, calls);
       else
-        tile_decide<ENC, WPT, false, false>(J, sh, queue[warp], K, tl.w0, t, typ, S, V, H, F,
+        tile_decide<ENC, WPT, false, false>(J, sh, queue[warp], qn, K, tl.w0, typ, S, V, H, F,
                                             dstbuf, acc, calls);
     }
     if (sh.fuse) {
@@ -581,6 +632,9 @@ __global__ void __launch_bounds__(kTile, kLatMinBlocks) lattice_half_kernel(cons
       block_sum_atomic<1>(v1, J.sums + kSumCut, red);
     }
   }
+  if (qn != 0u)
+    tail_drain<ENC>(sh.job, sh, queue[warp], qn, K, sh.typ, half == 0u ? sh.job.B : sh.job.A,
+                    calls);
   if (rng_calls != nullptr) {
     const uint32_t wsum = __reduce_add_sync(0xffffffffu, calls);
     if (lane == 0 && wsum) atomicAdd(rng_calls, (unsigned long long)wsum);
