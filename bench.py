@@ -166,6 +166,8 @@ def run_ours(args, rank, world, local_rank):
         c = S.shaken_init(p, seeds[g], stream)
         S.shaken_batch_add(batch, c)
         ctxs.append(c)
+    if args.no_autotune:  # fixed launch-shape rule (profiling runs: no timed trial launches)
+        S.shaken_batch_set_autotune(batch, False)
     tile_wpt = S.shaken_batch_lattice_wpt(batch, S.MULTISPIN)  # autotuned launch shape
     # RNG accounting over two warm-up steps (not timed)
     counter = torch.zeros(1, dtype=torch.int64, device=dev)
@@ -669,6 +671,8 @@ def main():
     ap.add_argument("--only-graphs", action="store_true",
                     help="run the sparse-graph section only (profiling runs)")
     ap.add_argument("--only-serving", action="store_true", help="run the serving section only")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="fixed lattice launch-shape rule instead of timed trials (profiling)")
     ap.add_argument("--graph-anneal-steps", type=int, default=5000)
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--serve-horizon", type=float, default=8.0,
