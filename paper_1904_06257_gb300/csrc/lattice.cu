@@ -832,7 +832,7 @@ __global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* _
   constexpr int SENC = ENC == kEncMultispin ? kEncMultispin : kEncPacked;  // smem layout
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ LatTable stab;
-  __shared__ double red[kTile / 32][3];
+  __shared__ int red[kTile / 32][3];
   const LatJob J = jobs[blockIdx.x];  // by value: the fields stay in registers
   const uint32_t nw = J.nwords;
   uint32_t* sA = smem;
@@ -842,6 +842,16 @@ __global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* _
   const bool track = ENC != kEncMultispin && cd->tracking && J.sums != nullptr;
   const uint32_t order = cd->order;
   const bool record = track && cd->record;
+  // the context's constants for the per-step tracking, read once (nothing else
+  // touches this context while the run is resident); the best energy in a register
+  const uint32_t r = J.rep0;
+  const double Jc = cd->Jc, lamc = cd->lamc, inv_n = cd->inv_n;
+  const uint32_t series_t0 = cd->series_t0, series_cap = cd->series_cap, Rn = cd->R;
+  double* const best_p = cd->best;
+  long long* const best_step_p = cd->best_step;
+  double* const series_m = cd->series_m;
+  double* const series_H = cd->series_H;
+  double best = track && threadIdx.x == 0 ? best_p[r] : 0.0;
   for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) sA[w] = resident_load<ENC>(J, w);
   const PhKey K = ph_key(J.key0, J.key1);
   const LatTable* staged = nullptr;
@@ -863,7 +873,7 @@ __global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* _
     }
     __syncthreads();  // sA complete (previous half step or the load), table staged
     const PhShared P = ph_shared(K, J.b, t);
-    double acc[3] = {0.0, 0.0, 0.0};
+    int acc[3] = {0, 0, 0};  // integer sums (at most 32 x 4096 sites per block)
     for (uint32_t pos = 0; pos < 2; ++pos) {
       const uint32_t half = pos ^ order;  // update type of this position
       const uint32_t* in = pos == 0u ? sA : sB;
@@ -885,9 +895,9 @@ __global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* _
         out[w] = Lw.res;
         if (track && pos == 0u) {
           const int dv = __popc(S ^ V), dh = __popc(S ^ H);
-          acc[0] += (double)(2 * __popc(S) - 32);
-          acc[1] += (double)(64 - 2 * dv - 2 * dh);
-          acc[2] += (double)(dv + dh);
+          acc[0] += 2 * __popc(S) - 32;
+          acc[1] += 64 - 2 * dv - 2 * dh;
+          acc[2] += dv + dh;
         }
       }
       __syncthreads();
@@ -895,28 +905,27 @@ __global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* _
     if (track) {
       // block totals of sigma_t's sums -> best energy and series (Eq. (HGibbs))
 #pragma unroll
-      for (int q = 0; q < 3; ++q)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+      for (int q = 0; q < 2; ++q) acc[q] = __reduce_add_sync(0xffffffffu, acc[q]);
       if ((threadIdx.x & 31) == 0)
-        for (int q = 0; q < 3; ++q) red[threadIdx.x >> 5][q] = acc[q];
+        for (int q = 0; q < 2; ++q) red[threadIdx.x >> 5][q] = acc[q];
       __syncthreads();
       if (threadIdx.x == 0) {
-        double M = 0.0, E = 0.0;
+        int Mi = 0, Ei = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-          M += red[w][0];
-          E += red[w][1];
+          Mi += red[w][0];
+          Ei += red[w][1];
         }
-        const double Hs = -(cd->Jc * E) - 2.0 * cd->lamc * M;
-        const uint32_t r = J.rep0;
-        if (Hs < cd->best[r]) {
-          cd->best[r] = Hs;
-          cd->best_step[r] = (long long)t;
+        const double M = (double)Mi, E = (double)Ei;
+        const double Hs = -(Jc * E) - 2.0 * lamc * M;
+        if (Hs < best) {
+          best = Hs;
+          best_p[r] = Hs;
+          best_step_p[r] = (long long)t;
         }
-        if (record && t - cd->series_t0 < cd->series_cap) {
-          const size_t k = (size_t)(t - cd->series_t0) * cd->R + r;
-          if (cd->series_m) cd->series_m[k] = M * cd->inv_n;
-          if (cd->series_H) cd->series_H[k] = Hs;
+        if (record && t - series_t0 < series_cap) {
+          const size_t k = (size_t)(t - series_t0) * Rn + r;
+          if (series_m) series_m[k] = M * inv_n;
+          if (series_H) series_H[k] = Hs;
         }
       }
     }
