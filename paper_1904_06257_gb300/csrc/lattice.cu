@@ -303,6 +303,26 @@ __device__ __forceinline__ void block_sum_atomic(double (&v)[NV], double* dst, d
   __syncthreads();
 }
 
+// Integer block sums added to fp64 totals (one atomic per value and block).
+template <int NV>
+__device__ __forceinline__ void block_sum_atomic_int(int (&v)[NV], double* dst, int* smem) {
+  // smem: at least (blockDim/32) * NV ints
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = __reduce_add_sync(0xffffffffu, v[k]);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) smem[warp * NV + k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    long long s = 0;
+    for (int w = 0; w < nw; ++w) s += smem[w * NV + threadIdx.x];
+    if (s != 0) atomicAdd(dst + threadIdx.x, (double)s);
+  }
+  __syncthreads();
+}
+
 // --------------------------------------------------------------------------- half step
 enum { kEncInt8 = 0, kEncPacked = 1, kEncMultispin = 2 };
 
@@ -470,7 +490,7 @@ __device__ __forceinline__ void tile_commit(const LatJob& J, const TileShared& s
                                             uint32_t half, const uint32_t (&S)[WPT],
                                             const uint32_t (&V)[WPT], const uint32_t (&H)[WPT],
                                             const LaneWord (&Lws)[WPT], void* dstbuf,
-                                            double (&acc)[3], uint32_t& calls) {
+                                            int (&acc)[3], uint32_t& calls) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
@@ -496,9 +516,9 @@ __device__ __forceinline__ void tile_commit(const LatJob& J, const TileShared& s
     if (ENC != kEncMultispin && sh.fuse && act) {
       // sums of sigma_t over the lane word: M, E (in-edges down and left), cut
       const int dv = __popc(S[k] ^ V[k]), dh = __popc(S[k] ^ H[k]);
-      acc[0] += (double)(2 * __popc(S[k]) - 32);
-      acc[1] += (double)(64 - 2 * dv - 2 * dh);
-      acc[2] += (double)(dv + dh);
+      acc[0] += 2 * __popc(S[k]) - 32;
+      acc[1] += 64 - 2 * dv - 2 * dh;
+      acc[2] += dv + dh;
     }
   }
   __syncwarp();
@@ -518,7 +538,7 @@ __device__ __forceinline__ void tile_decide(const LatJob& J, const TileShared& s
                                             uint32_t half, const uint32_t (&S)[WPT],
                                             const uint32_t (&V)[WPT], const uint32_t (&H)[WPT],
                                             const uint32_t (&F)[WPT], void* dstbuf,
-                                            double (&acc)[3], uint32_t& calls) {
+                                            int (&acc)[3], uint32_t& calls) {
   LaneWord Lws[WPT];
   uint32_t a[WPT];
 #pragma unroll
@@ -608,7 +628,7 @@ __global__ void __launch_bounds__(kTile, kLatMinBlocks) lattice_half_kernel(cons
         if (J.frozen != nullptr) F[k] = __ldg(J.frozen + w);
       }
     }
-    double acc[3] = {0.0, 0.0, 0.0};
+    int acc[3] = {0, 0, 0};  // tracking sums of this tile (|sum| <= 64 per word)
     const bool full_tile = tl.w0 + kTile * WPT <= J.nwords;
     if (sh.tab.collapsed) {
       if (full_tile)
@@ -626,10 +646,11 @@ __global__ void __launch_bounds__(kTile, kLatMinBlocks) lattice_half_kernel(cons
                                             dstbuf, acc, calls);
     }
     if (sh.fuse) {
-      double v2[2] = {acc[0], acc[1]};
-      block_sum_atomic<2>(v2, J.sums + kSumM, red);
-      double v1[1] = {acc[2]};
-      block_sum_atomic<1>(v1, J.sums + kSumCut, red);
+      int* redi = reinterpret_cast<int*>(red);
+      int v2[2] = {acc[0], acc[1]};
+      block_sum_atomic_int<2>(v2, J.sums + kSumM, redi);
+      int v1[1] = {acc[2]};
+      block_sum_atomic_int<1>(v1, J.sums + kSumCut, redi);
     }
   }
   if (qn != 0u)
