@@ -152,3 +152,34 @@ def test_device_philox_and_thresholds_match_oracle(S):
     T = dout.cpu().numpy().astype(np.uint64)
     for i in range(h.size):
         assert int(T[i]) == core.threshold(h[i], beta[i]), (h[i], beta[i])
+
+
+def test_server_free_cancels_queued_and_running_jobs(S):
+    # a job far too long to finish and one queued behind it (budget fits one job):
+    # freeing the server stops after the current chunk and releases both
+    import time
+    n = 4000
+    u, v = W.erdos_renyi(n, 6.0, 17)
+    J = W.couplings_pm1(u.size, 18)
+    p = graph_problem(S, n, u, v, J, 64, 1.0)
+    srv = S.shaken_server_create(300_000, 8)  # one ~206 kB job fits at a time
+    sched = W.linear_schedule(0.2, 2.0, 2_000_000)
+    a = S.shaken_server_submit(srv, p, 1, sched)
+    b = S.shaken_server_submit(srv, p, 2, sched)
+    t_end = time.perf_counter() + 30.0
+    while S.shaken_server_poll(srv, a) != 1 and time.perf_counter() < t_end:
+        time.sleep(0.01)
+    assert S.shaken_server_poll(srv, a) == 1   # running
+    assert S.shaken_server_poll(srv, b) == 0   # queued behind it
+    t0 = time.perf_counter()
+    S.shaken_server_free(srv)
+    assert time.perf_counter() - t0 < 10.0
+
+
+def test_microbenchmarks(S):
+    for kind in range(8):
+        rate, ms = S.shaken_microbench(kind)
+        assert rate > 0 and ms > 0
+    for bad in (-1, 8):
+        with pytest.raises(S.ShakenError):
+            S.shaken_microbench(bad)
