@@ -58,40 +58,79 @@ def lib():
     global _LIB
     with _LOCK:
         if _LIB is None:
-            L = ctypes.CDLL(build())
-            u32, u64, i64, d = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64, ctypes.c_double
-            vp = ctypes.c_void_p
-            L.orc_philox.argtypes = [vp, vp, vp]
-            L.orc_exp.argtypes = [d]
-            L.orc_exp.restype = d
-            L.orc_threshold.argtypes = [d, d]
-            L.orc_threshold.restype = u64
-            L.orc_field.argtypes = [d, i64, d, ctypes.c_int, d]
-            L.orc_field.restype = d
-            L.orc_draw_plane.argtypes = [u64, u32, u32, u32, u32, ctypes.c_int]
-            L.orc_draw_plane.restype = u32
-            L.orc_draw_direct.argtypes = [u64, u32, u32, u32, u32, ctypes.c_int]
-            L.orc_draw_direct.restype = u32
-            L.orc_lattice_init.argtypes = [vp, i64, i64, vp, u64, ctypes.c_int, ctypes.c_int]
-            L.orc_lattice_site.argtypes = [vp, i64, i64, i64, vp, d, d, d, d, u64, u32,
-                                           ctypes.c_int, ctypes.c_int, i64]
-            L.orc_lattice_site.restype = ctypes.c_int
-            L.orc_lattice_half.argtypes = [vp, vp, i64, i64, vp, d, d, d, vp, u64, u32,
-                                           ctypes.c_int, ctypes.c_int]
-            L.orc_lattice_run.argtypes = [vp, vp, i64, i64, vp, d, d, d, vp, u64, u32, i64,
-                                          ctypes.c_int]
-            L.orc_lattice_anneal.argtypes = [vp, vp, i64, i64, vp, d, d, d, vp, u64, u32, i64,
-                                             ctypes.c_int]
-            L.orc_lattice_sums.argtypes = [vp, vp, i64, vp]
-            L.orc_orient.argtypes = [i64, vp, vp, ctypes.c_int, vp, vp]
-            L.orc_graph_half.argtypes = [vp, vp, i64, i64, vp, vp, vp, ctypes.c_int, vp, vp, d,
-                                         vp, i64, u64, u32, ctypes.c_int]
-            L.orc_graph_init.argtypes = [vp, i64, i64, vp, u64, ctypes.c_int]
-            L.orc_graph_run.argtypes = [vp, vp, i64, i64, vp, vp, vp, ctypes.c_int, vp, vp, d,
-                                        vp, vp, i64, u64, u32, i64]
-            L.orc_graph_sums.argtypes = [vp, vp, i64, i64, vp, vp, vp, vp, vp]
-            _LIB = L
+            _LIB = _open(build())
     return _LIB
+
+
+def build_variant(source: str, tag: str) -> str:
+    """Compile a modified copy of the oracle source (the planted-mistake tests) into
+    ``oracle/_build/liboracle_<tag>.so`` with the flags of ``build``."""
+    os.makedirs(_BUILD, exist_ok=True)
+    src = os.path.join(_BUILD, f"variant_{tag}.c")
+    so = os.path.join(_BUILD, f"liboracle_{tag}.so")
+    with open(src, "w") as f:
+        f.write(source)
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-shared", "-fPIC",
+           "-o", so, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    return so
+
+
+class using:
+    """Context manager: every wrapper below calls the library at `path` instead."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _LIB
+        lib()
+        with _LOCK:
+            self.saved = _LIB
+            _LIB = _open(self.path)
+        return self
+
+    def __exit__(self, *exc):
+        global _LIB
+        with _LOCK:
+            _LIB = self.saved
+        return False
+
+
+def _open(path: str):
+    L = ctypes.CDLL(path)
+    u32, u64, i64, d = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64, ctypes.c_double
+    vp = ctypes.c_void_p
+    L.orc_philox.argtypes = [vp, vp, vp]
+    L.orc_exp.argtypes = [d]
+    L.orc_exp.restype = d
+    L.orc_threshold.argtypes = [d, d]
+    L.orc_threshold.restype = u64
+    L.orc_field.argtypes = [d, i64, d, ctypes.c_int, d]
+    L.orc_field.restype = d
+    L.orc_draw_plane.argtypes = [u64, u32, u32, u32, u32, ctypes.c_int]
+    L.orc_draw_plane.restype = u32
+    L.orc_draw_direct.argtypes = [u64, u32, u32, u32, u32, ctypes.c_int]
+    L.orc_draw_direct.restype = u32
+    L.orc_lattice_init.argtypes = [vp, i64, i64, vp, u64, ctypes.c_int, ctypes.c_int]
+    L.orc_lattice_site.argtypes = [vp, i64, i64, i64, vp, d, d, d, d, u64, u32,
+                                   ctypes.c_int, ctypes.c_int, i64]
+    L.orc_lattice_site.restype = ctypes.c_int
+    L.orc_lattice_half.argtypes = [vp, vp, i64, i64, vp, d, d, d, vp, u64, u32,
+                                   ctypes.c_int, ctypes.c_int]
+    L.orc_lattice_run.argtypes = [vp, vp, i64, i64, vp, d, d, d, vp, u64, u32, i64,
+                                  ctypes.c_int]
+    L.orc_lattice_anneal.argtypes = [vp, vp, i64, i64, vp, d, d, d, vp, u64, u32, i64,
+                                     ctypes.c_int]
+    L.orc_lattice_sums.argtypes = [vp, vp, i64, vp]
+    L.orc_orient.argtypes = [i64, vp, vp, ctypes.c_int, vp, vp]
+    L.orc_graph_half.argtypes = [vp, vp, i64, i64, vp, vp, vp, ctypes.c_int, vp, vp, d,
+                                 vp, i64, u64, u32, ctypes.c_int]
+    L.orc_graph_init.argtypes = [vp, i64, i64, vp, u64, ctypes.c_int]
+    L.orc_graph_run.argtypes = [vp, vp, i64, i64, vp, vp, vp, ctypes.c_int, vp, vp, d,
+                                vp, vp, i64, u64, u32, i64]
+    L.orc_graph_sums.argtypes = [vp, vp, i64, i64, vp, vp, vp, vp, vp]
+    return L
 
 
 def _ptr(a):
