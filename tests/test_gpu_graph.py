@@ -174,3 +174,50 @@ def test_fused_tracking_best_energy(S):
     H = np.array([o["H"] for o in core.graph_observables(cur, cur, tail, head, Jd, ld, 1.0)])
     best = np.minimum(best, H)
     assert np.allclose(obs["best_energy"], best, rtol=1e-6, atol=1e-4)
+
+
+def test_full_size_anneal_step_sampled(S):
+    """The bench's graph workload (Erdos-Renyi n = 10^6, mean degree 8, +-1 couplings,
+    lambda_x ~ N(0, 0.1^2), q = 1, 256 replicas, one anneal step with its beta on every
+    replica and the best-energy tracking fused into half 0): sampled (vertex, replica)
+    pairs of the full step against the oracle's single-site decisions."""
+    n, R, q, beta = 1_000_000, 256, 1.0, 1.7
+    u, v = W.erdos_renyi(n, 8.0, W.BASE_SEED + 1)
+    J = W.couplings_pm1(u.size, W.BASE_SEED + 2)
+    lam = W.fields_normal(n, 0.1, W.BASE_SEED + 3)
+    seed = W.BASE_SEED + 11
+    ctx = S.shaken_init(graph_problem(S, n, u, v, J, R, 0.1, q=q, lam=lam), seed)
+    S.shaken_step(ctx, 2)
+    S.shaken_set_tracking(ctx, True)
+    s0 = S.shaken_get_spins(ctx, R, n)
+    S.shaken_anneal(ctx, np.array([beta]))
+    s1 = S.shaken_get_spins(ctx, R, n)
+    S.shaken_free(ctx)
+    tail, head = core.orient(u, v, 0)
+    order_in, order_out = np.argsort(head, kind="stable"), np.argsort(tail, kind="stable")
+    in_ptr = np.searchsorted(head[order_in], np.arange(n + 1))
+    out_ptr = np.searchsorted(tail[order_out], np.arange(n + 1))
+    t = 2
+
+    def site(sr, x, half, r):
+        # tau_x from the in-neighbours (half 0) or out-neighbours (half 1) of x in sr
+        if half == 0:
+            es = order_in[in_ptr[x]:in_ptr[x + 1]]
+            ys = tail[es]
+        else:
+            es = order_out[out_ptr[x]:out_ptr[x + 1]]
+            ys = head[es]
+        s = int(np.sum(np.where(J[es] > 0, 1, -1) * sr[ys].astype(np.int64)))
+        h = core.field(1.0, s, q, int(sr[x]), float(lam[x]))
+        T = core.threshold(h, beta)
+        uu = core.draw_direct(seed, x, r >> 5, t, half, r & 31)
+        return 1 if uu < T else -1
+
+    g = np.random.default_rng(21)
+    for _ in range(150):
+        x, r = int(g.integers(n)), int(g.integers(R))
+        sr = s0[r].copy()
+        ys = head[order_out[out_ptr[x]:out_ptr[x + 1]]]
+        for y in list(ys) + [x]:  # sigma' where the second half step reads it
+            sr[y] = site(s0[r], int(y), 0, r)
+        assert s1[r, x] == site(sr, x, 1, r), (x, r)
