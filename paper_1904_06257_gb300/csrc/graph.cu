@@ -87,7 +87,9 @@ struct GraphShared;
 // u (1 + e~) > 2^32 (1 + eps); otherwise its bit is set in `und` for the fp64 test.
 // eps = 2^-18 + 2^-18 beta B, B = d + |q| + |lambda| + 1, is at least five times the
 // fp32 error of the compared products (h~: three roundings of magnitude <= B;
-// kb h~; ex2.approx, relative error 2^-22; 1 + e~; u to float; the product).
+// kb h~ -- with one beta on all lanes kb (2 cnt) + kb base, kb base rounded once,
+// in one fused multiply-add, the same bound; ex2.approx, relative error 2^-22;
+// 1 + e~; u to float; the product).
 template <bool UNI>
 __device__ __forceinline__ void int_lanes(const uint32_t (&C)[8], uint32_t S, const PhKey& K,
                                           uint32_t x, uint32_t b, uint32_t t, uint32_t typ,
@@ -112,9 +114,12 @@ __device__ __forceinline__ void int_lanes(const uint32_t (&C)[8], uint32_t S, co
                                           const GraphShared& sh, bool fuse, float (*acc)[32],
                                           int lane, uint32_t& res, uint32_t& und) {
   const float two32 = 4294967296.0f;
-  float kb0 = 0.0f, lo0 = 0.0f, hi0 = 0.0f;
-  if (UNI) {
-    kb0 = sh.kb[0];
+  float kb2 = 0.0f, kbp = 0.0f, kbm = 0.0f, lo0 = 0.0f, hi0 = 0.0f;
+  if (UNI) {  // one beta: the exponent kb (2 cnt + base) is one fused multiply-add
+    const float kb0 = sh.kb[0];
+    kb2 = 2.0f * kb0;
+    kbp = kb0 * bp;
+    kbm = kb0 * bm;
     const float eps = 3.814697265625e-06f + sh.epc[0] * B;
     lo0 = two32 * (1.0f - eps);
     hi0 = two32 * (1.0f + eps);
@@ -134,15 +139,17 @@ __device__ __forceinline__ void int_lanes(const uint32_t (&C)[8], uint32_t S, co
       const float cf = __fsub_rn(__int_as_float((int)__byte_perm(C[m], 0x4B000000u, selb)),
                                  8388608.0f);
       const bool up = (s8 >> m) & 1u;
-      const float hf = __fmaf_rn(2.0f, cf, up ? bp : bm);
-      float kb = kb0, lo = lo0, hi = hi0;
-      if (!UNI) {
-        kb = sh.kb[k];
+      float x, lo = lo0, hi = hi0;
+      if (UNI) {
+        x = __fmaf_rn(kb2, cf, up ? kbp : kbm);
+      } else {
+        const float hf = __fmaf_rn(2.0f, cf, up ? bp : bm);
+        x = sh.kb[k] * hf;
         const float eps = 3.814697265625e-06f + sh.epc[k] * B;
         lo = two32 * (1.0f - eps);
         hi = two32 * (1.0f + eps);
       }
-      const float onep = 1.0f + ex2_approx(kb * hf);
+      const float onep = 1.0f + ex2_approx(x);
       const float uf = __uint2float_rn(uw[m]);
       const bool plus = __fmaf_rn(uf, onep, onep) < lo;
       const bool minus = uf * onep > hi;
