@@ -198,7 +198,8 @@ __device__ __forceinline__ void decide_head(LaneWord& L, const LatTable& tab, co
 // are compared as an eight-bit subtraction, least significant plane first:
 // the borrow lt <- maj(~w, P, lt) ends as [u_top < T_top] and eq as
 // [u_top == T_top].  Lanes with equal top bits stay undecided for planes 23..0
-// (decide_tail); the others are decided exactly as by the first differing plane.
+// (the warp queue of the tiled kernel, or decide_tail); the others are decided
+// exactly as by the first differing plane.
 // Four planes of one call (planes 4c+3 .. 4c, least significant first) for
 // the WPT words: one step of the borrow chain per plane.
 template <bool COLL, int WPT>
@@ -248,7 +249,8 @@ __device__ __forceinline__ void decide_head_words(LaneWord (&Lw)[WPT], const Lat
   head_finish<WPT>(Lw, lt, eq);
 }
 
-// Calls 2..7 while some lane is undecided.
+// Calls 2..7 while some lane is undecided (one word at a time: the resident
+// small-lattice kernel).
 template <bool COLL>
 __device__ __forceinline__ void decide_tail(LaneWord& L, const LatTable& tab, const PhKey& K,
                                             const PhShared& P, uint32_t a, uint32_t half,
@@ -481,8 +483,9 @@ __device__ __forceinline__ void tail_drain(const LatJob& J, const TileShared& sh
 }
 
 // After the head: words with undecided lanes go to the warp's queue, the others
-// are stored; then the queue is finished 32 words at a time (planes 23..0).
-// With sh.fuse the sums of sigma_t over the words are accumulated as well.
+// are stored; the queue runs a round (one more call for each of 32 words, planes
+// 23..0 four at a time) whenever it holds 32 words.  With sh.fuse the sums of
+// sigma_t over the words are accumulated as well.
 template <int ENC, int WPT, bool COLL, bool FULL>
 __device__ __forceinline__ void tile_commit(const LatJob& J, const TileShared& sh,
                                             Pending* __restrict__ q, uint32_t& qn,
