@@ -404,11 +404,12 @@ struct TileShared {
   const LatTable* tab_src;
 };
 
-// A lane word with undecided lanes, parked in its warp's queue; `call` is the
-// next Philox call it needs (2..7: planes 4 call .. 4 call + 3).
-struct Pending {
-  uint32_t w, S, V, X, U, res, call;
-};
+// A lane word with undecided lanes, parked in its warp's queue as one 16-byte
+// entry: (w, U, res, call), `call` the next Philox call it needs (2..7: planes
+// 4 call .. 4 call + 3).  The class bits are recomputed from the state when the
+// word's round comes (the source buffer does not change during the half step),
+// so parking a word is a single 16-byte store.
+using Pending = uint4;
 
 
 
@@ -433,34 +434,36 @@ __device__ __forceinline__ void store_word(const LatJob& J, void* dstbuf, uint32
 template <int ENC, bool COLL>
 __device__ __forceinline__ void tail_round(const LatJob& J, const TileShared& sh,
                                            Pending* __restrict__ q, uint32_t& qn,
-                                           const PhKey& K, uint32_t typ, void* dstbuf,
-                                           uint32_t& calls) {
+                                           const PhKey& K, uint32_t typ, const void* srcbuf,
+                                           void* dstbuf, uint32_t& calls) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt_mask = (1u << lane) - 1u;
   const uint32_t n = qn < 32u ? qn : 32u;
   const uint32_t base = qn - n;
   const bool act = (uint32_t)lane < n;
-  Pending e{};
+  Pending e = make_uint4(0u, 0u, 0u, 0u);  // (w, U, res, call)
   if (act) e = q[base + lane];
   __syncwarp();
   bool still = false;
   if (act) {
+    const uint4 w = ph_call_shared(K, sh.ph, e.x, typ + 2u * e.w);
+    uint32_t S, V, H;
+    load_lane_words<ENC>(J, srcbuf, e.x, typ, S, V, H);
     LaneWord L;
-    L.S = e.S;
-    L.V = e.V;
-    L.X = e.X;
-    L.U = e.U;
-    L.res = e.res;
-    const uint4 w = ph_call_shared(K, sh.ph, e.w, typ + 2u * e.call);
+    L.S = S;
+    L.V = COLL ? ((V & H) | (S & (V | H))) : V;  // as classify: majority / in-neighbour
+    L.X = COLL ? (V ^ H ^ S) : (V ^ H);          // parity / one +1 neighbour
+    L.U = e.y;
+    L.res = e.z;
     ++calls;
-    apply_call<COLL>(L, w, sh.tab, e.call);
-    if (L.U == 0u || e.call == 7u) {
-      store_word<ENC>(J, dstbuf, e.w, L.res);  // after plane 0 of call 7: u == T, tau = -1
+    apply_call<COLL>(L, w, sh.tab, e.w);
+    if (L.U == 0u || e.w == 7u) {
+      store_word<ENC>(J, dstbuf, e.x, L.res);  // after plane 0 of call 7: u == T, tau = -1
     } else {
       still = true;
-      e.U = L.U;
-      e.res = L.res;
-      e.call += 1u;
+      e.y = L.U;
+      e.z = L.res;
+      e.w += 1u;
     }
   }
   const uint32_t sm = __ballot_sync(0xffffffffu, still);
@@ -473,12 +476,12 @@ __device__ __forceinline__ void tail_round(const LatJob& J, const TileShared& sh
 template <int ENC>
 __device__ __forceinline__ void tail_drain(const LatJob& J, const TileShared& sh,
                                            Pending* __restrict__ q, uint32_t& qn,
-                                           const PhKey& K, uint32_t typ, void* dstbuf,
-                                           uint32_t& calls) {
+                                           const PhKey& K, uint32_t typ, const void* srcbuf,
+                                           void* dstbuf, uint32_t& calls) {
   if (sh.tab.collapsed) {
-    while (qn != 0u) tail_round<ENC, true>(J, sh, q, qn, K, typ, dstbuf, calls);
+    while (qn != 0u) tail_round<ENC, true>(J, sh, q, qn, K, typ, srcbuf, dstbuf, calls);
   } else {
-    while (qn != 0u) tail_round<ENC, false>(J, sh, q, qn, K, typ, dstbuf, calls);
+    while (qn != 0u) tail_round<ENC, false>(J, sh, q, qn, K, typ, srcbuf, dstbuf, calls);
   }
 }
 
@@ -492,8 +495,8 @@ __device__ __forceinline__ void tile_commit(const LatJob& J, const TileShared& s
                                             const PhKey& K, const uint32_t (&a)[WPT],
                                             uint32_t half, const uint32_t (&S)[WPT],
                                             const uint32_t (&V)[WPT], const uint32_t (&H)[WPT],
-                                            const LaneWord (&Lws)[WPT], void* dstbuf,
-                                            int (&acc)[3], uint32_t& calls) {
+                                            const LaneWord (&Lws)[WPT], const void* srcbuf,
+                                            void* dstbuf, int (&acc)[3], uint32_t& calls) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
@@ -504,14 +507,7 @@ __device__ __forceinline__ void tile_commit(const LatJob& J, const TileShared& s
     const bool pend = act && Lw.U != 0u;
     const uint32_t pm = __ballot_sync(0xffffffffu, pend);
     if (pend) {
-      Pending& e = q[qn + __popc(pm & lt_mask)];
-      e.w = w;
-      e.S = COLL ? 0u : Lw.S;  // the collapsed planes do not use sigma
-      e.V = Lw.V;
-      e.X = Lw.X;
-      e.U = Lw.U;
-      e.res = Lw.res;
-      e.call = 2u;
+      q[qn + __popc(pm & lt_mask)] = make_uint4(w, Lw.U, Lw.res, 2u);
     } else if (act) {
       store_word<ENC>(J, dstbuf, w, Lw.res);
     }
@@ -526,7 +522,7 @@ __device__ __forceinline__ void tile_commit(const LatJob& J, const TileShared& s
   }
   __syncwarp();
   // words of this and earlier tiles wait until a full warp of them can go on
-  while (qn >= 32u) tail_round<ENC, COLL>(J, sh, q, qn, K, half, dstbuf, calls);
+  while (qn >= 32u) tail_round<ENC, COLL>(J, sh, q, qn, K, half, srcbuf, dstbuf, calls);
 }
 
 // Decisions of one tile: planes 31..24 of each of the thread's WPT lane words;
@@ -540,8 +536,8 @@ __device__ __forceinline__ void tile_decide(const LatJob& J, const TileShared& s
                                             const PhKey& K, uint32_t w0,
                                             uint32_t half, const uint32_t (&S)[WPT],
                                             const uint32_t (&V)[WPT], const uint32_t (&H)[WPT],
-                                            const uint32_t (&F)[WPT], void* dstbuf,
-                                            int (&acc)[3], uint32_t& calls) {
+                                            const uint32_t (&F)[WPT], const void* srcbuf,
+                                            void* dstbuf, int (&acc)[3], uint32_t& calls) {
   LaneWord Lws[WPT];
   uint32_t a[WPT];
 #pragma unroll
@@ -552,7 +548,8 @@ __device__ __forceinline__ void tile_decide(const LatJob& J, const TileShared& s
   }
   decide_head_words<COLL, WPT>(Lws, sh.tab, K, sh.ph, a, half);
   calls += 2u * WPT;
-  tile_commit<ENC, WPT, COLL, FULL>(J, sh, q, qn, K, a, half, S, V, H, Lws, dstbuf, acc, calls);
+  tile_commit<ENC, WPT, COLL, FULL>(J, sh, q, qn, K, a, half, S, V, H, Lws, srcbuf, dstbuf, acc,
+                                    calls);
 }
 
 // Each block walks a contiguous range of tiles (kLatTile lane words each; a
@@ -582,7 +579,8 @@ __global__ void __launch_bounds__(kTile, kLatMinBlocks) lattice_half_kernel(cons
     if ((int)tl.job != cur_job) {
       if (qn != 0u)  // finish the previous job's queued words while its state is staged
         tail_drain<ENC>(sh.job, sh, queue[warp], qn, K, sh.typ,
-                        half == 0u ? sh.job.B : sh.job.A, calls);
+                        half == 0u ? sh.job.A : sh.job.B, half == 0u ? sh.job.B : sh.job.A,
+                        calls);
       __syncthreads();  // every warp is done with the previous job's staged state
       constexpr int nw = sizeof(LatJob) / 4;
       if (threadIdx.x < nw)
@@ -636,17 +634,17 @@ __global__ void __launch_bounds__(kTile, kLatMinBlocks) lattice_half_kernel(cons
     if (sh.tab.collapsed) {
       if (full_tile)
         tile_decide<ENC, WPT, true, true>(J, sh, queue[warp], qn, K, tl.w0, typ, S, V, H, F,
-                                          dstbuf, acc, calls);
+                                          src, dstbuf, acc, calls);
       else
         tile_decide<ENC, WPT, true, false>(J, sh, queue[warp], qn, K, tl.w0, typ, S, V, H, F,
-                                           dstbuf, acc, calls);
+                                           src, dstbuf, acc, calls);
     } else {
       if (full_tile)
         tile_decide<ENC, WPT, false, true>(J, sh, queue[warp], qn, K, tl.w0, typ, S, V, H, F,
-                                           dstbuf, acc, calls);
+                                           src, dstbuf, acc, calls);
       else
         tile_decide<ENC, WPT, false, false>(J, sh, queue[warp], qn, K, tl.w0, typ, S, V, H, F,
-                                            dstbuf, acc, calls);
+                                            src, dstbuf, acc, calls);
     }
     if (sh.fuse) {
       int* redi = reinterpret_cast<int*>(red);
@@ -657,8 +655,8 @@ __global__ void __launch_bounds__(kTile, kLatMinBlocks) lattice_half_kernel(cons
     }
   }
   if (qn != 0u)
-    tail_drain<ENC>(sh.job, sh, queue[warp], qn, K, sh.typ, half == 0u ? sh.job.B : sh.job.A,
-                    calls);
+    tail_drain<ENC>(sh.job, sh, queue[warp], qn, K, sh.typ, half == 0u ? sh.job.A : sh.job.B,
+                    half == 0u ? sh.job.B : sh.job.A, calls);
   if (rng_calls != nullptr) {
     const uint32_t wsum = __reduce_add_sync(0xffffffffu, calls);
     if (lane == 0 && wsum) atomicAdd(rng_calls, (unsigned long long)wsum);
