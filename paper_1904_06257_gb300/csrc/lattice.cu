@@ -355,6 +355,23 @@ __device__ __forceinline__ void load_lane_words(const LatJob& J, const void* buf
                                                 uint32_t half, uint32_t& S, uint32_t& V,
                                                 uint32_t& H) {
   const uint32_t L = J.L, wpr = J.wpr;
+  if (ENC != kEncInt8 && J.wpr_shift != 0xffffffffu) {
+    // power-of-two rows (then L * wpr is one too): the neighbour words by masks --
+    // the vertical one wpr words away modulo the lattice, the horizontal one the
+    // next word of the same row, cyclically
+    const uint32_t* A = static_cast<const uint32_t*>(buf);
+    const uint32_t rowmask = wpr - 1u, allmask = J.nwords - 1u;
+    const uint32_t dv = half == 0u ? 0u - wpr : wpr;
+    const uint32_t dh = half == 0u ? 0xffffffffu : 1u;
+    S = ld_ro<NC>(A + w);
+    V = ld_ro<NC>(A + ((w + dv) & allmask));
+    const uint32_t hn = ld_ro<NC>(A + ((w & ~rowmask) | ((w + dh) & rowmask)));
+    if (ENC == kEncPacked)
+      H = half == 0u ? ((S << 1) | (hn >> 31)) : ((S >> 1) | (hn << 31));
+    else
+      H = hn;
+    return;
+  }
   uint32_t i, c;
   word_rc(J, w, i, c);
   const uint32_t iv = half == 0u ? (i == 0u ? L - 1u : i - 1u) : (i + 1u == L ? 0u : i + 1u);
