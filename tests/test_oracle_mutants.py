@@ -49,6 +49,7 @@ MUTANTS = {
 def _pins():
     """The pins as plain calls, cheapest first; each raises AssertionError on failure."""
     return [
+        ("philox_curand", pins.test_philox_matches_curand_host_generator),
         ("draw_layouts", pins.test_draw_layouts_match_definition),
         ("threshold_points", pins.test_threshold_exact_points_and_saturation),
         ("threshold_precision", pins.test_threshold_against_high_precision),

@@ -4,6 +4,8 @@ CPU only.
 * Philox-4x32-10 against an independent implementation (Triton's ``tl.philox``
   run by the Triton CPU interpreter) and the draw layouts against their
   definition assembled from that independent generator.
+* Philox-4x32-10 against NVIDIA's cuRAND host generator (run on the CPU through
+  its C API), under the key (seed low word, seed high word).
 * The exponential against libm (<= 2 ulp) and exact values; the threshold
   T = floor(2^32 / (1 + e^{-2 beta h})) against a 60-digit evaluation (+-1) and
   its exact values at h = 0 and in saturation.
@@ -16,6 +18,8 @@ CPU only.
   1 / (1 + e^{2 beta (2J + q - lambda)}) (proof of Thm 3.3), binomial test.
 * Observables against the independent numpy Hamiltonians of oracle/exact.py.
 """
+import ctypes
+import ctypes.util
 import json
 import math
 import os
@@ -53,6 +57,55 @@ def test_philox_matches_independent_implementation():
         key = np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint32)
         mine = np.array([core.philox(key, c) for c in ctrs])
         assert np.array_equal(mine, ref), seed
+
+
+def _curand():
+    names = [ctypes.util.find_library("curand"), "libcurand.so", "libcurand.so.10"]
+    names += [os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), d, "libcurand.so")
+              for d in ("lib64", "lib")]
+    for name in names:
+        if not name:
+            continue
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    pytest.skip("libcurand not found")
+
+
+def _curand_philox_host(lib, seed, offset, n):
+    """n 32-bit outputs of cuRAND's host-side PHILOX4_32_10 generator (generator
+    type 161 in curand.h) for `seed`, starting at output `offset`."""
+    gen = ctypes.c_void_p()
+    if lib.curandCreateGeneratorHost(ctypes.byref(gen), 161) != 0:
+        pytest.skip("cuRAND host generator unavailable")
+    try:
+        assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        assert lib.curandSetGeneratorOffset(gen, ctypes.c_ulonglong(offset)) == 0
+        out = np.zeros(n, dtype=np.uint32)
+        assert lib.curandGenerate(gen, out.ctypes.data_as(ctypes.c_void_p),
+                                  ctypes.c_size_t(n)) == 0
+    finally:
+        lib.curandDestroyGenerator(gen)
+    return out
+
+
+def test_philox_matches_curand_host_generator():
+    """A second implementation outside this project.  Its output block b (outputs
+    4b .. 4b+3) is the Philox block of counter (p mod 2^32, p >> 32, s, 0) with
+    s = b mod 2^16 and p = b >> 16 (65,536 subsequences in counter word 2, the
+    position in words 0 and 1), so counter words 0, 1 and 2 and both key words are
+    exercised; two consecutive blocks from each offset."""
+    lib = _curand()
+    for seed in (0, 1, 0x5348414B, 2**32 + 7, 0x123456789ABCDEF0, 2**64 - 1):
+        key = np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint32)
+        for block in (0, 77, 65535, 65536 + 3, 2**31 + 3, 2**32 - 1, 2**48 + 5 * 65536 + 9):
+            got = _curand_philox_host(lib, seed, 4 * block, 8).reshape(2, 4)
+            for i in range(2):
+                b = block + i
+                p, sub = b >> 16, b & 0xFFFF
+                ref = core.philox(key, [p & 0xFFFFFFFF, p >> 32, sub, 0])
+                assert np.array_equal(got[i], ref), (seed, b)
 
 
 def test_draw_layouts_match_definition():
