@@ -5,7 +5,9 @@ references (lambda = 0, J = 1):
   (oracle/exact.py, numpy) must give the same energy and |m| within 4 standard
   errors;
 * as q grows the energy approaches Onsager's closed form (Thm 3.1: the measure
-  tends to Gibbs when e^{-2 beta q} is small), monotonically in q."""
+  tends to Gibbs when e^{-2 beta q} is small), monotonically in q;
+* a small field lambda = 0.01 (no closed form) raises m at every q, and the CUDA
+  chain's m at lambda = 0.01 agrees with the oracle chain's run from other seeds."""
 import numpy as np
 import pytest
 
@@ -21,8 +23,8 @@ def S():
     return lib()
 
 
-def gpu_series(S, L, q, beta, burn, steps, seed, R=32, init=0):
-    ctx = S.shaken_init(lattice_problem(S, S.MULTISPIN, L, R, beta, 1.0, q, 0.0, init=init), seed)
+def gpu_series(S, L, q, beta, burn, steps, seed, R=32, init=0, lam=0.0):
+    ctx = S.shaken_init(lattice_problem(S, S.MULTISPIN, L, R, beta, 1.0, q, lam, init=init), seed)
     S.shaken_step(ctx, burn)
     mag, en = S.shaken_step_record(ctx, steps, R)
     S.shaken_free(ctx)
@@ -51,3 +53,22 @@ def test_energy_approaches_onsager_as_q_grows(S):
     # e^{-2 beta q} = 0.74 ... 0.008: the deviation from Onsager shrinks with q
     assert all(a > b for a, b in zip(dev, dev[1:])), dev
     assert dev[-1] < 0.1 * dev[0], dev
+
+
+@pytest.mark.parametrize("q", [0.5, 1.0, 2.0])
+def test_small_field_raises_magnetisation(S, q):
+    L, beta = 64, 0.4407
+    _, m0 = gpu_series(S, L, q, beta, burn=300, steps=800, seed=31)
+    _, m1 = gpu_series(S, L, q, beta, burn=300, steps=800, seed=31, lam=0.01)
+    d = m1.mean(axis=0) - m0.mean(axis=0)  # per replica, same draws in both runs
+    assert d.mean() > 4 * d.std(ddof=1) / np.sqrt(d.size), (q, d.mean())
+
+
+def test_small_field_magnetisation_matches_oracle_chain(S):
+    from tests.test_oracle_physics import _oracle_m
+    L, R, q, beta, lam = 16, 32, 1.0, 0.4407, 0.01
+    _, m = gpu_series(S, L, q, beta, burn=100, steps=3000, seed=41, lam=lam)
+    g = m.mean(axis=0)
+    o = _oracle_m(L, R, q, lam, beta, 0x5348414B + 99, 50, 40, 6)
+    se = np.hypot(g.std(ddof=1) / np.sqrt(R), o.std(ddof=1) / np.sqrt(R))
+    assert abs(g.mean() - o.mean()) < 4 * se, (g.mean(), o.mean(), se)
