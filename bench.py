@@ -139,6 +139,58 @@ def oracle_sample(pool, workers, Ls, betas, seeds, steps_per_group=1, max_groups
     return upd / wall, workers, desc, upd, wall
 
 
+def _oracle_config(task):
+    """One bounded single-threaded oracle run of a configuration's workload:
+    returns (name, updates, seconds, description)."""
+    from oracle import core
+    kind = task[0]
+    if kind == "lattice":
+        _, name, L, beta, q, steps = task
+        s = core.lattice_init(L, 1, W.BASE_SEED, core.MODE_SINGLE, 0)
+        t0 = time.perf_counter()
+        core.lattice_run(s, 1.0, q, 0.0, beta, W.BASE_SEED, 0, steps, core.MODE_SINGLE)
+        dt = time.perf_counter() - t0
+        return name, 2.0 * L * L * steps, dt, f"L={L}, 1 replica, {steps} full step(s)"
+    if kind == "multispin":
+        _, name, L, steps = task
+        betas = W.beta_grid(REPLICAS_PER_GROUP, 0.3, 0.6, 64)
+        s = core.lattice_init(L, REPLICAS_PER_GROUP, W.BASE_SEED, core.MODE_MULTISPIN, 0)
+        t0 = time.perf_counter()
+        core.lattice_run(s, J, Q, LAM, betas, W.BASE_SEED, 0, steps, core.MODE_MULTISPIN)
+        dt = time.perf_counter() - t0
+        return name, 2.0 * REPLICAS_PER_GROUP * L * L * steps, dt, \
+            f"one group of 32 replicas at L={L}, {steps} full step(s)"
+    _, name, n, integer, R, steps = task
+    u, v = W.erdos_renyi(n, 8.0, W.BASE_SEED + 1)
+    Jc = (W.couplings_pm1(u.size, W.BASE_SEED + 2) if integer
+          else W.couplings_normal(u.size, W.BASE_SEED + 2))
+    lam = W.fields_normal(n, 0.1, W.BASE_SEED + 3)
+    tail, head = core.orient(u, v, 0)
+    s = core.graph_init(n, R, W.BASE_SEED)
+    t0 = time.perf_counter()
+    core.graph_run(s, tail, head, Jc, integer, lam, 1.0, 0.1, W.BASE_SEED, 0, steps)
+    dt = time.perf_counter() - t0
+    return name, 2.0 * n * R * steps, dt, \
+        f"ER n={n}, mean degree 8, {'+-1' if integer else 'N(0,1)'} couplings, " \
+        f"lambda ~ N(0, 0.1^2), {R} replicas, {steps} full step(s) at beta = 0.1"
+
+
+def oracle_configs():
+    """The oracle, as it stands, on bounded samples of each configuration (one
+    single-threaded process per sample, the samples run side by side)."""
+    tasks = [("lattice", "C1 L=64", 64, 0.40, 1.0, 500),
+             ("lattice", "C2 L=4096", 4096, 0.4407, 1.0, 1)]
+    tasks += [("multispin", f"C3 L={L}", L, 1) for L in (32, 64, 128, 256, 512)]
+    tasks += [("graph", "C4 ER n=1e5 +-1", 100_000, True, 256, 1),
+              ("graph", "C4 ER n=1e5 N(0,1)", 100_000, False, 256, 1)]
+    pool, _ = oracle_pool(len(tasks))
+    res = pool.map(_oracle_config, tasks)
+    pool.close()
+    pool.join()
+    return {name: {"updates_per_s": upd / dt, "updates": upd, "seconds": dt, "sample": desc,
+                   "cores": 1} for name, upd, dt, desc in res}
+
+
 # ------------------------------------------------------------------------ GPU arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -280,7 +332,7 @@ def run_ours(args, rank, world, local_rank):
     for name, enc in (("int8", S.INT8), ("packed", S.PACKED)):
         pp = S.Problem(S.LATTICE, enc, 1, 0.4407, Q, L=Lp, J=J, lambda_const=LAM)
         cp = S.shaken_init(pp, W.BASE_SEED + 7, stream)
-        S.shaken_step(cp, 3)
+        S.shaken_step(cp, 128)  # warm-up; also captures the step graph timed below
         S.shaken_sync(cp)
         pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
@@ -687,6 +739,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--oracle-configs", action="store_true",
+                    help="with --impl reference: time the oracle on a bounded sample of "
+                         "every configuration instead")
     ap.add_argument("--only-batched", action="store_true",
                     help="time the batched workload only (profiling runs)")
     ap.add_argument("--skip-graphs", action="store_true", help="skip the sparse-graph section")
@@ -713,7 +768,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
+    if args.impl == "reference" and args.oracle_configs:
+        out = {"impl": "reference", "oracle_configs": oracle_configs()} if rank == 0 else None
+    elif args.impl == "reference":
         out = run_reference(args, rank, world)
     else:
         if world > 1:
