@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(256) build_lattice_tables_kernel(
       uint32_t a = 0u;
       for (int k = 0; k < 6; ++k) a |= sat_any[k];
       T->anysat = a != 0u ? 1u : 0u;
-      T->pad[0] = T->pad[1] = 0u;
+      T->pad = 0u;
     }
   }
   __syncthreads();
@@ -85,6 +85,16 @@ __global__ void __launch_bounds__(256) build_lattice_tables_kernel(
     const int j = threadIdx.x >> 2, cc = threadIdx.x & 3;
     const int cls = cc == 0 ? 0 : cc == 1 ? 1 : cc == 2 ? 3 : 5;
     T->tmc[j][cc] = T->tm[j][cls];
+  }
+  __syncthreads();
+  // mirror test on the eight planes the head compares (lane j checks plane j)
+  if (threadIdx.x < 32) {
+    bool ok = true;
+    if (lane < 8)
+      ok = (T->tmc[lane][0] ^ T->tmc[lane][3]) == 0xffffffffu &&
+           (T->tmc[lane][1] ^ T->tmc[lane][2]) == 0xffffffffu;
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0) T->mirror = (ok && T->collapsed != 0u && T->anysat == 0u) ? 1u : 0u;
   }
 }
 
@@ -219,6 +229,31 @@ __device__ __forceinline__ void head_planes(const LaneWord (&Lw)[WPT], const Lat
   }
 }
 
+// The same four planes for mirror tables: with c1 = majority (L.V) and c0 =
+// parity (L.X), the class c = c0 + 2 c1 has field h > 0 exactly when c1 = 1, and
+// |h| is the larger value when c0 == c1.  The plane is the T(|h|) plane picked by
+// sel = ~(c0 ^ c1) from the rows of c = 2 and c = 3, complemented on the lanes
+// with h < 0: two logic operations instead of three selects.
+template <int WPT>
+__device__ __forceinline__ void head_planes_mirror(const LaneWord (&Lw)[WPT],
+                                                   const uint32_t (&sel)[WPT],
+                                                   const LatTable& tab, int call,
+                                                   const uint4 (&W)[WPT], uint32_t (&lt)[WPT],
+                                                   uint32_t (&eq)[WPT]) {
+#pragma unroll
+  for (int i = 3; i >= 0; --i) {
+    const uint2 r = *reinterpret_cast<const uint2*>(&tab.tmc[4 * call + i][2]);
+#pragma unroll
+    for (int k = 0; k < WPT; ++k) {
+      const uint32_t w = i == 0 ? W[k].x : i == 1 ? W[k].y : i == 2 ? W[k].z : W[k].w;
+      const uint32_t Q = (sel[k] & r.y) | (~sel[k] & r.x);
+      const uint32_t P = ~(Q ^ Lw[k].V);
+      lt[k] = (~w & P) | (~w & lt[k]) | (P & lt[k]);
+      eq[k] &= ~(w ^ P);
+    }
+  }
+}
+
 template <int WPT>
 __device__ __forceinline__ void head_finish(LaneWord (&Lw)[WPT], const uint32_t (&lt)[WPT],
                                             const uint32_t (&eq)[WPT]) {
@@ -229,22 +264,27 @@ __device__ __forceinline__ void head_finish(LaneWord (&Lw)[WPT], const uint32_t 
   }
 }
 
-template <bool COLL, int WPT>
+// MIR: the table is a mirror table (collapsed, `mirror` set).
+template <bool COLL, int WPT, bool MIR = false>
 __device__ __forceinline__ void decide_head_words(LaneWord (&Lw)[WPT], const LatTable& tab,
                                                   const PhKey& K, const PhShared& P,
                                                   const uint32_t (&a)[WPT], uint32_t half) {
-  uint32_t lt[WPT], eq[WPT];
+  uint32_t lt[WPT], eq[WPT], sel[WPT];
 #pragma unroll
   for (int k = 0; k < WPT; ++k) {
     lt[k] = 0u;
     eq[k] = 0xffffffffu;
+    sel[k] = MIR ? ~(Lw[k].X ^ Lw[k].V) : 0u;
   }
 #pragma unroll
   for (int call = 1; call >= 0; --call) {
     uint4 W[WPT];
 #pragma unroll
     for (int k = 0; k < WPT; ++k) W[k] = ph_call_shared(K, P, a[k], half + 2u * (uint32_t)call);
-    head_planes<COLL, WPT>(Lw, tab, call, W, lt, eq);
+    if (MIR)
+      head_planes_mirror<WPT>(Lw, sel, tab, call, W, lt, eq);
+    else
+      head_planes<COLL, WPT>(Lw, tab, call, W, lt, eq);
   }
   head_finish<WPT>(Lw, lt, eq);
 }
@@ -547,7 +587,7 @@ __device__ __forceinline__ void tile_commit(const LatJob& J, const TileShared& s
 // a full warp of them (one call per word and round; words still undecided go
 // back).  The queue carries over to the block's next tile of the same job and is
 // drained when the job changes.  FULL: every word of the tile exists.
-template <int ENC, int WPT, bool COLL, bool FULL>
+template <int ENC, int WPT, bool COLL, bool FULL, bool MIR>
 __device__ __forceinline__ void tile_decide(const LatJob& J, const TileShared& sh,
                                             Pending* __restrict__ q, uint32_t& qn,
                                             const PhKey& K, uint32_t w0,
@@ -563,7 +603,7 @@ __device__ __forceinline__ void tile_decide(const LatJob& J, const TileShared& s
     Lws[k] = classify<COLL>(S[k], V[k], H[k], F[k], sh.tab);
     if (!FULL && a[k] >= J.nwords) Lws[k].U = 0u;
   }
-  decide_head_words<COLL, WPT>(Lws, sh.tab, K, sh.ph, a, half);
+  decide_head_words<COLL, WPT, MIR>(Lws, sh.tab, K, sh.ph, a, half);
   calls += 2u * WPT;
   tile_commit<ENC, WPT, COLL, FULL>(J, sh, q, qn, K, a, half, S, V, H, Lws, srcbuf, dstbuf, acc,
                                     calls);
@@ -648,20 +688,27 @@ __global__ void __launch_bounds__(kTile, kLatMinBlocks) lattice_half_kernel(cons
     }
     int acc[3] = {0, 0, 0};  // tracking sums of this tile (|sum| <= 64 per word)
     const bool full_tile = tl.w0 + kTile * WPT <= J.nwords;
-    if (sh.tab.collapsed) {
+    if (sh.tab.mirror) {
       if (full_tile)
-        tile_decide<ENC, WPT, true, true>(J, sh, queue[warp], qn, K, tl.w0, typ, S, V, H, F,
-                                          src, dstbuf, acc, calls);
+        tile_decide<ENC, WPT, true, true, true>(J, sh, queue[warp], qn, K, tl.w0, typ, S, V, H,
+                                                F, src, dstbuf, acc, calls);
       else
-        tile_decide<ENC, WPT, true, false>(J, sh, queue[warp], qn, K, tl.w0, typ, S, V, H, F,
-                                           src, dstbuf, acc, calls);
+        tile_decide<ENC, WPT, true, false, true>(J, sh, queue[warp], qn, K, tl.w0, typ, S, V, H,
+                                                 F, src, dstbuf, acc, calls);
+    } else if (sh.tab.collapsed) {
+      if (full_tile)
+        tile_decide<ENC, WPT, true, true, false>(J, sh, queue[warp], qn, K, tl.w0, typ, S, V, H,
+                                                 F, src, dstbuf, acc, calls);
+      else
+        tile_decide<ENC, WPT, true, false, false>(J, sh, queue[warp], qn, K, tl.w0, typ, S, V,
+                                                  H, F, src, dstbuf, acc, calls);
     } else {
       if (full_tile)
-        tile_decide<ENC, WPT, false, true>(J, sh, queue[warp], qn, K, tl.w0, typ, S, V, H, F,
-                                           src, dstbuf, acc, calls);
+        tile_decide<ENC, WPT, false, true, false>(J, sh, queue[warp], qn, K, tl.w0, typ, S, V,
+                                                  H, F, src, dstbuf, acc, calls);
       else
-        tile_decide<ENC, WPT, false, false>(J, sh, queue[warp], qn, K, tl.w0, typ, S, V, H, F,
-                                            src, dstbuf, acc, calls);
+        tile_decide<ENC, WPT, false, false, false>(J, sh, queue[warp], qn, K, tl.w0, typ, S, V,
+                                                   H, F, src, dstbuf, acc, calls);
     }
     if (sh.fuse) {
       int* redi = reinterpret_cast<int*>(red);

@@ -162,7 +162,11 @@ __device__ __forceinline__ double field_h(double Jc, int s, double q, int sigma,
 // When the thresholds of every lane depend on n + s only (classes (0,1) and
 // (1,0) equal, (1,1) and (2,0) equal -- the case J = q), tmc[j][c] holds the
 // planes by c = n + s in 0..3 and `collapsed` is set; `anysat` marks tables
-// with at least one saturated lane.
+// with at least one saturated lane.  `mirror` (collapsed, no saturated lane):
+// on planes 0..7 the fields -h take the complemented planes of +h on every lane,
+// tmc[j][0] == ~tmc[j][3] and tmc[j][1] == ~tmc[j][2] (T(-h) = 2^32 - T(h) up to
+// rounding, which reaches the top eight bits only when the low 24 bits of T
+// are within a few units of a multiple of 2^24).
 struct __align__(16) LatTable {
   uint32_t tm[32][8];
   uint32_t tmc[32][4];
@@ -170,7 +174,8 @@ struct __align__(16) LatTable {
   uint32_t satm[8];
   uint32_t collapsed;
   uint32_t anysat;
-  uint32_t pad[2];
+  uint32_t mirror;
+  uint32_t pad;
 };
 
 // ---------------------------------------------------------------- descriptors
