@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import multiprocessing as mp
 import os
 import statistics
@@ -360,6 +361,9 @@ def run_ours(args, rank, world, local_rank):
              "m_mean": float(m1[5000:].mean()), "e_per_site_mean": float(e1[5000:].mean() / Ls1**2),
              "what": "shaken_step_record wall time: 10^4 steps with per-step m and H to host"}
 
+    # ---- metastable regime (Sec. 3.2): m(t) from -1 at q = 0.1, lambda = 0.15
+    meta = run_metastability(S, stream)
+
     # ---- arbitrary sparse graphs: n = 1e6, 256 replicas, lambda_x ~ N(0, 0.1^2), q = 1
     graphs = {} if args.skip_graphs else run_graphs(S, stream, torch, args)
 
@@ -428,6 +432,7 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clocks,
             "graphs": graphs,
             "small_lattice": small,
+            "metastability": meta,
             "serving": serving,
             "batched_vs_plain": {
                 "batched_updates_per_s": value / world,
@@ -500,6 +505,45 @@ def committed_traffic(kernel: str):
     if not rec or rec.get("source_hash") != kernel_source_hash():
         return None
     return rec.get("bytes_per_launch")
+
+
+# ------------------------------------------------------------------------ metastability
+META_BETAS = (1.3, 2.3, 3.3, 4.0)
+
+
+def run_metastability(S, stream, L=64, groups=4, steps=8000):
+    """The shaken side of the paper's metastability runs (Sec. 3.2): J = 1, q = 0.1,
+    lambda = 0.15, all replicas started at -1, m recorded every full step, for each
+    beta of the paper's figure.  Reports m(t) averaged over the replicas at a few
+    times, the first exit from -1, the tunnelling time (first step with m > 0) and
+    the fraction of replicas that reached +1 itself."""
+    out = {"L": L, "replicas": 32 * groups, "steps": steps, "J": 1.0, "q": 0.1,
+           "lambda": 0.15, "betas": {}}
+    marks = [t for t in (1, 10, 100, 1000, 4000, steps) if t <= steps]
+    for beta in META_BETAS:
+        mags = []
+        for g in range(groups):
+            p = S.Problem(S.LATTICE, S.MULTISPIN, 32, beta, 0.1, L=L, J=1.0, lambda_const=0.15,
+                          init=2)
+            c = S.shaken_init(p, W.BASE_SEED + 500 + g, stream)
+            m, _ = S.shaken_step_record(c, steps, 32)
+            S.shaken_free(c)
+            mags.append(m)
+        m = np.concatenate(mags, axis=1)  # [steps][replicas]
+        out_ = m > -1.0
+        first = np.where(out_.any(axis=0), out_.argmax(axis=0) + 1, -1)
+        cross = m > 0.0  # in the + phase
+        tun = np.where(cross.any(axis=0), cross.argmax(axis=0) + 1, -1)
+        done = tun > 0
+        out["betas"][str(beta)] = {
+            "m_mean_at_step": {str(t): float(m[t - 1].mean()) for t in marks},
+            "exit_from_minus_mean_steps": float(first[first > 0].mean()) if (first > 0).any()
+            else None,
+            "tunnelled_fraction": float(done.mean()),
+            "tunnelling_median_steps": float(np.median(tun[done])) if done.any() else None,
+            "all_plus_reached_fraction": float((m == 1.0).any(axis=0).mean()),
+            "flip_probability_from_minus": 1.0 / (1.0 + math.exp(2 * beta * (2 + 0.1 - 0.15)))}
+    return out
 
 
 # ------------------------------------------------------------------------ graphs

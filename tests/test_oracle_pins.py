@@ -338,6 +338,47 @@ def test_first_exit_probability_from_minus():
     assert stats.binomtest(k, N, p).pvalue > 1e-4
 
 
+def exit_probability_per_step(J, q, lam, beta, N):
+    """P(sigma_{t+1} != -1 | sigma_t = -1) on an N-site torus, to first order in the
+    single-site flip probability p0 (proof of Thm 3.3).  Half dl from -1: every site
+    has h0 = -2J - q + lambda.  If sigma' = -1, half ur gives h0 again.  If sigma' has
+    one + at x, half ur gives x the field h1 = -2J + q + lambda, the two sites below
+    and left of x (whose up / right neighbour is x) h2 = lambda - q, the rest h0.
+    Terms with two or more flips, O((N p0)^2), are dropped."""
+    def p(h):
+        return 1.0 / (1.0 + math.exp(-2.0 * beta * h))
+    p0, p1, p2 = p(-2 * J - q + lam), p(-2 * J + q + lam), p(lam - q)
+    stay = (1 - p0) ** (2 * N)
+    stay += N * p0 * (1 - p0) ** (N - 1) * (1 - p1) * (1 - p2) ** 2 * (1 - p0) ** (N - 3)
+    return 1.0 - stay
+
+
+def exit_rate_mle(first, T):
+    """Censored geometric MLE of the per-step exit probability: exits / exposure, with
+    `first` the step (1-based) of each replica's first exit, 0 if none by step T."""
+    first = np.asarray(first)
+    exits = int((first > 0).sum())
+    exposure = float(np.where(first > 0, first, T).sum())
+    return exits / exposure, exits
+
+
+def test_exit_time_from_minus_matches_first_order_law():
+    """Full steps from -1 (J = 1, q = 0.1, lambda = 0.15: the regime 0 < q < lambda < J
+    of Thm 3.1) until the first full-step configuration other than -1: geometric with
+    the per-step probability of exit_probability_per_step."""
+    J, q, lam, beta = 1.0, 0.1, 0.15, 2.5
+    L, R, T = 16, 128, 150
+    s = core.lattice_init(L, R, 0x5348414B + 5, core.MODE_SINGLE, kind=2)
+    first = np.zeros(R, dtype=np.int64)
+    for t in range(1, T + 1):
+        s, _ = core.lattice_run(s, J, q, lam, beta, 0x5348414B + 5, t - 1, 1, core.MODE_SINGLE)
+        out = (s.reshape(R, -1) > 0).any(axis=1)
+        first[(first == 0) & out] = t
+    P = exit_probability_per_step(J, q, lam, beta, L * L)
+    Phat, exits = exit_rate_mle(first, T)
+    assert abs(Phat - P) < 4 * Phat / math.sqrt(exits), (Phat, P, exits)
+
+
 # --------------------------------------------------------------------------- observables
 def test_lattice_sums_match_numpy_hamiltonians():
     L = 5
