@@ -178,6 +178,12 @@ shaken_status shaken_set_spins(shaken_ctx* ctx, const int8_t* in);
 shaken_status shaken_state_bytes(shaken_ctx* ctx, size_t* bytes);
 shaken_status shaken_set_state_raw(shaken_ctx* ctx, const void* host_words, size_t bytes);
 shaken_status shaken_get_state_raw(shaken_ctx* ctx, void* host_words, size_t bytes);
+/* As shaken_get_state_raw, without waiting: the copy of sigma is enqueued on the
+ * context's stream (the batch's stream for a member) and host_words (pinned
+ * memory for a truly asynchronous copy) holds it after the next shaken_sync,
+ * shaken_batch_sync or other synchronising call on that stream.  The caller
+ * keeps host_words alive until then. */
+shaken_status shaken_get_state_raw_async(shaken_ctx* ctx, void* host_words, size_t bytes);
 
 /* Current step counter t (number of full steps taken since init or load). */
 shaken_status shaken_get_step(shaken_ctx* ctx, uint64_t* t);
@@ -223,6 +229,12 @@ shaken_status shaken_batch_remove(shaken_batch* b, shaken_ctx* ctx);
  * chunk of steps are captured once into a CUDA graph and replayed. */
 shaken_status shaken_batch_step(shaken_batch* b, uint64_t n_steps, int use_graph);
 shaken_status shaken_batch_sync(shaken_batch* b);
+/* Observables of every member's replicas, as shaken_observables computes them,
+ * into host out[sum of the members' R], members in the order they were added
+ * (replica r of the k-th member at out[R_0 + ... + R_{k-1} + r]).  One
+ * observables launch per encoding family covers all members; synchronises once
+ * (so it also completes earlier asynchronous copies on the batch's stream). */
+shaken_status shaken_batch_observables(shaken_batch* b, shaken_obs* out);
 /* Kernel timing: with timing on, every half-step launch of a non-graph batch
  * step is bracketed by CUDA events on the batch stream.  kernel_time syncs
  * the stream and returns the summed device time (ms) and the number of timed

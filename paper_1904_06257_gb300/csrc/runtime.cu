@@ -1082,61 +1082,119 @@ shaken_status shaken_step_record(shaken_ctx* ctx, uint64_t n_steps, double* mag,
   return SHAKEN_OK;
 }
 
-shaken_status shaken_observables(shaken_ctx* ctx, shaken_obs* out) {
-  if (!ctx || !out) return fail(SHAKEN_E_INVAL, "NULL argument");
-  cudaStream_t st = ctx_stream(ctx);
-  if (ctx->solo.dirty) TRY(build_plan(ctx->solo, st));
-  CU(cudaMemsetAsync(ctx->obs_sums.p, 0, ctx->obs_sums.bytes, st));
-  for (auto& F : ctx->solo.fams) {
-    if (F->kind == 0)
-      CU(shk::launch_lattice_obs(F->enc, F->wpt, F->jobs.as<LatJob>(), F->tiles.as<Tile>(),
-                                 F->n_tiles, 1, 1, st));
-    else
-      CU(shk::launch_graph_obs(F->jobs.as<GraphJob>(), F->tiles.as<Tile>(), F->n_tiles, 1, 1,
-                               st));
-    ctx->launches++;
-  }
-  const int R = ctx->R;
-  std::vector<double> sums((size_t)R * kNumSums), best(R);
-  std::vector<long long> bstep(R);
-  CU(cudaMemcpyAsync(sums.data(), ctx->obs_sums.p, sums.size() * 8, cudaMemcpyDeviceToHost, st));
-  CU(cudaMemcpyAsync(best.data(), ctx->best.p, best.size() * 8, cudaMemcpyDeviceToHost, st));
-  CU(cudaMemcpyAsync(bstep.data(), ctx->best_step.p, bstep.size() * 8, cudaMemcpyDeviceToHost,
+// Observables in two parts: the device sums of a context's replicas are
+// cleared and, after the observables launches, copied to host buffers (obs_copy);
+// after a synchronisation obs_finish turns them into shaken_obs records and
+// updates the best energies (an H2D copy when one changed, which is waited for
+// by the caller's final synchronisation).
+struct ObsHost {
+  std::vector<double> sums, best;
+  std::vector<long long> bstep;
+};
+
+static shaken_status obs_copy(shaken_ctx* c, ObsHost& h, cudaStream_t st) {
+  const int R = c->R;
+  h.sums.assign((size_t)R * kNumSums, 0.0);
+  h.best.assign(R, 0.0);
+  h.bstep.assign(R, 0);
+  CU(cudaMemcpyAsync(h.sums.data(), c->obs_sums.p, h.sums.size() * 8, cudaMemcpyDeviceToHost,
                      st));
-  CU(cudaStreamSynchronize(st));
-  const double N = (double)ctx->sites();
+  CU(cudaMemcpyAsync(h.best.data(), c->best.p, h.best.size() * 8, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(h.bstep.data(), c->best_step.p, h.bstep.size() * 8,
+                     cudaMemcpyDeviceToHost, st));
+  return SHAKEN_OK;
+}
+
+static shaken_status obs_finish(shaken_ctx* c, ObsHost& h, shaken_obs* out, cudaStream_t st,
+                                bool* h2d) {
+  const int R = c->R;
+  const double N = (double)c->sites();
   bool changed = false;
   for (int r = 0; r < R; ++r) {
-    const double* s = &sums[(size_t)r * kNumSums];
+    const double* s = &h.sums[(size_t)r * kNumSums];
     shaken_obs& o = out[r];
     o.magnetization = s[shk::kSumM] / N;
     o.cut_edges = (int64_t)llround(s[shk::kSumCut]);
-    if (ctx->kind == SHAKEN_LATTICE) {
-      const double J = ctx->J, lam = ctx->lam_c, q = ctx->q;
+    if (c->kind == SHAKEN_LATTICE) {
+      const double J = c->J, lam = c->lam_c, q = c->q;
       o.energy = -(J * s[shk::kSumE]) - 2.0 * lam * s[shk::kSumM];
       o.pair_energy = -(J * s[shk::kSumP1] + q * s[shk::kSumP2] +
                         lam * (s[shk::kSumM] + s[shk::kSumM2]));
       o.cut_weight = -J * s[shk::kSumCut];
     } else {
       o.energy = -s[shk::kSumE] - 2.0 * s[shk::kSumLS];
-      o.pair_energy = -(s[shk::kSumP1] + ctx->q * s[shk::kSumP2] + s[shk::kSumLS] +
+      o.pair_energy = -(s[shk::kSumP1] + c->q * s[shk::kSumP2] + s[shk::kSumLS] +
                         s[shk::kSumLS2]);
-      o.cut_weight = 0.5 * (s[shk::kSumE] - ctx->sumJ);
+      o.cut_weight = 0.5 * (s[shk::kSumE] - c->sumJ);
     }
-    if (o.energy < best[r]) {
-      best[r] = o.energy;
-      bstep[r] = (long long)ctx->host_step;
+    if (o.energy < h.best[r]) {
+      h.best[r] = o.energy;
+      h.bstep[r] = (long long)c->host_step;
       changed = true;
     }
-    o.best_energy = best[r];
-    o.best_step = bstep[r];
+    o.best_energy = h.best[r];
+    o.best_step = h.bstep[r];
   }
   if (changed) {
-    CU(cudaMemcpyAsync(ctx->best.p, best.data(), best.size() * 8, cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(ctx->best_step.p, bstep.data(), bstep.size() * 8, cudaMemcpyHostToDevice,
-                       st));
-    CU(cudaStreamSynchronize(st));
+    CU(cudaMemcpyAsync(c->best.p, h.best.data(), h.best.size() * 8, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(c->best_step.p, h.bstep.data(), h.bstep.size() * 8,
+                       cudaMemcpyHostToDevice, st));
+    *h2d = true;
   }
+  return SHAKEN_OK;
+}
+
+static shaken_status obs_launch(Plan& P, cudaStream_t st, uint64_t* launches) {
+  for (auto& F : P.fams) {
+    if (F->kind == 0)
+      CU(shk::launch_lattice_obs(F->enc, F->wpt, F->jobs.as<LatJob>(), F->tiles.as<Tile>(),
+                                 F->n_tiles, 1, 1, st));
+    else
+      CU(shk::launch_graph_obs(F->jobs.as<GraphJob>(), F->tiles.as<Tile>(), F->n_tiles, 1, 1,
+                               st));
+    ++*launches;
+  }
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_observables(shaken_ctx* ctx, shaken_obs* out) {
+  if (!ctx || !out) return fail(SHAKEN_E_INVAL, "NULL argument");
+  cudaStream_t st = ctx_stream(ctx);
+  if (ctx->solo.dirty) TRY(build_plan(ctx->solo, st));
+  CU(cudaMemsetAsync(ctx->obs_sums.p, 0, ctx->obs_sums.bytes, st));
+  uint64_t nl = 0;
+  TRY(obs_launch(ctx->solo, st, &nl));
+  ctx->launches += nl;
+  ObsHost h;
+  TRY(obs_copy(ctx, h, st));
+  CU(cudaStreamSynchronize(st));
+  bool h2d = false;
+  TRY(obs_finish(ctx, h, out, st, &h2d));
+  if (h2d) CU(cudaStreamSynchronize(st));
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_batch_observables(shaken_batch* b, shaken_obs* out) {
+  if (!b || !out) return fail(SHAKEN_E_INVAL, "NULL argument");
+  Plan& P = b->plan;
+  if (P.members.empty()) return SHAKEN_OK;
+  cudaStream_t st = b->stream;
+  if (P.dirty) TRY(build_plan(P, st));
+  for (shaken_ctx* c : P.members)
+    CU(cudaMemsetAsync(c->obs_sums.p, 0, c->obs_sums.bytes, st));
+  uint64_t nl = 0;
+  TRY(obs_launch(P, st, &nl));
+  b->launches += nl;
+  std::vector<ObsHost> h(P.members.size());
+  for (size_t i = 0; i < P.members.size(); ++i) TRY(obs_copy(P.members[i], h[i], st));
+  CU(cudaStreamSynchronize(st));
+  bool h2d = false;
+  size_t off = 0;
+  for (size_t i = 0; i < P.members.size(); ++i) {
+    TRY(obs_finish(P.members[i], h[i], out + off, st, &h2d));
+    off += (size_t)P.members[i]->R;
+  }
+  if (h2d) CU(cudaStreamSynchronize(st));
   return SHAKEN_OK;
 }
 
@@ -1182,6 +1240,13 @@ shaken_status shaken_get_state_raw(shaken_ctx* ctx, void* host_words, size_t byt
   cudaStream_t st = ctx_stream(ctx);
   CU(cudaMemcpyAsync(host_words, ctx->A.p, bytes, cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_get_state_raw_async(shaken_ctx* ctx, void* host_words, size_t bytes) {
+  if (!ctx || !host_words) return fail(SHAKEN_E_INVAL, "NULL argument");
+  if (bytes != ctx->spin_bytes) return fail(SHAKEN_E_INVAL, "state size mismatch");
+  CU(cudaMemcpyAsync(host_words, ctx->A.p, bytes, cudaMemcpyDeviceToHost, ctx_stream(ctx)));
   return SHAKEN_OK;
 }
 

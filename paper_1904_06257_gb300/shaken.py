@@ -101,6 +101,8 @@ def _load():
         "shaken_state_bytes": [vp, ctypes.POINTER(sz)],
         "shaken_set_state_raw": [vp, vp, sz],
         "shaken_get_state_raw": [vp, vp, sz],
+        "shaken_get_state_raw_async": [vp, vp, sz],
+        "shaken_batch_observables": [vp, vp],
         "shaken_server_create": [ctypes.POINTER(vp), sz, ctypes.c_uint32, vp],
         "shaken_server_submit": [vp, ctypes.POINTER(shaken_problem), u64, vp, u64,
                                  ctypes.POINTER(i64)],
@@ -374,6 +376,18 @@ def shaken_set_state_raw(ctx, host_buf_ptr: int, nbytes: int):
 
 def shaken_get_state_raw(ctx, host_buf_ptr: int, nbytes: int):
     _check(_lib.shaken_get_state_raw(ctx, ctypes.c_void_p(host_buf_ptr), nbytes))
+
+
+def shaken_get_state_raw_async(ctx, host_buf_ptr: int, nbytes: int):
+    """Enqueue the copy of sigma; the buffer holds it after the next synchronising call."""
+    _check(_lib.shaken_get_state_raw_async(ctx, ctypes.c_void_p(host_buf_ptr), nbytes))
+
+
+def shaken_batch_observables(batch, replicas_total: int):
+    """Observables of every member's replicas, members in the order they were added."""
+    out = np.zeros(replicas_total, dtype=OBS_DTYPE)
+    _check(_lib.shaken_batch_observables(batch, _ptr(out)))
+    return out
 
 
 def shaken_batch_free(batch):

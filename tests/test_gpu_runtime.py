@@ -59,6 +59,40 @@ def test_batch_equals_alone(S, use_graph):
     S.shaken_batch_free(b)
 
 
+def test_batch_observables_and_async_state_equal_per_context_calls(S):
+    """shaken_batch_observables (one launch per family for all members) gives each
+    member's records exactly as shaken_observables on the same states, in member
+    order; shaken_get_state_raw_async gives the bytes of shaken_get_state_raw."""
+    import torch
+    b = S.shaken_batch_create()
+    ctxs = []
+    for p, seed, n, R in make_members(S):
+        c = S.shaken_init(p, seed)
+        S.shaken_batch_add(b, c)
+        ctxs.append((c, R))
+    S.shaken_batch_step(b, 9, False)
+    total = sum(R for _, R in ctxs)
+    sizes = [S.shaken_state_bytes(c) for c, _ in ctxs]
+    bufs = [torch.zeros(n, dtype=torch.uint8, pin_memory=True) for n in sizes]
+    for (c, _), buf, n in zip(ctxs, bufs, sizes):
+        S.shaken_get_state_raw_async(c, buf.data_ptr(), n)
+    batched = S.shaken_batch_observables(b, total)
+    off = 0
+    for (c, R), buf, n in zip(ctxs, bufs, sizes):
+        ref = torch.zeros(n, dtype=torch.uint8, pin_memory=True)
+        S.shaken_get_state_raw(c, ref.data_ptr(), n)
+        assert torch.equal(buf, ref)
+        single = S.shaken_observables(c, R)
+        for f in ("magnetization", "energy", "pair_energy", "cut_edges", "cut_weight"):
+            assert np.array_equal(batched[f][off:off + R], single[f]), f
+        off += R
+    assert off == total
+    for c, _ in ctxs:
+        S.shaken_batch_remove(b, c)
+        S.shaken_free(c)
+    S.shaken_batch_free(b)
+
+
 def test_checkpoint_resume_bit_exact(S):
     p = lattice_problem(S, S.MULTISPIN, 64, 32, W.beta_grid(32))
     c = S.shaken_init(p, 12)
