@@ -235,6 +235,17 @@ shaken_status shaken_batch_sync(shaken_batch* b);
  * observables launch per encoding family covers all members; synchronises once
  * (so it also completes earlier asynchronous copies on the batch's stream). */
 shaken_status shaken_batch_observables(shaken_batch* b, shaken_obs* out);
+/* Raw states of all members in one transfer each way: the members' raw states
+ * (shaken_state_bytes each, the layout of shaken_get_state_raw) concatenated in
+ * member order; state_bytes gives the total.  set copies host -> device in one
+ * copy and spreads it over the members' sigma and sigma' (a kernel), without
+ * waiting; get gathers the members' sigma (a kernel) and copies it to host in one
+ * copy, without waiting: host holds it after the next synchronising call on the
+ * batch's stream (pinned memory for asynchronous copies; keep host alive and
+ * unchanged until then).  bytes must equal the total, else E_INVAL. */
+shaken_status shaken_batch_state_bytes(shaken_batch* b, size_t* bytes);
+shaken_status shaken_batch_set_states_raw(shaken_batch* b, const void* host, size_t bytes);
+shaken_status shaken_batch_get_states_raw_async(shaken_batch* b, void* host, size_t bytes);
 /* Kernel timing: with timing on, every half-step launch of a non-graph batch
  * step is bracketed by CUDA events on the batch stream.  kernel_time syncs
  * the stream and returns the summed device time (ms) and the number of timed

@@ -52,6 +52,78 @@ __global__ void threshold_kernel(const double* __restrict__ h, const double* __r
     out[i] = threshold_T(h[i], beta[i]);
 }
 
+// Batched copies between the members' device arrays and one packed buffer, so
+// that a batch moves its states and observables to or from the host in one
+// transfer each.  Grid: x strides over a member's words, y = member.
+__global__ void __launch_bounds__(256) pack_states_kernel(const MemberDev* __restrict__ m,
+                                                          uint32_t* __restrict__ dst) {
+  const MemberDev M = m[blockIdx.y];
+  uint32_t* d = dst + M.state_off;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < M.state_words;
+       i += gridDim.x * blockDim.x)
+    d[i] = M.A[i];
+}
+
+__global__ void __launch_bounds__(256) unpack_states_kernel(const MemberDev* __restrict__ m,
+                                                            const uint32_t* __restrict__ src) {
+  const MemberDev M = m[blockIdx.y];
+  const uint32_t* s = src + M.state_off;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < M.state_words;
+       i += gridDim.x * blockDim.x) {
+    const uint32_t v = s[i];
+    M.A[i] = v;
+    M.B[i] = v;
+  }
+}
+
+__global__ void __launch_bounds__(256) pack_obs_kernel(const MemberDev* __restrict__ m,
+                                                       double* __restrict__ dst) {
+  const MemberDev M = m[blockIdx.y];
+  double* d = dst + M.obs_off;
+  const uint32_t ns = M.R * (uint32_t)kNumSums;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ns + 2u * M.R;
+       i += gridDim.x * blockDim.x) {
+    double v;
+    if (i < ns)
+      v = M.obs[i];
+    else if (i < ns + M.R)
+      v = M.best[i - ns];
+    else
+      v = __longlong_as_double(M.best_step[i - ns - M.R]);
+    d[i] = v;
+  }
+}
+
+__global__ void __launch_bounds__(256) unpack_best_kernel(const MemberDev* __restrict__ m,
+                                                          const double* __restrict__ src) {
+  const MemberDev M = m[blockIdx.y];
+  const double* s = src + M.obs_off + (size_t)M.R * kNumSums;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < M.R;
+       i += gridDim.x * blockDim.x) {
+    M.best[i] = s[i];
+    M.best_step[i] = __double_as_longlong(s[M.R + i]);
+  }
+}
+
+// what: 0 pack states, 1 unpack states, 2 pack observables, 3 unpack best energies
+cudaError_t launch_member_copy(int what, const MemberDev* m, int n, void* buf,
+                               uint32_t max_words, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  uint32_t bx = (max_words + 255u) / 256u;
+  if (bx < 1u) bx = 1u;
+  if (bx > 64u) bx = 64u;
+  const dim3 grid(bx, (unsigned)n);
+  if (what == 0)
+    pack_states_kernel<<<grid, 256, 0, st>>>(m, static_cast<uint32_t*>(buf));
+  else if (what == 1)
+    unpack_states_kernel<<<grid, 256, 0, st>>>(m, static_cast<const uint32_t*>(buf));
+  else if (what == 2)
+    pack_obs_kernel<<<grid, 256, 0, st>>>(m, static_cast<double*>(buf));
+  else
+    unpack_best_kernel<<<grid, 256, 0, st>>>(m, static_cast<const double*>(buf));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_epilogue(CtxDev* const* ctxs, int n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   epilogue_kernel<<<n, 256, 0, st>>>(ctxs, n);

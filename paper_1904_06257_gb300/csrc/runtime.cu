@@ -46,6 +46,7 @@ cudaError_t launch_graph_obs(const GraphJob*, const Tile*, int, int, int, cudaSt
 cudaError_t launch_graph_fields(const GraphJob*, const Tile*, int, uint32_t, float*,
                                 cudaStream_t);
 cudaError_t launch_epilogue(CtxDev* const*, int, cudaStream_t);
+cudaError_t launch_member_copy(int, const shk::MemberDev*, int, void*, uint32_t, cudaStream_t);
 cudaError_t launch_lattice_resident(int, const LatJob*, int, uint32_t, uint32_t, uint32_t,
                                     cudaStream_t);
 cudaError_t launch_philox(uint64_t, const uint32_t*, uint32_t*, int64_t, cudaStream_t);
@@ -151,6 +152,13 @@ struct Plan {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
   double timed_ms = 0.0;
   uint64_t timed_n = 0;
+  // batched state / observables copies (built on first use, dropped with the plan)
+  bool mtab_valid = false;
+  DevMem mtab;                 // MemberDev per member
+  size_t state_words = 0;      // packed states, 32-bit words
+  size_t obs_doubles = 0;      // packed observables, doubles
+  uint32_t max_state_words = 0, max_obs = 0;
+  DevMem stage_state, stage_obs;
   ~Plan() {
     drop_graph();
     for (auto& pr : ev_pending) {
@@ -190,6 +198,7 @@ struct Plan {
   }
   void invalidate() {
     dirty = true;
+    mtab_valid = false;
     drop_graph();
   }
 };
@@ -1083,10 +1092,10 @@ shaken_status shaken_step_record(shaken_ctx* ctx, uint64_t n_steps, double* mag,
 }
 
 // Observables in two parts: the device sums of a context's replicas are
-// cleared and, after the observables launches, copied to host buffers (obs_copy);
-// after a synchronisation obs_finish turns them into shaken_obs records and
-// updates the best energies (an H2D copy when one changed, which is waited for
-// by the caller's final synchronisation).
+// cleared and, after the observables launches, copied to host buffers (obs_copy,
+// or one packed copy for a whole batch); after a synchronisation obs_values turns
+// them into shaken_obs records and lowers the best energies where the current
+// energy is below them (the caller writes those back to the device).
 struct ObsHost {
   std::vector<double> sums, best;
   std::vector<long long> bstep;
@@ -1105,11 +1114,9 @@ static shaken_status obs_copy(shaken_ctx* c, ObsHost& h, cudaStream_t st) {
   return SHAKEN_OK;
 }
 
-static shaken_status obs_finish(shaken_ctx* c, ObsHost& h, shaken_obs* out, cudaStream_t st,
-                                bool* h2d) {
+static shaken_status obs_values(shaken_ctx* c, ObsHost& h, shaken_obs* out, bool* changed) {
   const int R = c->R;
   const double N = (double)c->sites();
-  bool changed = false;
   for (int r = 0; r < R; ++r) {
     const double* s = &h.sums[(size_t)r * kNumSums];
     shaken_obs& o = out[r];
@@ -1130,16 +1137,10 @@ static shaken_status obs_finish(shaken_ctx* c, ObsHost& h, shaken_obs* out, cuda
     if (o.energy < h.best[r]) {
       h.best[r] = o.energy;
       h.bstep[r] = (long long)c->host_step;
-      changed = true;
+      *changed = true;
     }
     o.best_energy = h.best[r];
     o.best_step = h.bstep[r];
-  }
-  if (changed) {
-    CU(cudaMemcpyAsync(c->best.p, h.best.data(), h.best.size() * 8, cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(c->best_step.p, h.bstep.data(), h.bstep.size() * 8,
-                       cudaMemcpyHostToDevice, st));
-    *h2d = true;
   }
   return SHAKEN_OK;
 }
@@ -1168,9 +1169,50 @@ shaken_status shaken_observables(shaken_ctx* ctx, shaken_obs* out) {
   ObsHost h;
   TRY(obs_copy(ctx, h, st));
   CU(cudaStreamSynchronize(st));
-  bool h2d = false;
-  TRY(obs_finish(ctx, h, out, st, &h2d));
-  if (h2d) CU(cudaStreamSynchronize(st));
+  bool changed = false;
+  TRY(obs_values(ctx, h, out, &changed));
+  if (changed) {
+    CU(cudaMemcpyAsync(ctx->best.p, h.best.data(), h.best.size() * 8, cudaMemcpyHostToDevice,
+                       st));
+    CU(cudaMemcpyAsync(ctx->best_step.p, h.bstep.data(), h.bstep.size() * 8,
+                       cudaMemcpyHostToDevice, st));
+    CU(cudaStreamSynchronize(st));
+  }
+  return SHAKEN_OK;
+}
+
+// The member table of a batch plan for the packed copies.
+static shaken_status member_table(Plan& P, cudaStream_t st) {
+  if (P.mtab_valid) return SHAKEN_OK;
+  std::vector<shk::MemberDev> m;
+  size_t so = 0, oo = 0;
+  P.max_state_words = P.max_obs = 0;
+  for (shaken_ctx* c : P.members) {
+    shk::MemberDev d{};
+    d.A = static_cast<uint32_t*>(c->A.p);
+    d.B = static_cast<uint32_t*>(c->B.p);
+    d.obs = c->obs_sums.as<double>();
+    d.best = c->best.as<double>();
+    d.best_step = c->best_step.as<long long>();
+    d.state_off = so;
+    d.obs_off = oo;
+    d.state_words = (uint32_t)(c->spin_bytes / 4);
+    d.R = (uint32_t)c->R;
+    so += d.state_words;
+    oo += (size_t)c->R * (kNumSums + 2);
+    P.max_state_words = std::max(P.max_state_words, d.state_words);
+    P.max_obs = std::max(P.max_obs, (uint32_t)(c->R * (kNumSums + 2)));
+    m.push_back(d);
+  }
+  TRY(upload(P.mtab, m.data(), m.size() * sizeof(shk::MemberDev), st));
+  P.state_words = so;
+  P.obs_doubles = oo;
+  P.mtab_valid = true;
+  return SHAKEN_OK;
+}
+
+static shaken_status stage(DevMem& d, size_t bytes) {
+  if (d.p == nullptr || d.bytes < bytes) TRY(d.alloc(bytes));
   return SHAKEN_OK;
 }
 
@@ -1180,21 +1222,85 @@ shaken_status shaken_batch_observables(shaken_batch* b, shaken_obs* out) {
   if (P.members.empty()) return SHAKEN_OK;
   cudaStream_t st = b->stream;
   if (P.dirty) TRY(build_plan(P, st));
+  TRY(member_table(P, st));
+  TRY(stage(P.stage_obs, P.obs_doubles * sizeof(double)));
   for (shaken_ctx* c : P.members)
     CU(cudaMemsetAsync(c->obs_sums.p, 0, c->obs_sums.bytes, st));
   uint64_t nl = 0;
   TRY(obs_launch(P, st, &nl));
-  b->launches += nl;
-  std::vector<ObsHost> h(P.members.size());
-  for (size_t i = 0; i < P.members.size(); ++i) TRY(obs_copy(P.members[i], h[i], st));
+  const int n = (int)P.members.size();
+  CU(shk::launch_member_copy(2, P.mtab.as<shk::MemberDev>(), n, P.stage_obs.p, P.max_obs, st));
+  b->launches += nl + 1;
+  std::vector<double> packed(P.obs_doubles);
+  CU(cudaMemcpyAsync(packed.data(), P.stage_obs.p, packed.size() * sizeof(double),
+                     cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
-  bool h2d = false;
-  size_t off = 0;
-  for (size_t i = 0; i < P.members.size(); ++i) {
-    TRY(obs_finish(P.members[i], h[i], out + off, st, &h2d));
-    off += (size_t)P.members[i]->R;
+  // members' records from the packed buffer; best energies updated in place
+  bool any = false;
+  size_t off = 0, oo = 0;
+  for (shaken_ctx* c : P.members) {
+    const size_t R = (size_t)c->R, ns = R * kNumSums;
+    ObsHost h;
+    h.sums.assign(packed.begin() + oo, packed.begin() + oo + ns);
+    h.best.assign(packed.begin() + oo + ns, packed.begin() + oo + ns + R);
+    h.bstep.resize(R);
+    std::memcpy(h.bstep.data(), packed.data() + oo + ns + R, R * sizeof(long long));
+    bool changed = false;
+    TRY(obs_values(c, h, out + off, &changed));
+    if (changed) {
+      std::copy(h.best.begin(), h.best.end(), packed.begin() + oo + ns);
+      std::memcpy(packed.data() + oo + ns + R, h.bstep.data(), R * sizeof(long long));
+      any = true;
+    }
+    off += R;
+    oo += R * (kNumSums + 2);
   }
-  if (h2d) CU(cudaStreamSynchronize(st));
+  if (any) {
+    CU(cudaMemcpyAsync(P.stage_obs.p, packed.data(), packed.size() * sizeof(double),
+                       cudaMemcpyHostToDevice, st));
+    CU(shk::launch_member_copy(3, P.mtab.as<shk::MemberDev>(), n, P.stage_obs.p, P.max_obs,
+                               st));
+    b->launches += 1;
+    CU(cudaStreamSynchronize(st));
+  }
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_batch_state_bytes(shaken_batch* b, size_t* bytes) {
+  if (!b || !bytes) return fail(SHAKEN_E_INVAL, "NULL argument");
+  size_t n = 0;
+  for (shaken_ctx* c : b->plan.members) n += c->spin_bytes;
+  *bytes = n;
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_batch_set_states_raw(shaken_batch* b, const void* host, size_t bytes) {
+  if (!b || !host) return fail(SHAKEN_E_INVAL, "NULL argument");
+  Plan& P = b->plan;
+  if (P.members.empty()) return SHAKEN_OK;
+  cudaStream_t st = b->stream;
+  TRY(member_table(P, st));
+  if (bytes != P.state_words * 4) return fail(SHAKEN_E_INVAL, "state size mismatch");
+  TRY(stage(P.stage_state, bytes));
+  CU(cudaMemcpyAsync(P.stage_state.p, host, bytes, cudaMemcpyHostToDevice, st));
+  CU(shk::launch_member_copy(1, P.mtab.as<shk::MemberDev>(), (int)P.members.size(),
+                             P.stage_state.p, P.max_state_words, st));
+  b->launches += 1;
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_batch_get_states_raw_async(shaken_batch* b, void* host, size_t bytes) {
+  if (!b || !host) return fail(SHAKEN_E_INVAL, "NULL argument");
+  Plan& P = b->plan;
+  if (P.members.empty()) return SHAKEN_OK;
+  cudaStream_t st = b->stream;
+  TRY(member_table(P, st));
+  if (bytes != P.state_words * 4) return fail(SHAKEN_E_INVAL, "state size mismatch");
+  TRY(stage(P.stage_state, bytes));
+  CU(shk::launch_member_copy(0, P.mtab.as<shk::MemberDev>(), (int)P.members.size(),
+                             P.stage_state.p, P.max_state_words, st));
+  b->launches += 1;
+  CU(cudaMemcpyAsync(host, P.stage_state.p, bytes, cudaMemcpyDeviceToHost, st));
   return SHAKEN_OK;
 }
 

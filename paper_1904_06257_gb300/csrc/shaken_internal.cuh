@@ -204,6 +204,22 @@ struct CtxDev {
   double* series_H;     // [cap][R] or null
 };
 
+// One member of a batch for the batched state and observables copies: its state
+// buffers and observables arrays and where they sit in the packed buffers.  The
+// packed observables of a member are [R][kNumSums] sums, then R best energies,
+// then R best steps (as the bits of a double).
+struct MemberDev {
+  uint32_t* A;                   // sigma
+  uint32_t* B;                   // sigma'
+  const double* obs;             // [R][kNumSums] observables sums
+  double* best;                  // [R]
+  long long* best_step;          // [R]
+  unsigned long long state_off;  // first 32-bit word of its state in the packed states
+  unsigned long long obs_off;    // first double of its records in the packed observables
+  uint32_t state_words;          // state size in 32-bit words
+  uint32_t R;
+};
+
 // Sum slots of a replica (all integer valued except the real-J graph sums).
 enum : int {
   kSumM = 0,   // sum sigma

@@ -103,6 +103,9 @@ def _load():
         "shaken_get_state_raw": [vp, vp, sz],
         "shaken_get_state_raw_async": [vp, vp, sz],
         "shaken_batch_observables": [vp, vp],
+        "shaken_batch_state_bytes": [vp, ctypes.POINTER(sz)],
+        "shaken_batch_set_states_raw": [vp, vp, sz],
+        "shaken_batch_get_states_raw_async": [vp, vp, sz],
         "shaken_server_create": [ctypes.POINTER(vp), sz, ctypes.c_uint32, vp],
         "shaken_server_submit": [vp, ctypes.POINTER(shaken_problem), u64, vp, u64,
                                  ctypes.POINTER(i64)],
@@ -381,6 +384,22 @@ def shaken_get_state_raw(ctx, host_buf_ptr: int, nbytes: int):
 def shaken_get_state_raw_async(ctx, host_buf_ptr: int, nbytes: int):
     """Enqueue the copy of sigma; the buffer holds it after the next synchronising call."""
     _check(_lib.shaken_get_state_raw_async(ctx, ctypes.c_void_p(host_buf_ptr), nbytes))
+
+
+def shaken_batch_state_bytes(batch) -> int:
+    n = ctypes.c_size_t()
+    _check(_lib.shaken_batch_state_bytes(batch, ctypes.byref(n)))
+    return n.value
+
+
+def shaken_batch_set_states_raw(batch, host_buf_ptr: int, nbytes: int):
+    """All members' raw states (concatenated in member order) in one host-to-device copy."""
+    _check(_lib.shaken_batch_set_states_raw(batch, ctypes.c_void_p(host_buf_ptr), nbytes))
+
+
+def shaken_batch_get_states_raw_async(batch, host_buf_ptr: int, nbytes: int):
+    """Enqueue the gather and one device-to-host copy of all members' states."""
+    _check(_lib.shaken_batch_get_states_raw_async(batch, ctypes.c_void_p(host_buf_ptr), nbytes))
 
 
 def shaken_batch_observables(batch, replicas_total: int):

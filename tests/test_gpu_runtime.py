@@ -62,7 +62,8 @@ def test_batch_equals_alone(S, use_graph):
 def test_batch_observables_and_async_state_equal_per_context_calls(S):
     """shaken_batch_observables (one launch per family for all members) gives each
     member's records exactly as shaken_observables on the same states, in member
-    order; shaken_get_state_raw_async gives the bytes of shaken_get_state_raw."""
+    order; shaken_get_state_raw_async gives the bytes of shaken_get_state_raw; the
+    packed batch copies (one transfer for all members) agree with both."""
     import torch
     b = S.shaken_batch_create()
     ctxs = []
@@ -87,6 +88,30 @@ def test_batch_observables_and_async_state_equal_per_context_calls(S):
             assert np.array_equal(batched[f][off:off + R], single[f]), f
         off += R
     assert off == total
+    # all states in one transfer each way: equal to the per-context raw copies, and
+    # a second batch loaded from them holds the same states
+    tot = S.shaken_batch_state_bytes(b)
+    assert tot == sum(sizes)
+    packed = torch.zeros(tot, dtype=torch.uint8, pin_memory=True)
+    S.shaken_batch_get_states_raw_async(b, packed.data_ptr(), tot)
+    S.shaken_batch_sync(b)
+    assert torch.equal(packed, torch.cat(bufs))
+    b2 = S.shaken_batch_create()
+    ctxs2 = []
+    for p, seed, n, R in make_members(S):
+        c = S.shaken_init(p, seed + 100)
+        S.shaken_batch_add(b2, c)
+        ctxs2.append(c)
+    S.shaken_batch_set_states_raw(b2, packed.data_ptr(), tot)
+    S.shaken_batch_sync(b2)
+    for c, buf, n in zip(ctxs2, bufs, sizes):
+        got = torch.zeros(n, dtype=torch.uint8, pin_memory=True)
+        S.shaken_get_state_raw(c, got.data_ptr(), n)
+        assert torch.equal(got, buf)
+    for c in ctxs2:
+        S.shaken_batch_remove(b2, c)
+        S.shaken_free(c)
+    S.shaken_batch_free(b2)
     for c, _ in ctxs:
         S.shaken_batch_remove(b, c)
         S.shaken_free(c)
