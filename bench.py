@@ -39,6 +39,9 @@ REPLICAS_PER_GROUP = 32
 L_CHOICES = (32, 64, 128, 256, 512)
 Q, J, LAM = 1.0, 1.0, 0.0
 FLUSH_BYTES = 256 << 20  # > 129 MB L2
+# the half-step launches of every 4th timed step are bracketed by CUDA events: the
+# events take device time themselves (about 4% of a step when every launch is timed)
+TIMING_STRIDE = 4
 
 
 def workload(rank: int):
@@ -242,7 +245,7 @@ def run_ours(args, rank, world, local_rank):
     while time.perf_counter() < t_end:
         S.shaken_batch_step(batch, 32, True)
         S.shaken_batch_sync(batch)
-    S.shaken_batch_set_timing(batch, True)
+    S.shaken_batch_set_timing(batch, TIMING_STRIDE)
     l0 = S.shaken_batch_launch_count(batch)
     if world > 1:
         torch.distributed.barrier()
@@ -399,6 +402,7 @@ def run_ours(args, rank, world, local_rank):
                 "updates_per_launch": ups / 2.0,
                 "avg_launch_ms": avg_kernel_s * 1e3,
                 "timed_launches": kern_n,
+                "timed_every_nth_step": TIMING_STRIDE,
                 "microbench_per_s": rates,
                 # HBM side: 0.25 B per update (one state bit read and written)
                 "hbm_view": {

@@ -246,11 +246,14 @@ shaken_status shaken_batch_observables(shaken_batch* b, shaken_obs* out);
 shaken_status shaken_batch_state_bytes(shaken_batch* b, size_t* bytes);
 shaken_status shaken_batch_set_states_raw(shaken_batch* b, const void* host, size_t bytes);
 shaken_status shaken_batch_get_states_raw_async(shaken_batch* b, void* host, size_t bytes);
-/* Kernel timing: with timing on, every half-step launch of a non-graph batch
- * step is bracketed by CUDA events on the batch stream.  kernel_time syncs
- * the stream and returns the summed device time (ms) and the number of timed
- * half-step launches since timing was switched on; launch_count is the total
- * number of kernels the batch has launched. */
+/* Kernel timing: set_timing(b, n) with n > 0 brackets the half-step launches of
+ * every n-th non-graph batch step (counted from this call; n = 1: every step)
+ * by CUDA events on the batch stream, n = 0 switches timing off, n < 0 is
+ * E_INVAL (the events cost device time themselves, so a stride keeps the
+ * timed run close to an untimed one).  kernel_time syncs the stream and returns
+ * the summed device time (ms) and the number of timed half-step launches since
+ * timing was set; launch_count is the total number of kernels the batch has
+ * launched. */
 shaken_status shaken_batch_set_timing(shaken_batch* b, int on);
 shaken_status shaken_batch_kernel_time(shaken_batch* b, double* ms, uint64_t* launches);
 shaken_status shaken_batch_launch_count(shaken_batch* b, uint64_t* count);

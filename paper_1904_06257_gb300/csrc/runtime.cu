@@ -146,7 +146,8 @@ struct Plan {
   bool dirty = true;
   bool autotune = true;  // pick the lattice tile shape by timing trial launches
   int blocks_per_sm = 8;
-  bool timing = false;
+  int timing = 0;           // bracket the half-step launches of every timing-th step (0: off)
+  uint64_t steps_issued = 0;  // non-graph steps launched (for the timing stride)
   unsigned long long* rng_counter = nullptr;  // device counter of Philox calls (lattice), or null
   std::vector<cudaEvent_t> ev_free;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
@@ -479,7 +480,8 @@ static shaken_status build_plan(Plan& P, cudaStream_t st) {
 static shaken_status plan_step_launch(Plan& P, cudaStream_t st, uint64_t* nl,
                                       bool capturing = false) {
   uint64_t count = 0;
-  const bool timed = P.timing && !capturing;
+  const bool timed = P.timing > 0 && !capturing && P.steps_issued % (uint64_t)P.timing == 0;
+  if (!capturing) ++P.steps_issued;
   bool obs_needed = false;
   int ex = 0;
   for (shaken_ctx* c : P.members) {
@@ -1578,7 +1580,9 @@ shaken_status shaken_batch_set_timing(shaken_batch* b, int on) {
   if (!b) return fail(SHAKEN_E_INVAL, "batch is NULL");
   CU(cudaStreamSynchronize(b->stream));
   b->plan.collect();
-  b->plan.timing = on != 0;
+  if (on < 0) return fail(SHAKEN_E_INVAL, "timing stride must be >= 0");
+  b->plan.timing = on;
+  b->plan.steps_issued = 0;
   b->plan.timed_ms = 0.0;
   b->plan.timed_n = 0;
   return SHAKEN_OK;

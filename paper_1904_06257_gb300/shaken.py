@@ -345,8 +345,9 @@ def shaken_autotune_clear():
     _check(_lib.shaken_autotune_clear())
 
 
-def shaken_batch_set_timing(batch, on: bool):
-    _check(_lib.shaken_batch_set_timing(batch, int(bool(on))))
+def shaken_batch_set_timing(batch, every):
+    """every: 0 off, n > 0 time the half-step launches of every n-th step (True = 1)."""
+    _check(_lib.shaken_batch_set_timing(batch, int(every)))
 
 
 def shaken_batch_kernel_time(batch):
