@@ -331,7 +331,10 @@ def run_ours(args, rank, world, local_rank):
            "what": "per job of K steps: the raw states of all 128 groups H2D in one copy "
                    "from pinned memory, K batched steps (CUDA graph), all states D2H in one "
                    "copy and the observables of all 4096 replicas (one batched call); "
-                   "wall clock"}
+                   "wall clock",
+           "note": "can exceed value: the steps replay a CUDA graph and the state stays in "
+                   "L2 between them, while every device-timed step starts after an L2 "
+                   "flush"}
 
     # ---- plain single-lattice kernel: L = 4096, one replica, int8 and bit-packed
     Lp = 4096
