@@ -623,6 +623,7 @@ __global__ void __launch_bounds__(kTile, kLatMinBlocks) lattice_half_kernel(cons
   __shared__ TileShared sh;
   __shared__ Pending queue[kTile / 32][32 * WPT + 32];  // a tile's words + fewer than 32 left
   __shared__ double red[(kTile / 32) * 3];
+  pdl_enter();
   uint32_t calls = 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // balanced contiguous split: block b walks tiles [b n / G, (b+1) n / G)
@@ -777,6 +778,7 @@ __global__ void __launch_bounds__(kTile) lattice_obs_single_kernel(
     const LatJob* __restrict__ jobs, const Tile* __restrict__ tiles, int n_tiles, int which,
     int full, int wpt) {
   __shared__ double red[(kTile / 32) * 3];
+  pdl_enter();
   for (int ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
     const Tile tl = tiles[ti];
     const LatJob& J = jobs[tl.job];
@@ -815,6 +817,7 @@ __global__ void __launch_bounds__(kTile) lattice_obs_multispin_kernel(
     const LatJob* __restrict__ jobs, const Tile* __restrict__ tiles, int n_tiles, int which,
     int full, int wpt) {
   __shared__ int red[kTile / 32][32][6];
+  pdl_enter();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
     const Tile tl = tiles[ti];
@@ -1051,8 +1054,8 @@ static cudaError_t launch_half_t(const LatJob* jobs, const Tile* tiles, int n_ti
     occ = o > 0 ? o : 1;
   }
   const int grid = grid_for(n_tiles, occ);
-  lattice_half_kernel<ENC, WPT><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, half, rng_calls);
-  return cudaGetLastError();
+  return launch_dependent(lattice_half_kernel<ENC, WPT>, dim3(grid), dim3(kTile), 0, st, jobs,
+                          tiles, n_tiles, half, rng_calls);
 }
 
 int lattice_resident_blocks() {
@@ -1107,18 +1110,15 @@ cudaError_t launch_lattice_obs(int enc, int wpt, const LatJob* jobs, const Tile*
   const int grid = grid_for(n_tiles, 8);
   switch (enc) {
     case kEncInt8:
-      lattice_obs_single_kernel<kEncInt8><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, which, full,
-                                                                   wpt);
-      break;
+      return launch_dependent(lattice_obs_single_kernel<kEncInt8>, dim3(grid), dim3(kTile), 0,
+                              st, jobs, tiles, n_tiles, which, full, wpt);
     case kEncPacked:
-      lattice_obs_single_kernel<kEncPacked><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, which,
-                                                                    full, wpt);
-      break;
+      return launch_dependent(lattice_obs_single_kernel<kEncPacked>, dim3(grid), dim3(kTile), 0,
+                              st, jobs, tiles, n_tiles, which, full, wpt);
     default:
-      lattice_obs_multispin_kernel<<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, which, full, wpt);
-      break;
+      return launch_dependent(lattice_obs_multispin_kernel, dim3(grid), dim3(kTile), 0, st, jobs,
+                              tiles, n_tiles, which, full, wpt);
   }
-  return cudaGetLastError();
 }
 
 }  // namespace shk

@@ -10,6 +10,7 @@ namespace shk {
 // best and the optional series, and the sums are cleared; then t += 1.
 // H = -(Jc E) - 2 lamc M - 2 LS (Eq. (ham1); on the lattice Eq. (HGibbs)).
 __global__ void __launch_bounds__(256) epilogue_kernel(CtxDev* const* __restrict__ ctxs, int n) {
+  pdl_enter();
   if (blockIdx.x >= (unsigned)n) return;
   CtxDev* cd = ctxs[blockIdx.x];
   const uint32_t t = cd->step;
@@ -126,8 +127,7 @@ cudaError_t launch_member_copy(int what, const MemberDev* m, int n, void* buf,
 
 cudaError_t launch_epilogue(CtxDev* const* ctxs, int n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  epilogue_kernel<<<n, 256, 0, st>>>(ctxs, n);
-  return cudaGetLastError();
+  return launch_dependent(epilogue_kernel, dim3(n), dim3(256), 0, st, ctxs, n);
 }
 
 cudaError_t launch_philox(uint64_t seed, const uint32_t* ctr, uint32_t* out, int64_t n,

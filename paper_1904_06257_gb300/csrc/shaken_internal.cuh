@@ -30,6 +30,33 @@ constexpr uint32_t kPhW1 = 0xBB67AE85u;
 constexpr uint32_t kInitStep = 0xFFFFFFFFu;  // step index of the initial draw
 
 constexpr int kTile = 256;  // threads per block; graph tiles hold kTile vertices
+
+// ---------------------------------------------------------------- dependent launches
+// The kernels of a step (half steps, observables, epilogue) are launched with
+// programmatic stream serialization: a kernel may be scheduled while its
+// predecessor on the stream drains, and it waits for that predecessor's completion
+// and memory (griddepcontrol.wait) before it touches global memory.  Each such
+// kernel also lets its own successor be scheduled as soon as all its blocks run.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... P, typename... A>
+cudaError_t launch_dependent(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t st, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 constexpr int kWordsPerThread = 4;                   // lattice lane words per thread and tile
 constexpr int kLatTile = kTile * kWordsPerThread;    // lattice lane words per tile
 constexpr int kLatMinBlocks = 3;                     // resident blocks per SM of the half-step kernel
