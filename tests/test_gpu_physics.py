@@ -7,7 +7,8 @@ references (lambda = 0, J = 1):
 * as q grows the energy approaches Onsager's closed form (Thm 3.1: the measure
   tends to Gibbs when e^{-2 beta q} is small), monotonically in q;
 * a small field lambda = 0.01 (no closed form) raises m at every q, and the CUDA
-  chain's m at lambda = 0.01 agrees with the oracle chain's run from other seeds."""
+  chain's m at lambda = 0.01 agrees with the oracle chain's run from other seeds;
+* in the paramagnetic phase the chain started at +1 relaxes to m = 0."""
 import numpy as np
 import pytest
 
@@ -41,6 +42,11 @@ def test_energy_matches_triangular_heat_bath(S, q, beta):
     e_ref, m_ref = exact.triangular_heat_bath(L, 1.0, q, beta, sweeps=3000, burn=300, seed=5)
     r_mean, r_se = e_ref.mean(), exact.batch_means_se(e_ref)
     assert abs(g_mean - r_mean) < 4 * np.hypot(g_se, r_se), (g_mean, r_mean, g_se, r_se)
+    # |m| as well (all four points are in the paramagnetic phase: finite-size |m|)
+    am = np.abs(m_gpu).mean(axis=0)
+    ga, ga_se = am.mean(), am.std(ddof=1) / np.sqrt(am.size)
+    ra, ra_se = np.abs(m_ref).mean(), exact.batch_means_se(np.abs(m_ref))
+    assert abs(ga - ra) < 4 * np.hypot(ga_se, ra_se), (ga, ra, ga_se, ra_se)
 
 
 def test_energy_approaches_onsager_as_q_grows(S):
@@ -53,6 +59,15 @@ def test_energy_approaches_onsager_as_q_grows(S):
     # e^{-2 beta q} = 0.74 ... 0.008: the deviation from Onsager shrinks with q
     assert all(a > b for a, b in zip(dev, dev[1:])), dev
     assert dev[-1] < 0.1 * dev[0], dev
+
+
+def test_paramagnetic_relaxation_from_all_plus(S):
+    """beta = 0.40 at q = 1 is below the shaken chain's critical beta (0.658, the
+    honeycomb curve of its doubled graph): from +1 the magnetisation relaxes to 0."""
+    _, m = gpu_series(S, 128, 1.0, 0.40, burn=500, steps=500, seed=51, init=1)
+    per = m.mean(axis=0)
+    assert abs(per.mean()) < 4 * per.std(ddof=1) / np.sqrt(per.size) + 1e-3, per.mean()
+    assert abs(per.mean()) < 0.02
 
 
 @pytest.mark.parametrize("q", [0.5, 1.0, 2.0])
