@@ -60,8 +60,8 @@ __global__ void __launch_bounds__(256) pack_states_kernel(const MemberDev* __res
                                                           uint32_t* __restrict__ dst) {
   const MemberDev M = m[blockIdx.y];
   uint32_t* d = dst + M.state_off;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < M.state_words;
-       i += gridDim.x * blockDim.x)
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < M.state_words;
+       i += (size_t)gridDim.x * blockDim.x)
     d[i] = M.A[i];
 }
 
@@ -69,8 +69,8 @@ __global__ void __launch_bounds__(256) unpack_states_kernel(const MemberDev* __r
                                                             const uint32_t* __restrict__ src) {
   const MemberDev M = m[blockIdx.y];
   const uint32_t* s = src + M.state_off;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < M.state_words;
-       i += gridDim.x * blockDim.x) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < M.state_words;
+       i += (size_t)gridDim.x * blockDim.x) {
     const uint32_t v = s[i];
     M.A[i] = v;
     M.B[i] = v;
@@ -108,12 +108,13 @@ __global__ void __launch_bounds__(256) unpack_best_kernel(const MemberDev* __res
 
 // what: 0 pack states, 1 unpack states, 2 pack observables, 3 unpack best energies
 cudaError_t launch_member_copy(int what, const MemberDev* m, int n, void* buf,
-                               uint32_t max_words, cudaStream_t st) {
+                               unsigned long long max_words, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  uint32_t bx = (max_words + 255u) / 256u;
-  if (bx < 1u) bx = 1u;
-  if (bx > 64u) bx = 64u;
-  const dim3 grid(bx, (unsigned)n);
+  if (n > 65535) return cudaErrorInvalidConfiguration;  // one grid row per member
+  unsigned long long bx = (max_words + 255ull) / 256ull;
+  if (bx < 1ull) bx = 1ull;
+  if (bx > 64ull) bx = 64ull;
+  const dim3 grid((unsigned)bx, (unsigned)n);
   if (what == 0)
     pack_states_kernel<<<grid, 256, 0, st>>>(m, static_cast<uint32_t*>(buf));
   else if (what == 1)

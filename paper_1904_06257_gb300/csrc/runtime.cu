@@ -46,7 +46,8 @@ cudaError_t launch_graph_obs(const GraphJob*, const Tile*, int, int, int, cudaSt
 cudaError_t launch_graph_fields(const GraphJob*, const Tile*, int, uint32_t, float*,
                                 cudaStream_t);
 cudaError_t launch_epilogue(CtxDev* const*, int, cudaStream_t);
-cudaError_t launch_member_copy(int, const shk::MemberDev*, int, void*, uint32_t, cudaStream_t);
+cudaError_t launch_member_copy(int, const shk::MemberDev*, int, void*, unsigned long long,
+                               cudaStream_t);
 cudaError_t launch_lattice_resident(int, const LatJob*, int, uint32_t, uint32_t, uint32_t,
                                     cudaStream_t);
 cudaError_t launch_philox(uint64_t, const uint32_t*, uint32_t*, int64_t, cudaStream_t);
@@ -158,7 +159,7 @@ struct Plan {
   DevMem mtab;                 // MemberDev per member
   size_t state_words = 0;      // packed states, 32-bit words
   size_t obs_doubles = 0;      // packed observables, doubles
-  uint32_t max_state_words = 0, max_obs = 0;
+  unsigned long long max_state_words = 0, max_obs = 0;
   DevMem stage_state, stage_obs;
   ~Plan() {
     drop_graph();
@@ -1186,6 +1187,8 @@ shaken_status shaken_observables(shaken_ctx* ctx, shaken_obs* out) {
 // The member table of a batch plan for the packed copies.
 static shaken_status member_table(Plan& P, cudaStream_t st) {
   if (P.mtab_valid) return SHAKEN_OK;
+  if (P.members.size() > 65535)
+    return fail(SHAKEN_E_INVAL, "batched copies take at most 65535 members");
   std::vector<shk::MemberDev> m;
   size_t so = 0, oo = 0;
   P.max_state_words = P.max_obs = 0;
@@ -1198,12 +1201,12 @@ static shaken_status member_table(Plan& P, cudaStream_t st) {
     d.best_step = c->best_step.as<long long>();
     d.state_off = so;
     d.obs_off = oo;
-    d.state_words = (uint32_t)(c->spin_bytes / 4);
+    d.state_words = c->spin_bytes / 4;
     d.R = (uint32_t)c->R;
     so += d.state_words;
     oo += (size_t)c->R * (kNumSums + 2);
     P.max_state_words = std::max(P.max_state_words, d.state_words);
-    P.max_obs = std::max(P.max_obs, (uint32_t)(c->R * (kNumSums + 2)));
+    P.max_obs = std::max(P.max_obs, (unsigned long long)c->R * (kNumSums + 2));
     m.push_back(d);
   }
   TRY(upload(P.mtab, m.data(), m.size() * sizeof(shk::MemberDev), st));

@@ -243,8 +243,9 @@ struct MemberDev {
   long long* best_step;          // [R]
   unsigned long long state_off;  // first 32-bit word of its state in the packed states
   unsigned long long obs_off;    // first double of its records in the packed observables
-  uint32_t state_words;          // state size in 32-bit words
+  unsigned long long state_words;  // state size in 32-bit words
   uint32_t R;
+  uint32_t pad;
 };
 
 // Sum slots of a replica (all integer valued except the real-J graph sums).
