@@ -304,19 +304,28 @@ __device__ __forceinline__ void decide_tail(LaneWord& L, const LatTable& tab, co
 }
 
 // --------------------------------------------------------------------------- int8 <-> bits
-// 4 bytes of +1/-1 -> 4 bits (bit k = byte k is +1).  +1 = 0x01, -1 = 0xFF: the
-// sign bit of each byte is clear for +1.
-__device__ __forceinline__ uint32_t bits4(uint32_t w) {
-  const uint32_t pos = (~w >> 7) & 0x01010101u;        // 1 per +1 byte at bit 0 of each byte
-  return ((pos * 0x00204081u) >> 21) & 0xFu;           // gather bytes 0..3 -> bits 0..3
+// +1 = 0x01, -1 = 0xFF: the sign bit of a byte is clear for +1.
+// Eight bytes (w0: sites 0..3, w1: sites 4..7, memory order) -> bits 24..31 of the
+// result (bit 24 + j = site j is +1): the clear sign bits go to bits 0, 8, 16, 24
+// (w0) and 4, 12, 20, 28 (w1), and one multiply by 2^24 + 2^17 + 2^10 + 2^3 moves
+// byte k of w0 to bit 24 + k and byte k of w1 to bit 28 + k; every other partial
+// product lands below bit 24 at a distinct position or above bit 31, so nothing
+// carries into the top byte.
+__device__ __forceinline__ uint32_t bits8_top(uint32_t w0, uint32_t w1) {
+  const uint32_t m = ((~w0 >> 7) & 0x01010101u) | ((~w1 >> 3) & 0x10101010u);
+  return m * 0x01020408u;
 }
-__device__ __forceinline__ uint32_t bits16(uint4 v) {
-  return bits4(v.x) | (bits4(v.y) << 4) | (bits4(v.z) << 8) | (bits4(v.w) << 12);
+// 32 bytes (sites 0..15 in a, 16..31 in b) -> 32 bits, bit j = site j is +1.
+__device__ __forceinline__ uint32_t bits32(uint4 a, uint4 b) {
+  const uint32_t lo = __byte_perm(bits8_top(a.x, a.y), bits8_top(a.z, a.w), 0x0073u);
+  const uint32_t hi = __byte_perm(bits8_top(b.x, b.y), bits8_top(b.z, b.w), 0x0073u);
+  return __byte_perm(lo, hi, 0x5410u);
 }
-// 4 bits -> 4 bytes of +1/-1
+// 4 bits -> 4 bytes of +1/-1: bit k -> byte k (0 or 1), then 0xFF - 0xFE t per byte
+// (no byte borrows from its neighbour)
 __device__ __forceinline__ uint32_t bytes4(uint32_t b) {
-  const uint32_t spread = ((b & 0xFu) * 0x00204081u) & 0x01010101u;  // bit k -> byte k
-  return ~(spread * 0xFEu);                                           // 1 -> 0x01, 0 -> 0xFF
+  const uint32_t t = ((b & 0xFu) * 0x00204081u) & 0x01010101u;
+  return 0xFFFFFFFFu - 0xFEu * t;
 }
 __device__ __forceinline__ uint4 bytes16(uint32_t b) {
   return make_uint4(bytes4(b), bytes4(b >> 4), bytes4(b >> 8), bytes4(b >> 12));
@@ -424,8 +433,8 @@ __device__ __forceinline__ void load_lane_words(const LatJob& J, const void* buf
     const uint32_t jn = half == 0u ? (c == 0u ? L - 1u : 32u * c - 1u)
                                    : (32u * c + 32u == L ? 0u : 32u * c + 32u);
     const uint32_t nb = (ld_ro<NC>(A + (size_t)i * L + jn) >> 7) ^ 1u;  // 1 if +1
-    S = bits16(o0) | (bits16(o1) << 16);
-    V = bits16(v0) | (bits16(v1) << 16);
+    S = bits32(o0, o1);
+    V = bits32(v0, v1);
     H = half == 0u ? ((S << 1) | nb) : ((S >> 1) | (nb << 31));
   } else if (ENC == kEncPacked) {
     const uint32_t* A = static_cast<const uint32_t*>(buf);
@@ -896,7 +905,7 @@ __device__ __forceinline__ uint32_t resident_load(const LatJob& J, uint32_t w) {
     word_rc(J, w, i, c);
     const uint4* p = reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(J.A) +
                                                     (size_t)i * J.L + 32u * c);
-    return bits16(p[0]) | (bits16(p[1]) << 16);
+    return bits32(p[0], p[1]);
   }
   return static_cast<const uint32_t*>(J.A)[w];
 }
