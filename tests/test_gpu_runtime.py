@@ -108,6 +108,22 @@ def test_batch_observables_and_async_state_equal_per_context_calls(S):
         got = torch.zeros(n, dtype=torch.uint8, pin_memory=True)
         S.shaken_get_state_raw(c, got.data_ptr(), n)
         assert torch.equal(got, buf)
+    # size mismatches and a negative timing stride are rejected
+    with pytest.raises(S.ShakenError):
+        S.shaken_batch_set_states_raw(b2, packed.data_ptr(), tot - 4)
+    with pytest.raises(S.ShakenError):
+        S.shaken_batch_get_states_raw_async(b2, packed.data_ptr(), tot + 4)
+    with pytest.raises(S.ShakenError):
+        S.shaken_batch_set_timing(b2, -1)
+    # timing every step vs a stride of 3 (steps 0 and 3 of 5): 2/5 of the launches
+    S.shaken_batch_set_timing(b2, 1)
+    S.shaken_batch_step(b2, 5, False)
+    ms1, n1 = S.shaken_batch_kernel_time(b2)
+    S.shaken_batch_set_timing(b2, 3)
+    S.shaken_batch_step(b2, 5, False)
+    ms3, n3 = S.shaken_batch_kernel_time(b2)
+    S.shaken_batch_set_timing(b2, 0)
+    assert n1 > 0 and n1 % 10 == 0 and n3 * 5 == n1 * 2 and ms1 > 0.0 and ms3 > 0.0
     for c in ctxs2:
         S.shaken_batch_remove(b2, c)
         S.shaken_free(c)
