@@ -188,18 +188,34 @@ __device__ __forceinline__ LaneWord classify(uint32_t S, uint32_t V, uint32_t H,
   return L;
 }
 
-// Calls 0 and 1 (planes 31..24) of a lane word, made unconditionally: the two
-// Philox calls are independent and overlap.  After them about 12% of the words
-// still have an undecided lane (each lane is undecided with probability 2^-8).
+// Calls 0, 1 and 2 (planes 31..20) of a lane word, made unconditionally (the
+// resident small-lattice kernel, where a half step is a dependent chain and the
+// warp needs call 2 for some word about 98% of the time anyway): the three
+// Philox calls are independent and overlap.  A lane is decided by its first
+// differing plane, as call by call; after the twelve planes a lane is undecided
+// with probability 2^-12.
 template <bool COLL>
-__device__ __forceinline__ void decide_head(LaneWord& L, const LatTable& tab, const PhKey& K,
-                                            uint32_t a, uint32_t b, uint32_t t, uint32_t half,
-                                            uint32_t& calls) {
-  const uint4 w0 = ph_call(K, a, b, t, half);
-  const uint4 w1 = ph_call(K, a, b, t, half + 2u);
-  calls += 2;
-  apply_call<COLL>(L, w0, tab, 0u);
-  apply_call<COLL>(L, w1, tab, 1u);
+__device__ __forceinline__ void decide_head3(LaneWord& L, const LatTable& tab, const PhKey& K,
+                                             const PhShared& P, uint32_t a, uint32_t half,
+                                             uint32_t& calls) {
+  const uint4 w0 = ph_call_shared(K, P, a, half);
+  const uint4 w1 = ph_call_shared(K, P, a, half + 2u);
+  const uint4 w2 = ph_call_shared(K, P, a, half + 4u);
+  calls += 3;
+  // the top twelve bits of u and T compared as a subtraction, least significant
+  // plane first (borrow lt, equality eq): two short independent chains
+  uint32_t lt = 0u, eq = 0xffffffffu;
+#pragma unroll
+  for (int j = 11; j >= 0; --j) {
+    const uint4 Wc = j >= 8 ? w2 : j >= 4 ? w1 : w0;
+    const int i = j & 3;
+    const uint32_t w = i == 0 ? Wc.x : i == 1 ? Wc.y : i == 2 ? Wc.z : Wc.w;
+    const uint32_t Pj = plane_bits<COLL>(L, plane_row<COLL>(tab, j));
+    lt = (~w & Pj) | (~w & lt) | (Pj & lt);
+    eq &= ~(w ^ Pj);
+  }
+  L.res |= L.U & ~eq & lt;
+  L.U &= eq;
 }
 
 // Planes 31..24 (calls 0 and 1) of the thread's WPT lane words, plane-major:
@@ -289,14 +305,14 @@ __device__ __forceinline__ void decide_head_words(LaneWord (&Lw)[WPT], const Lat
   head_finish<WPT>(Lw, lt, eq);
 }
 
-// Calls 2..7 while some lane is undecided (one word at a time: the resident
+// Calls first..7 while some lane is undecided (one word at a time: the resident
 // small-lattice kernel).
 template <bool COLL>
 __device__ __forceinline__ void decide_tail(LaneWord& L, const LatTable& tab, const PhKey& K,
                                             const PhShared& P, uint32_t a, uint32_t half,
-                                            uint32_t& calls) {
+                                            uint32_t first, uint32_t& calls) {
 #pragma unroll 1
-  for (uint32_t call = 2; call < 8 && L.U != 0u; ++call) {
+  for (uint32_t call = first; call < 8 && L.U != 0u; ++call) {
     const uint4 w = ph_call_shared(K, P, a, half + 2u * call);
     ++calls;
     apply_call<COLL>(L, w, tab, call);
@@ -983,12 +999,12 @@ __global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* _
         LaneWord Lw;
         if (stab.collapsed) {
           Lw = classify<true>(S, V, H, F, stab);
-          decide_head<true>(Lw, stab, K, w, J.b, t, half, calls);
-          decide_tail<true>(Lw, stab, K, P, w, half, calls);
+          decide_head3<true>(Lw, stab, K, P, w, half, calls);
+          decide_tail<true>(Lw, stab, K, P, w, half, 3u, calls);
         } else {
           Lw = classify<false>(S, V, H, F, stab);
-          decide_head<false>(Lw, stab, K, w, J.b, t, half, calls);
-          decide_tail<false>(Lw, stab, K, P, w, half, calls);
+          decide_head3<false>(Lw, stab, K, P, w, half, calls);
+          decide_tail<false>(Lw, stab, K, P, w, half, 3u, calls);
         }
         out[w] = Lw.res;
         if (track && pos == 0u) {
