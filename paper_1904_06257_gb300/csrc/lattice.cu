@@ -992,6 +992,27 @@ __global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* _
       const uint32_t half = pos ^ order;  // update type of this position
       const uint32_t* in = pos == 0u ? sA : sB;
       uint32_t* out = pos == 0u ? sB : sA;
+      if (track && pos == 1u && threadIdx.x == 0) {
+        // block totals of sigma_t's sums (written before the barrier that ended
+        // position 0) -> best energy and series (Eq. (HGibbs)), off the barriers
+        int Mi = 0, Ei = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+          Mi += red[w][0];
+          Ei += red[w][1];
+        }
+        const double M = (double)Mi, E = (double)Ei;
+        const double Hs = -(Jc * E) - 2.0 * lamc * M;
+        if (Hs < best) {
+          best = Hs;
+          best_p[r] = Hs;
+          best_step_p[r] = (long long)t;
+        }
+        if (record && t - series_t0 < series_cap) {
+          const size_t k = (size_t)(t - series_t0) * Rn + r;
+          if (series_m) series_m[k] = M * inv_n;
+          if (series_H) series_H[k] = Hs;
+        }
+      }
       for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) {
         uint32_t S, V, H;
         load_lane_words<SENC, false>(J, in, w, half, S, V, H);
@@ -1014,34 +1035,13 @@ __global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* _
           acc[2] += dv + dh;
         }
       }
-      __syncthreads();
-    }
-    if (track) {
-      // block totals of sigma_t's sums -> best energy and series (Eq. (HGibbs))
+      if (track && pos == 0u) {  // warp totals of sigma_t's sums
 #pragma unroll
-      for (int q = 0; q < 2; ++q) acc[q] = __reduce_add_sync(0xffffffffu, acc[q]);
-      if ((threadIdx.x & 31) == 0)
-        for (int q = 0; q < 2; ++q) red[threadIdx.x >> 5][q] = acc[q];
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        int Mi = 0, Ei = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-          Mi += red[w][0];
-          Ei += red[w][1];
-        }
-        const double M = (double)Mi, E = (double)Ei;
-        const double Hs = -(Jc * E) - 2.0 * lamc * M;
-        if (Hs < best) {
-          best = Hs;
-          best_p[r] = Hs;
-          best_step_p[r] = (long long)t;
-        }
-        if (record && t - series_t0 < series_cap) {
-          const size_t k = (size_t)(t - series_t0) * Rn + r;
-          if (series_m) series_m[k] = M * inv_n;
-          if (series_H) series_H[k] = Hs;
-        }
+        for (int q = 0; q < 2; ++q) acc[q] = __reduce_add_sync(0xffffffffu, acc[q]);
+        if ((threadIdx.x & 31) == 0)
+          for (int q = 0; q < 2; ++q) red[threadIdx.x >> 5][q] = acc[q];
       }
+      __syncthreads();
     }
   }
   __syncthreads();
