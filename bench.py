@@ -204,10 +204,14 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
-    if args.only_graphs or args.only_serving:
+    if args.only_graphs or args.only_serving or args.only_small:
         if rank == 0:
-            part = (run_graphs(S, stream, torch, args) if args.only_graphs
-                    else run_serving(S, stream, args))
+            if args.only_small:
+                part = run_small(S, stream)
+            elif args.only_graphs:
+                part = run_graphs(S, stream, torch, args)
+            else:
+                part = run_serving(S, stream, args)
             print(json.dumps(part), flush=True)
         return None
     Ls, betas, seeds = workload(rank)
@@ -356,19 +360,7 @@ def run_ours(args, rank, world, local_rank):
     plain_rate = plain["int8"]
 
     # ---- small lattice: L = 64 int8, one replica, beta = 0.40, 10^4 steps with m and H per step
-    Ls1 = 64
-    p1 = S.Problem(S.LATTICE, S.INT8, 1, 0.40, Q, L=Ls1, J=J, lambda_const=LAM)
-    c1 = S.shaken_init(p1, W.BASE_SEED, stream)
-    S.shaken_step_record(c1, 100, 1)
-    t0 = time.perf_counter()
-    m1, e1 = S.shaken_step_record(c1, 10000, 1)
-    dt1 = time.perf_counter() - t0
-    S.shaken_free(c1)
-    small = {"L": Ls1, "steps": 10000, "seconds": dt1,
-             "updates_per_s": 2.0 * Ls1 * Ls1 * 10000 / dt1,
-             "us_per_step": dt1 / 10000 * 1e6,
-             "m_mean": float(m1[5000:].mean()), "e_per_site_mean": float(e1[5000:].mean() / Ls1**2),
-             "what": "shaken_step_record wall time: 10^4 steps with per-step m and H to host"}
+    small = run_small(S, stream)
 
     # ---- metastable regime (Sec. 3.2): m(t) from -1 at q = 0.1, lambda = 0.15
     meta = run_metastability(S, stream)
@@ -515,6 +507,26 @@ def committed_traffic(kernel: str):
     if not rec or rec.get("source_hash") != kernel_source_hash():
         return None
     return rec.get("bytes_per_launch")
+
+
+# ------------------------------------------------------------------------ small lattice
+def run_small(S, stream, L=64, steps=10000):
+    """The small-lattice workload: L = 64 int8, one replica, beta = 0.40, q = J = 1,
+    lambda = 0, 10^4 full steps with m and H of every step read back (one resident
+    launch per 65536 steps)."""
+    p1 = S.Problem(S.LATTICE, S.INT8, 1, 0.40, Q, L=L, J=J, lambda_const=LAM)
+    c1 = S.shaken_init(p1, W.BASE_SEED, stream)
+    S.shaken_step_record(c1, 100, 1)
+    t0 = time.perf_counter()
+    m1, e1 = S.shaken_step_record(c1, steps, 1)
+    dt1 = time.perf_counter() - t0
+    S.shaken_free(c1)
+    return {"L": L, "steps": steps, "seconds": dt1,
+            "updates_per_s": 2.0 * L * L * steps / dt1,
+            "us_per_step": dt1 / steps * 1e6,
+            "m_mean": float(m1[steps // 2:].mean()),
+            "e_per_site_mean": float(e1[steps // 2:].mean() / L**2),
+            "what": "shaken_step_record wall time: 10^4 steps with per-step m and H to host"}
 
 
 # ------------------------------------------------------------------------ metastability
@@ -802,6 +814,8 @@ def main():
     ap.add_argument("--only-graphs", action="store_true",
                     help="run the sparse-graph section only (profiling runs)")
     ap.add_argument("--only-serving", action="store_true", help="run the serving section only")
+    ap.add_argument("--only-small", action="store_true",
+                    help="run the small-lattice section only (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="fixed lattice launch-shape rule instead of timed trials (profiling)")
     ap.add_argument("--graph-anneal-steps", type=int, default=5000)
