@@ -147,6 +147,21 @@ def test_thm31_tv_to_gibbs_decreases_with_q():
     assert tv[-1] < 1e-4
 
 
+def test_thm31_tv_trend_on_4x4_torus():
+    """The same trend on a 4 x 4 torus (65,536 states), with pi in its product form
+    (equal to Z->_sigma / Z, pinned on the 3 x 3 torus above): the TV distance to
+    Gibbs falls strictly with q and is below 1e-5 at q = 16 (e^{-2 beta q} = 3e-6)."""
+    J, lam, beta, L = 1.0, 0.0, 0.4, 4
+    t, h = exact.lattice_edges(L)
+    S = exact.states(L * L)
+    Jo = exact.oriented_matrix(L * L, t, h, J)
+    g = exact.gibbs(S, t, h, J, lam, beta)
+    tv = [exact.total_variation(exact.stationary_product(S, Jo, lam, q, beta), g)
+          for q in (0.5, 1.0, 2.0, 4.0, 8.0, 16.0)]
+    assert all(a > b for a, b in zip(tv, tv[1:])), tv
+    assert tv[-1] < 1e-5, tv
+
+
 def test_frozen_set_restricts_chain():
     # a frozen site stays +1 and the restricted chain keeps Thm 2.1's measure
     J, q, lam, beta = 1.0, 0.6, 0.1, 0.8
