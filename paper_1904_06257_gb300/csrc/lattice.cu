@@ -1052,6 +1052,187 @@ __global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* _
   (void)calls;
 }
 
+// --------------------------------------------------------------------------- banded runs
+// Mid-size single lattices (INT8/PACKED, one replica, more lane words than one
+// block holds): a cooperative grid keeps the lattice in shared memory, in the
+// packed layout, as bands of rows for a whole run of n steps.  Block b owns rows
+// [b L / G, (b+1) L / G) and also holds the row above and the row below its band
+// (halo rows; the lattice wraps).  After each half step every block publishes the
+// first and the last row it computed to a global exchange area (two sets by
+// half-step parity, so a row is not overwritten while a neighbour may still read
+// it), passes a grid barrier and copies its neighbours' rows into its halo rows.
+// The draws, thresholds and decisions are those of lattice_half_kernel (head of
+// four words per thread, eight planes; words still undecided finish one by one),
+// so the trajectory is the same.
+
+constexpr uint32_t kBandSpinLimit = 1u << 21;  // barrier polls (about a second)
+
+// Grid barrier of a cooperative launch.  Every thread fences its global writes
+// (the published rows) first.  A block whose wait runs out, or that sees another
+// block's error, sets the error flag; returns false once the flag is set.
+__device__ __forceinline__ bool band_barrier(BandSync* bs, uint32_t& gen, uint32_t* s_flag) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t g = gen;
+    if (atomicAdd(&bs->count, 1u) == gridDim.x - 1u) {
+      atomicExch(&bs->count, 0u);
+      __threadfence();
+      atomicExch(&bs->gen, g + 1u);
+    } else {
+      uint32_t spins = 0;
+      while (atomicAdd(&bs->gen, 0u) == g) {
+        if (++spins > kBandSpinLimit || atomicAdd(&bs->err, 0u) != 0u) {
+          atomicExch(&bs->err, 1u);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    gen = g + 1u;
+    *s_flag = atomicAdd(&bs->err, 0u);
+  }
+  __syncthreads();
+  return *s_flag == 0u;
+}
+
+// S, V, H of local word l (column c) of a band buffer (packed rows of wpr words;
+// local rows 0 and nr + 1 are the halo rows, l lies in an own row).
+__device__ __forceinline__ void band_words(const uint32_t* buf, uint32_t l, uint32_t c,
+                                           uint32_t wpr, uint32_t typ, uint32_t& S, uint32_t& V,
+                                           uint32_t& H) {
+  S = buf[l];
+  const uint32_t rowbase = l - c;
+  if (typ == 0u) {  // dl: row i-1, column j-1
+    V = buf[l - wpr];
+    H = (S << 1) | (buf[rowbase + (c == 0u ? wpr - 1u : c - 1u)] >> 31);
+  } else {          // ur: row i+1, column j+1
+    V = buf[l + wpr];
+    H = (S >> 1) | (buf[rowbase + (c + 1u == wpr ? 0u : c + 1u)] << 31);
+  }
+}
+
+// One pass over W x kTile own words of the band starting at own word o0.
+template <bool COLL, bool MIR, int W>
+__device__ __forceinline__ void band_pass(const LatJob& J, const LatTable& tab,
+                                          const uint32_t* in, uint32_t* out, uint32_t o0,
+                                          uint32_t n_own, uint32_t w_first, uint32_t wpr,
+                                          uint32_t typ, const PhKey& K, const PhShared& P,
+                                          uint32_t& calls) {
+  LaneWord Lw[W];
+  uint32_t a[W], loc[W];
+  bool act[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    const uint32_t o = o0 + threadIdx.x + (uint32_t)k * kTile;
+    act[k] = o < n_own;
+    const uint32_t oo = act[k] ? o : 0u;
+    const uint32_t c = J.wpr_shift != 0xffffffffu ? (oo & (wpr - 1u)) : oo % wpr;
+    loc[k] = wpr + oo;    // own rows start at local row 1
+    a[k] = w_first + oo;  // global lane word: the Philox counter and the frozen mask
+    uint32_t S, V, H;
+    band_words(in, loc[k], c, wpr, typ, S, V, H);
+    const uint32_t F = (J.frozen != nullptr && act[k]) ? J.frozen[a[k]] : 0u;
+    Lw[k] = classify<COLL>(S, V, H, F, tab);
+    if (!act[k]) Lw[k].U = 0u;
+  }
+  decide_head_words<COLL, W, MIR>(Lw, tab, K, P, a, typ);
+  calls += 2u * W;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    if (!act[k]) continue;
+    if (Lw[k].U != 0u) decide_tail<COLL>(Lw[k], tab, K, P, a[k], typ, 2u, calls);
+    out[loc[k]] = Lw[k].res;
+  }
+}
+
+template <bool COLL, bool MIR>
+__device__ __forceinline__ void band_half(const LatJob& J, const LatTable& tab,
+                                          const uint32_t* in, uint32_t* out, uint32_t n_own,
+                                          uint32_t w_first, uint32_t wpr, uint32_t typ,
+                                          const PhKey& K, const PhShared& P, uint32_t& calls) {
+  uint32_t o0 = 0;
+  for (; o0 + (uint32_t)kLatTile <= n_own; o0 += kLatTile)
+    band_pass<COLL, MIR, kWordsPerThread>(J, tab, in, out, o0, n_own, w_first, wpr, typ, K, P,
+                                          calls);
+  for (; o0 < n_own; o0 += kTile)
+    band_pass<COLL, MIR, 1>(J, tab, in, out, o0, n_own, w_first, wpr, typ, K, P, calls);
+}
+
+// xch: exchange area, [2 parities][G blocks][first row, last row][wpr words].
+template <int ENC>
+__global__ void __launch_bounds__(kTile, kLatMinBlocks) lattice_band_kernel(
+    const LatJob* __restrict__ jobs, uint32_t* __restrict__ xch, BandSync* __restrict__ bs,
+    uint32_t t0, uint32_t n_steps) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ LatTable stab;
+  __shared__ LatJob sJ;  // the job descriptor, read from shared memory
+  __shared__ uint32_t s_flag;
+  if (threadIdx.x < sizeof(LatJob) / 4)
+    reinterpret_cast<uint32_t*>(&sJ)[threadIdx.x] =
+        reinterpret_cast<const uint32_t*>(jobs)[threadIdx.x];
+  __syncthreads();
+  const LatJob& J = sJ;
+  const uint32_t L = J.L, wpr = J.wpr, G = gridDim.x, b = blockIdx.x;
+  const uint32_t r0 = (uint32_t)(((uint64_t)b * L) / G);
+  const uint32_t r1 = (uint32_t)(((uint64_t)(b + 1u) * L) / G);
+  const uint32_t nr = r1 - r0, n_own = nr * wpr, n_loc = n_own + 2u * wpr;
+  uint32_t* buf[2] = {smem, smem + n_loc};  // sigma (A), sigma' (B)
+  const uint32_t order = J.cd->order;
+  uint32_t gen = 0;
+  if (threadIdx.x == 0) gen = atomicAdd(&bs->gen, 0u);
+  // sigma's rows r0 - 1 .. r1 (wrapping) and the table
+  for (uint32_t l = threadIdx.x; l < n_loc; l += blockDim.x) {
+    const uint32_t rl = l / wpr, c = l - rl * wpr;
+    const uint32_t g = (r0 + L + rl - 1u) % L;
+    buf[0][l] = resident_load<ENC>(J, g * wpr + c);
+  }
+  {
+    const uint32_t* g = reinterpret_cast<const uint32_t*>(J.table);
+    uint32_t* d = reinterpret_cast<uint32_t*>(&stab);
+    for (int k = threadIdx.x; k < (int)(sizeof(LatTable) / 4); k += blockDim.x) d[k] = g[k];
+  }
+  const PhKey K = ph_key(J.key0, J.key1);
+  const uint32_t w_first = r0 * wpr;
+  uint32_t calls = 0;
+  __syncthreads();
+  for (uint32_t st = 0; st < n_steps; ++st) {
+    const PhShared P = ph_shared(K, J.b, t0 + st);
+    for (uint32_t pos = 0; pos < 2u; ++pos) {
+      const uint32_t typ = pos ^ order;  // update type of this position
+      const uint32_t* in = buf[pos];
+      uint32_t* out = buf[pos ^ 1u];
+      if (stab.mirror)
+        band_half<true, true>(J, stab, in, out, n_own, w_first, wpr, typ, K, P, calls);
+      else if (stab.collapsed)
+        band_half<true, false>(J, stab, in, out, n_own, w_first, wpr, typ, K, P, calls);
+      else
+        band_half<false, false>(J, stab, in, out, n_own, w_first, wpr, typ, K, P, calls);
+      __syncthreads();
+      // publish the first and last computed rows, then take the neighbours'
+      uint32_t* mine = xch + ((size_t)pos * G + b) * 2u * wpr;
+      for (uint32_t c = threadIdx.x; c < wpr; c += blockDim.x) {
+        __stcg(mine + c, out[wpr + c]);
+        __stcg(mine + wpr + c, out[nr * wpr + c]);
+      }
+      if (!band_barrier(bs, gen, &s_flag)) return;
+      const uint32_t* above = xch + ((size_t)pos * G + (b + G - 1u) % G) * 2u * wpr + wpr;
+      const uint32_t* below = xch + ((size_t)pos * G + (b + 1u) % G) * 2u * wpr;
+      for (uint32_t c = threadIdx.x; c < wpr; c += blockDim.x) {
+        out[c] = __ldcg(above + c);
+        out[(nr + 1u) * wpr + c] = __ldcg(below + c);
+      }
+      __syncthreads();
+    }
+  }
+  for (uint32_t o = threadIdx.x; o < n_own; o += blockDim.x) {
+    resident_store<ENC>(J, J.A, w_first + o, buf[0][wpr + o]);
+    resident_store<ENC>(J, J.B, w_first + o, buf[1][wpr + o]);
+  }
+  (void)calls;
+}
+
 // --------------------------------------------------------------------------- launchers
 static int grid_for(int n_tiles, int per_sm) {
   int dev = 0, sms = 152;
@@ -1149,6 +1330,54 @@ cudaError_t launch_lattice_obs(int enc, int wpt, const LatJob* jobs, const Tile*
 }  // namespace shk
 
 namespace shk {
+// Grid and shared memory of the banded kernel for an L x L lattice of wpr words
+// per row: as many co-resident blocks as fit (at most L, one row each at least).
+// Returns false when the lattice does not fit that way.
+bool lattice_band_shape(int enc, uint32_t L, uint32_t wpr, int* grid, size_t* smem) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int max_smem = 0;
+  cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int G = sms * kLatMinBlocks;
+  for (int it = 0; it < 8; ++it) {
+    if (G > (int)L) G = (int)L;
+    const uint32_t rows = (L + (uint32_t)G - 1u) / (uint32_t)G + 2u;
+    const size_t bytes = (size_t)2 * rows * wpr * sizeof(uint32_t);
+    if (bytes > (size_t)max_smem - sizeof(LatTable) - 64) return false;
+    const void* k = enc == kEncInt8 ? (const void*)lattice_band_kernel<kEncInt8>
+                                    : (const void*)lattice_band_kernel<kEncPacked>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    int o = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, kTile, bytes);
+    cudaGetLastError();
+    if (o <= 0) return false;
+    if (o * sms >= G) {
+      *grid = G;
+      *smem = bytes;
+      return true;
+    }
+    G = o * sms;
+  }
+  return false;
+}
+
+// n steps of the one job in `jobs` by the banded kernel (cooperative launch; the
+// grid and shared memory from lattice_band_shape; bs zeroed by the caller).
+cudaError_t launch_lattice_band(int enc, const LatJob* jobs, int grid, size_t smem,
+                                uint32_t* xch, BandSync* bs, uint32_t t0, uint32_t n_steps,
+                                cudaStream_t st) {
+  if (n_steps == 0) return cudaSuccess;
+  void* args[] = {(void*)&jobs, (void*)&xch, (void*)&bs, (void*)&t0, (void*)&n_steps};
+  const void* k = enc == kEncInt8 ? (const void*)lattice_band_kernel<kEncInt8>
+                                  : (const void*)lattice_band_kernel<kEncPacked>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kTile), args, smem, st);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 // Run n steps of every job in `jobs` (one block each) inside one launch.
 cudaError_t launch_lattice_resident(int enc, const LatJob* jobs, int n_jobs, uint32_t nwords,
                                     uint32_t t0, uint32_t n_steps, cudaStream_t st) {

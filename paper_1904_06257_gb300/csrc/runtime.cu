@@ -48,6 +48,9 @@ cudaError_t launch_graph_fields(const GraphJob*, const Tile*, int, uint32_t, flo
 cudaError_t launch_epilogue(CtxDev* const*, int, cudaStream_t);
 cudaError_t launch_member_copy(int, const shk::MemberDev*, int, void*, unsigned long long,
                                cudaStream_t);
+bool lattice_band_shape(int, uint32_t, uint32_t, int*, size_t*);
+cudaError_t launch_lattice_band(int, const LatJob*, int, size_t, uint32_t*, BandSync*, uint32_t,
+                                uint32_t, cudaStream_t);
 cudaError_t launch_lattice_resident(int, const LatJob*, int, uint32_t, uint32_t, uint32_t,
                                     cudaStream_t);
 cudaError_t launch_philox(uint64_t, const uint32_t*, uint32_t*, int64_t, cudaStream_t);
@@ -227,6 +230,7 @@ struct shaken_ctx {
   DevMem step_sums, obs_sums, best, best_step;
   DevMem series_m, series_H;
   DevMem in_ptr, in_col, in_J, out_ptr, out_col, out_J, lam_dev;
+  DevMem band_xch, band_sync;  // banded runs: row exchange area and grid barrier
   CtxDev hcd{};
   uint64_t host_step = 0;
   bool tracking = false;
@@ -984,8 +988,50 @@ static shaken_status run_resident(shaken_ctx* c, uint64_t n_steps) {
   return push_cd(c);  // the device step counter follows the host's
 }
 
+// Mid-size single lattices (INT8/PACKED, one replica, beyond the resident size)
+// run whole chunks of steps in one cooperative launch that keeps the lattice in
+// shared memory as row bands.  Not for tracking, recording or annealing runs.
+static bool band_eligible(const shaken_ctx* c, uint64_t n_steps, int* grid, size_t* smem) {
+  if (c->kind != SHAKEN_LATTICE || c->owner || n_steps < 8 || c->R != 1) return false;
+  if (c->enc != SHAKEN_INT8 && c->enc != SHAKEN_PACKED) return false;
+  if (c->hcd.tracking || c->hcd.record || c->hcd.anneal_len != 0) return false;
+  if ((uint64_t)c->L * c->L / 32 <= 4096) return false;
+  const int enc = c->enc == SHAKEN_INT8 ? 0 : 1;
+  return shk::lattice_band_shape(enc, (uint32_t)c->L, (uint32_t)(c->L / 32), grid, smem);
+}
+
+static shaken_status run_band(shaken_ctx* c, uint64_t n_steps, int grid, size_t smem) {
+  cudaStream_t st = c->stream;
+  if (c->solo.dirty) TRY(build_plan(c->solo, st));
+  const Family& F = *c->solo.fams[0];
+  const uint32_t wpr = (uint32_t)(c->L / 32);
+  const size_t xbytes = (size_t)2 * grid * 2 * wpr * sizeof(uint32_t);
+  if (c->band_xch.p == nullptr || c->band_xch.bytes < xbytes) TRY(c->band_xch.alloc(xbytes));
+  if (c->band_sync.p == nullptr) TRY(c->band_sync.alloc(sizeof(shk::BandSync)));
+  uint64_t done = 0;
+  while (done < n_steps) {
+    const uint64_t chunk = std::min<uint64_t>(n_steps - done, 1u << 16);
+    CU(cudaMemsetAsync(c->band_sync.p, 0, sizeof(shk::BandSync), st));
+    CU(shk::launch_lattice_band(F.enc, F.jobs.as<LatJob>(), grid, smem,
+                                c->band_xch.as<uint32_t>(), c->band_sync.as<shk::BandSync>(),
+                                (uint32_t)(c->host_step + done), (uint32_t)chunk, st));
+    c->launches++;
+    shk::BandSync h{};
+    CU(cudaMemcpyAsync(&h, c->band_sync.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (h.err != 0u)
+      return fail(SHAKEN_E_TIMEOUT, "banded run: a grid barrier wait ran out; state undefined");
+    done += chunk;
+  }
+  c->host_step += n_steps;
+  return push_cd(c);  // the device step counter follows the host's
+}
+
 static shaken_status solo_run(shaken_ctx* ctx, uint64_t n_steps) {
   if (resident_eligible(ctx, n_steps)) return run_resident(ctx, n_steps);
+  int grid = 0;
+  size_t smem = 0;
+  if (band_eligible(ctx, n_steps, &grid, &smem)) return run_band(ctx, n_steps, grid, smem);
   uint64_t nl = 0;
   shaken_status s = plan_run(ctx->solo, ctx->stream, n_steps, n_steps >= 64, &nl);
   ctx->launches += nl;

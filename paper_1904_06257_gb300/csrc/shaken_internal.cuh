@@ -231,6 +231,16 @@ struct CtxDev {
   double* series_H;     // [cap][R] or null
 };
 
+// Grid barrier of the banded lattice kernel: arrival count, generation, and an
+// error flag set by a block whose wait ran out (the launch then stops early and
+// the host reports a timeout).
+struct BandSync {
+  unsigned int count;
+  unsigned int gen;
+  unsigned int err;
+  unsigned int pad;
+};
+
 // One member of a batch for the batched state and observables copies: its state
 // buffers and observables arrays and where they sit in the packed buffers.  The
 // packed observables of a member are [R][kNumSums] sums, then R best energies,

@@ -199,3 +199,44 @@ def test_tiled_and_resident_paths_agree_with_oracle(S, enc):
         t += n
         assert np.array_equal(S.shaken_get_spins(ctx, R, L * L).reshape(R, L, L), o), n
     S.shaken_free(ctx)
+
+
+@pytest.mark.parametrize("enc,L,frozen,order", [("INT8", 512, False, 0), ("PACKED", 512, True, 0),
+                                               ("PACKED", 416, False, 1), ("INT8", 800, True, 1)])
+def test_banded_path_agrees_with_oracle(S, enc, L, frozen, order):
+    """Single lattices above the resident size run chunks of >= 8 steps in one
+    cooperative launch holding the lattice in shared memory as row bands (halo rows
+    exchanged between blocks through a grid barrier); chunks of fewer steps use the
+    tiled kernels.  Both must follow the oracle: rows split unevenly (416, 800 are not
+    multiples of the block count), a frozen frame, the reversed order P^{sh'}."""
+    e = getattr(S, enc)
+    J, q, lam, beta, seed = 1.0, 0.9, 0.03, 0.42, 4242 + L
+    fz = W.frozen_frame(L) if frozen else None
+    ctx = S.shaken_init(lattice_problem(S, e, L, 1, beta, J, q, lam, fz), seed)
+    if order:
+        S.shaken_set_order(ctx, 1)
+    mode = mode_of(S, e)
+    o = core.lattice_init(L, 1, seed, mode, 0, fz)
+    sp = None
+    t = 0
+    for n in (9, 2, 8):  # banded, tiled, banded
+        l0 = S.shaken_launch_count(ctx)
+        S.shaken_step(ctx, n)
+        if n >= 8:
+            assert S.shaken_launch_count(ctx) - l0 == 1  # one banded launch
+        if order:
+            # reversed order: half ur then dl, draws keyed by update type
+            for k in range(n):
+                o1 = core.lattice_half(o, J, q, lam, beta, seed, t + k, 1, mode, fz)
+                o = core.lattice_half(o1, J, q, lam, beta, seed, t + k, 0, mode, fz)
+                sp = o1
+        else:
+            o, sp = core.lattice_run(o, J, q, lam, beta, seed, t, n, mode, fz)
+        t += n
+        got = S.shaken_get_spins(ctx, 1, L * L).reshape(1, L, L)
+        assert np.array_equal(got, o), (n, int((got != o).sum()))
+    obs = S.shaken_observables(ctx, 1)
+    ref = core.lattice_observables(o, sp, J, q, lam)[0]
+    assert abs(obs["magnetization"][0] - ref["m"]) < 1e-12
+    assert abs(obs["pair_energy"][0] - ref["pair"]) < 1e-9
+    S.shaken_free(ctx)
