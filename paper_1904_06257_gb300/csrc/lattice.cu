@@ -1062,10 +1062,11 @@ __global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* _
 // half-step parity, so a row is not overwritten while a neighbour may still read
 // it), passes a grid barrier and copies its neighbours' rows into its halo rows.
 // The draws, thresholds and decisions are those of lattice_half_kernel (head of
-// four words per thread, eight planes; words still undecided finish one by one),
-// so the trajectory is the same.
+// four words per thread, eight planes, a per-warp queue for the words still
+// undecided), so the trajectory is the same.
 
 constexpr uint32_t kBandSpinLimit = 1u << 21;  // barrier polls (about a second)
+constexpr int kBandMinBlocks = 2;  // blocks per SM: 126 registers, no spills (3: spills, slower)
 
 // Grid barrier of a cooperative launch.  Every thread fences its global writes
 // (the published rows) first.  A block whose wait runs out, or that sees another
@@ -1113,62 +1114,125 @@ __device__ __forceinline__ void band_words(const uint32_t* buf, uint32_t l, uint
   }
 }
 
-// One pass over W x kTile own words of the band starting at own word o0.
+// One round of a warp's queue of band words still undecided after eight planes
+// (entries (global word, undecided lanes, results, next call), as in the tiled
+// kernel): the top min(qn, 32) entries each make their next call; finished words
+// are written to out, the others go back on the queue.
+template <bool COLL>
+__device__ __forceinline__ void band_round(const LatTable& tab, const uint32_t* in, uint32_t* out,
+                                           Pending* __restrict__ q, uint32_t& qn,
+                                           uint32_t w_first, uint32_t wpr, bool pow2,
+                                           uint32_t typ, const PhKey& K, const PhShared& P,
+                                           uint32_t& calls) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const uint32_t n = qn < 32u ? qn : 32u;
+  const uint32_t base = qn - n;
+  const bool act = (uint32_t)lane < n;
+  Pending e = make_uint4(0u, 0u, 0u, 0u);
+  if (act) e = q[base + lane];
+  __syncwarp();
+  bool still = false;
+  if (act) {
+    const uint4 w = ph_call_shared(K, P, e.x, typ + 2u * e.w);
+    const uint32_t o = e.x - w_first;
+    const uint32_t loc = wpr + o, c = pow2 ? (o & (wpr - 1u)) : o % wpr;
+    uint32_t S, V, H;
+    band_words(in, loc, c, wpr, typ, S, V, H);
+    LaneWord L;
+    L.S = S;
+    L.V = COLL ? ((V & H) | (S & (V | H))) : V;
+    L.X = COLL ? (V ^ H ^ S) : (V ^ H);
+    L.U = e.y;
+    L.res = e.z;
+    ++calls;
+    apply_call<COLL>(L, w, tab, e.w);
+    if (L.U == 0u || e.w == 7u) {
+      out[loc] = L.res;
+    } else {
+      still = true;
+      e.y = L.U;
+      e.z = L.res;
+      e.w += 1u;
+    }
+  }
+  const uint32_t sm = __ballot_sync(0xffffffffu, still);
+  if (still) q[base + __popc(sm & lt_mask)] = e;
+  qn = base + (uint32_t)__popc(sm);
+  __syncwarp();
+}
+
+// One pass over W x kTile own words of the band starting at own word o0: planes
+// 31..24 of every word; words with undecided lanes go to the warp's queue, which
+// runs a round whenever it holds 32 of them.
 template <bool COLL, bool MIR, int W>
 __device__ __forceinline__ void band_pass(const LatJob& J, const LatTable& tab,
                                           const uint32_t* in, uint32_t* out, uint32_t o0,
                                           uint32_t n_own, uint32_t w_first, uint32_t wpr,
-                                          uint32_t typ, const PhKey& K, const PhShared& P,
-                                          uint32_t& calls) {
+                                          bool pow2, uint32_t typ, const PhKey& K,
+                                          const PhShared& P, Pending* __restrict__ q,
+                                          uint32_t& qn, uint32_t& calls) {
   LaneWord Lw[W];
-  uint32_t a[W], loc[W];
+  uint32_t a[W];
   bool act[W];
 #pragma unroll
   for (int k = 0; k < W; ++k) {
     const uint32_t o = o0 + threadIdx.x + (uint32_t)k * kTile;
     act[k] = o < n_own;
     const uint32_t oo = act[k] ? o : 0u;
-    const uint32_t c = J.wpr_shift != 0xffffffffu ? (oo & (wpr - 1u)) : oo % wpr;
-    loc[k] = wpr + oo;    // own rows start at local row 1
+    const uint32_t c = pow2 ? (oo & (wpr - 1u)) : oo % wpr;
     a[k] = w_first + oo;  // global lane word: the Philox counter and the frozen mask
     uint32_t S, V, H;
-    band_words(in, loc[k], c, wpr, typ, S, V, H);
+    band_words(in, wpr + oo, c, wpr, typ, S, V, H);  // own rows start at local row 1
     const uint32_t F = (J.frozen != nullptr && act[k]) ? J.frozen[a[k]] : 0u;
     Lw[k] = classify<COLL>(S, V, H, F, tab);
     if (!act[k]) Lw[k].U = 0u;
   }
   decide_head_words<COLL, W, MIR>(Lw, tab, K, P, a, typ);
   calls += 2u * W;
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
   for (int k = 0; k < W; ++k) {
-    if (!act[k]) continue;
-    if (Lw[k].U != 0u) decide_tail<COLL>(Lw[k], tab, K, P, a[k], typ, 2u, calls);
-    out[loc[k]] = Lw[k].res;
+    const bool pend = act[k] && Lw[k].U != 0u;
+    const uint32_t pm = __ballot_sync(0xffffffffu, pend);
+    if (pend)
+      q[qn + __popc(pm & lt_mask)] = make_uint4(a[k], Lw[k].U, Lw[k].res, 2u);
+    else if (act[k])
+      out[a[k] - w_first + wpr] = Lw[k].res;
+    qn += __popc(pm);
   }
+  __syncwarp();
+  while (qn >= 32u) band_round<COLL>(tab, in, out, q, qn, w_first, wpr, pow2, typ, K, P, calls);
 }
 
 template <bool COLL, bool MIR>
 __device__ __forceinline__ void band_half(const LatJob& J, const LatTable& tab,
                                           const uint32_t* in, uint32_t* out, uint32_t n_own,
                                           uint32_t w_first, uint32_t wpr, uint32_t typ,
-                                          const PhKey& K, const PhShared& P, uint32_t& calls) {
-  uint32_t o0 = 0;
+                                          const PhKey& K, const PhShared& P,
+                                          Pending* __restrict__ q, uint32_t& calls) {
+  const bool pow2 = J.wpr_shift != 0xffffffffu;
+  uint32_t qn = 0, o0 = 0;
   for (; o0 + (uint32_t)kLatTile <= n_own; o0 += kLatTile)
-    band_pass<COLL, MIR, kWordsPerThread>(J, tab, in, out, o0, n_own, w_first, wpr, typ, K, P,
-                                          calls);
+    band_pass<COLL, MIR, kWordsPerThread>(J, tab, in, out, o0, n_own, w_first, wpr, pow2, typ, K,
+                                          P, q, qn, calls);
   for (; o0 < n_own; o0 += kTile)
-    band_pass<COLL, MIR, 1>(J, tab, in, out, o0, n_own, w_first, wpr, typ, K, P, calls);
+    band_pass<COLL, MIR, 1>(J, tab, in, out, o0, n_own, w_first, wpr, pow2, typ, K, P, q, qn,
+                            calls);
+  while (qn != 0u) band_round<COLL>(tab, in, out, q, qn, w_first, wpr, pow2, typ, K, P, calls);
 }
 
 // xch: exchange area, [2 parities][G blocks][first row, last row][wpr words].
 template <int ENC>
-__global__ void __launch_bounds__(kTile, kLatMinBlocks) lattice_band_kernel(
+__global__ void __launch_bounds__(kTile, kBandMinBlocks) lattice_band_kernel(
     const LatJob* __restrict__ jobs, uint32_t* __restrict__ xch, BandSync* __restrict__ bs,
     uint32_t t0, uint32_t n_steps) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ LatTable stab;
   __shared__ LatJob sJ;  // the job descriptor, read from shared memory
   __shared__ uint32_t s_flag;
+  __shared__ Pending queue[kTile / 32][32 * kWordsPerThread + 32];
   if (threadIdx.x < sizeof(LatJob) / 4)
     reinterpret_cast<uint32_t*>(&sJ)[threadIdx.x] =
         reinterpret_cast<const uint32_t*>(jobs)[threadIdx.x];
@@ -1195,6 +1259,7 @@ __global__ void __launch_bounds__(kTile, kLatMinBlocks) lattice_band_kernel(
   }
   const PhKey K = ph_key(J.key0, J.key1);
   const uint32_t w_first = r0 * wpr;
+  Pending* q = queue[threadIdx.x >> 5];
   uint32_t calls = 0;
   __syncthreads();
   for (uint32_t st = 0; st < n_steps; ++st) {
@@ -1204,11 +1269,11 @@ __global__ void __launch_bounds__(kTile, kLatMinBlocks) lattice_band_kernel(
       const uint32_t* in = buf[pos];
       uint32_t* out = buf[pos ^ 1u];
       if (stab.mirror)
-        band_half<true, true>(J, stab, in, out, n_own, w_first, wpr, typ, K, P, calls);
+        band_half<true, true>(J, stab, in, out, n_own, w_first, wpr, typ, K, P, q, calls);
       else if (stab.collapsed)
-        band_half<true, false>(J, stab, in, out, n_own, w_first, wpr, typ, K, P, calls);
+        band_half<true, false>(J, stab, in, out, n_own, w_first, wpr, typ, K, P, q, calls);
       else
-        band_half<false, false>(J, stab, in, out, n_own, w_first, wpr, typ, K, P, calls);
+        band_half<false, false>(J, stab, in, out, n_own, w_first, wpr, typ, K, P, q, calls);
       __syncthreads();
       // publish the first and last computed rows, then take the neighbours'
       uint32_t* mine = xch + ((size_t)pos * G + b) * 2u * wpr;
@@ -1339,7 +1404,7 @@ bool lattice_band_shape(int enc, uint32_t L, uint32_t wpr, int* grid, size_t* sm
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int max_smem = 0;
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  int G = sms * kLatMinBlocks;
+  int G = sms * kBandMinBlocks;
   for (int it = 0; it < 8; ++it) {
     if (G > (int)L) G = (int)L;
     const uint32_t rows = (L + (uint32_t)G - 1u) / (uint32_t)G + 2u;
