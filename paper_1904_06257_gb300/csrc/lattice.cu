@@ -1068,32 +1068,38 @@ __global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* _
 constexpr uint32_t kBandSpinLimit = 1u << 21;  // barrier polls (about a second)
 constexpr int kBandMinBlocks = 2;  // blocks per SM: 126 registers, no spills (3: spills, slower)
 
-// Grid barrier of a cooperative launch.  Every thread fences its global writes
-// (the published rows) first.  A block whose wait runs out, or that sees another
-// block's error, sets the error flag; returns false once the flag is set.
-__device__ __forceinline__ bool band_barrier(BandSync* bs, uint32_t& gen, uint32_t* s_flag) {
+// Grid barrier of a cooperative launch in two phases, so a block can compute
+// between announcing its rows and needing its neighbours'.  band_arrive: every
+// thread fences its global writes (the published rows), then thread 0 counts the
+// block in; the last block resets the count and advances the generation.
+// band_wait: thread 0 polls the generation; a wait that runs out, or that sees
+// another block's error, sets the error flag.  Returns false once the flag is set.
+__device__ __forceinline__ void band_arrive(BandSync* bs, uint32_t gen) {
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
-    const uint32_t g = gen;
     if (atomicAdd(&bs->count, 1u) == gridDim.x - 1u) {
       atomicExch(&bs->count, 0u);
       __threadfence();
-      atomicExch(&bs->gen, g + 1u);
-    } else {
-      uint32_t spins = 0;
-      while (atomicAdd(&bs->gen, 0u) == g) {
-        if (++spins > kBandSpinLimit || atomicAdd(&bs->err, 0u) != 0u) {
-          atomicExch(&bs->err, 1u);
-          break;
-        }
-        __nanosleep(64);
+      atomicExch(&bs->gen, gen + 1u);
+    }
+  }
+}
+
+__device__ __forceinline__ bool band_wait(BandSync* bs, uint32_t& gen, uint32_t* s_flag) {
+  if (threadIdx.x == 0) {
+    uint32_t spins = 0;
+    while (atomicAdd(&bs->gen, 0u) == gen) {
+      if (++spins > kBandSpinLimit || atomicAdd(&bs->err, 0u) != 0u) {
+        atomicExch(&bs->err, 1u);
+        break;
       }
+      __nanosleep(32);
     }
     __threadfence();
-    gen = g + 1u;
     *s_flag = atomicAdd(&bs->err, 0u);
   }
+  gen += 1u;
   __syncthreads();
   return *s_flag == 0u;
 }
@@ -1165,10 +1171,17 @@ __device__ __forceinline__ void band_round(const LatTable& tab, const uint32_t* 
 // One pass over W x kTile own words of the band starting at own word o0: planes
 // 31..24 of every word; words with undecided lanes go to the warp's queue, which
 // runs a round whenever it holds 32 of them.
+// Own words are addressed through an index: word idx of a range is own word
+// idx + (idx < split ? off_lo : off_hi), so the first and the last own row can be
+// one range of 2 wpr indices.
+struct BandRange {
+  uint32_t n, split, off_lo, off_hi;
+};
+
 template <bool COLL, bool MIR, int W>
 __device__ __forceinline__ void band_pass(const LatJob& J, const LatTable& tab,
-                                          const uint32_t* in, uint32_t* out, uint32_t o0,
-                                          uint32_t n_own, uint32_t w_first, uint32_t wpr,
+                                          const uint32_t* in, uint32_t* out, uint32_t i0,
+                                          const BandRange& R, uint32_t w_first, uint32_t wpr,
                                           bool pow2, uint32_t typ, const PhKey& K,
                                           const PhShared& P, Pending* __restrict__ q,
                                           uint32_t& qn, uint32_t& calls) {
@@ -1177,9 +1190,9 @@ __device__ __forceinline__ void band_pass(const LatJob& J, const LatTable& tab,
   bool act[W];
 #pragma unroll
   for (int k = 0; k < W; ++k) {
-    const uint32_t o = o0 + threadIdx.x + (uint32_t)k * kTile;
-    act[k] = o < n_own;
-    const uint32_t oo = act[k] ? o : 0u;
+    const uint32_t idx = i0 + threadIdx.x + (uint32_t)k * kTile;
+    act[k] = idx < R.n;
+    const uint32_t oo = act[k] ? idx + (idx < R.split ? R.off_lo : R.off_hi) : 0u;
     const uint32_t c = pow2 ? (oo & (wpr - 1u)) : oo % wpr;
     a[k] = w_first + oo;  // global lane word: the Philox counter and the frozen mask
     uint32_t S, V, H;
@@ -1206,21 +1219,36 @@ __device__ __forceinline__ void band_pass(const LatJob& J, const LatTable& tab,
   while (qn >= 32u) band_round<COLL>(tab, in, out, q, qn, w_first, wpr, pow2, typ, K, P, calls);
 }
 
+// Every word of a range of own words decided (the queue drained at the end).
 template <bool COLL, bool MIR>
-__device__ __forceinline__ void band_half(const LatJob& J, const LatTable& tab,
-                                          const uint32_t* in, uint32_t* out, uint32_t n_own,
-                                          uint32_t w_first, uint32_t wpr, uint32_t typ,
-                                          const PhKey& K, const PhShared& P,
-                                          Pending* __restrict__ q, uint32_t& calls) {
+__device__ __forceinline__ void band_range(const LatJob& J, const LatTable& tab,
+                                           const uint32_t* in, uint32_t* out, const BandRange& R,
+                                           uint32_t w_first, uint32_t wpr, uint32_t typ,
+                                           const PhKey& K, const PhShared& P,
+                                           Pending* __restrict__ q, uint32_t& calls) {
   const bool pow2 = J.wpr_shift != 0xffffffffu;
-  uint32_t qn = 0, o0 = 0;
-  for (; o0 + (uint32_t)kLatTile <= n_own; o0 += kLatTile)
-    band_pass<COLL, MIR, kWordsPerThread>(J, tab, in, out, o0, n_own, w_first, wpr, pow2, typ, K,
-                                          P, q, qn, calls);
-  for (; o0 < n_own; o0 += kTile)
-    band_pass<COLL, MIR, 1>(J, tab, in, out, o0, n_own, w_first, wpr, pow2, typ, K, P, q, qn,
-                            calls);
+  uint32_t qn = 0, i0 = 0;
+  for (; i0 + (uint32_t)kLatTile <= R.n; i0 += kLatTile)
+    band_pass<COLL, MIR, kWordsPerThread>(J, tab, in, out, i0, R, w_first, wpr, pow2, typ, K, P,
+                                          q, qn, calls);
+  for (; i0 < R.n; i0 += kTile)
+    band_pass<COLL, MIR, 1>(J, tab, in, out, i0, R, w_first, wpr, pow2, typ, K, P, q, qn, calls);
   while (qn != 0u) band_round<COLL>(tab, in, out, q, qn, w_first, wpr, pow2, typ, K, P, calls);
+}
+
+// band_range with the table's decision form.
+__device__ __forceinline__ void band_decide(const LatJob& J, const LatTable& tab,
+                                            const uint32_t* in, uint32_t* out,
+                                            const BandRange& R, uint32_t w_first, uint32_t wpr,
+                                            uint32_t typ, const PhKey& K, const PhShared& P,
+                                            Pending* __restrict__ q, uint32_t& calls) {
+  if (R.n == 0u) return;
+  if (tab.mirror)
+    band_range<true, true>(J, tab, in, out, R, w_first, wpr, typ, K, P, q, calls);
+  else if (tab.collapsed)
+    band_range<true, false>(J, tab, in, out, R, w_first, wpr, typ, K, P, q, calls);
+  else
+    band_range<false, false>(J, tab, in, out, R, w_first, wpr, typ, K, P, q, calls);
 }
 
 // xch: exchange area, [2 parities][G blocks][first row, last row][wpr words].
@@ -1268,20 +1296,21 @@ __global__ void __launch_bounds__(kTile, kBandMinBlocks) lattice_band_kernel(
       const uint32_t typ = pos ^ order;  // update type of this position
       const uint32_t* in = buf[pos];
       uint32_t* out = buf[pos ^ 1u];
-      if (stab.mirror)
-        band_half<true, true>(J, stab, in, out, n_own, w_first, wpr, typ, K, P, q, calls);
-      else if (stab.collapsed)
-        band_half<true, false>(J, stab, in, out, n_own, w_first, wpr, typ, K, P, q, calls);
-      else
-        band_half<false, false>(J, stab, in, out, n_own, w_first, wpr, typ, K, P, q, calls);
+      // the first and last own rows (what the neighbours need) first, then publish
+      // them and announce; the interior rows overlap the other blocks' arrival
+      const BandRange Rb = nr == 1u ? BandRange{wpr, wpr, 0u, 0u}
+                                    : BandRange{2u * wpr, wpr, 0u, (nr - 2u) * wpr};
+      const BandRange Ri = {nr >= 3u ? (nr - 2u) * wpr : 0u, 0xffffffffu, wpr, 0u};
+      band_decide(J, stab, in, out, Rb, w_first, wpr, typ, K, P, q, calls);
       __syncthreads();
-      // publish the first and last computed rows, then take the neighbours'
       uint32_t* mine = xch + ((size_t)pos * G + b) * 2u * wpr;
       for (uint32_t c = threadIdx.x; c < wpr; c += blockDim.x) {
         __stcg(mine + c, out[wpr + c]);
         __stcg(mine + wpr + c, out[nr * wpr + c]);
       }
-      if (!band_barrier(bs, gen, &s_flag)) return;
+      band_arrive(bs, gen);
+      band_decide(J, stab, in, out, Ri, w_first, wpr, typ, K, P, q, calls);
+      if (!band_wait(bs, gen, &s_flag)) return;
       const uint32_t* above = xch + ((size_t)pos * G + (b + G - 1u) % G) * 2u * wpr + wpr;
       const uint32_t* below = xch + ((size_t)pos * G + (b + 1u) % G) * 2u * wpr;
       for (uint32_t c = threadIdx.x; c < wpr; c += blockDim.x) {
