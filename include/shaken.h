@@ -205,6 +205,16 @@ shaken_status shaken_debug_fields(shaken_ctx* ctx, int half, float* out);
  * slower); used to test the fast path's error margin. */
 shaken_status shaken_debug_exact_always(shaken_ctx* ctx, int on);
 
+/* Diagnostics for the failure path of banded runs (one mid-size INT8/PACKED
+ * lattice, chunks of >= 8 steps without tracking, held in shared memory by a
+ * cooperative grid with a grid barrier per half step): the next banded chunk
+ * starts with its barrier's arrival count preset so that no block is ever the
+ * last to arrive.  Every block's wait then runs out after its bounded spin
+ * (about a second), the blocks return without writing the chunk back, and the
+ * stepping call returns SHAKEN_E_TIMEOUT with sigma, sigma' and the step counter
+ * as before the chunk; the context stays usable. */
+shaken_status shaken_debug_band_stall(shaken_ctx* ctx);
+
 /* Number of kernel launches this context has issued (all kinds). */
 shaken_status shaken_launch_count(shaken_ctx* ctx, uint64_t* count);
 

@@ -1065,7 +1065,7 @@ __global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* _
 // four words per thread, eight planes, a per-warp queue for the words still
 // undecided), so the trajectory is the same.
 
-constexpr uint32_t kBandSpinLimit = 1u << 21;  // barrier polls (about a second)
+constexpr uint32_t kBandSpinLimit = 1u << 19;  // barrier polls: about a second (two L2 atomics each)
 constexpr int kBandMinBlocks = 2;  // blocks per SM: 126 registers, no spills (3: spills, slower)
 
 // Grid barrier of a cooperative launch in two phases, so a block can compute

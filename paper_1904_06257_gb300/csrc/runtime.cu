@@ -231,6 +231,7 @@ struct shaken_ctx {
   DevMem series_m, series_H;
   DevMem in_ptr, in_col, in_J, out_ptr, out_col, out_J, lam_dev;
   DevMem band_xch, band_sync;  // banded runs: row exchange area and grid barrier
+  bool band_stall = false;     // diagnostics: the next banded run's barrier never completes
   CtxDev hcd{};
   uint64_t host_step = 0;
   bool tracking = false;
@@ -1011,19 +1012,27 @@ static shaken_status run_band(shaken_ctx* c, uint64_t n_steps, int grid, size_t 
   uint64_t done = 0;
   while (done < n_steps) {
     const uint64_t chunk = std::min<uint64_t>(n_steps - done, 1u << 16);
-    CU(cudaMemsetAsync(c->band_sync.p, 0, sizeof(shk::BandSync), st));
+    shk::BandSync h0{};
+    if (c->band_stall) h0.count = (unsigned)grid;  // no block is ever the last to arrive
+    c->band_stall = false;
+    CU(cudaMemcpyAsync(c->band_sync.p, &h0, sizeof(h0), cudaMemcpyHostToDevice, st));
     CU(shk::launch_lattice_band(F.enc, F.jobs.as<LatJob>(), grid, smem,
                                 c->band_xch.as<uint32_t>(), c->band_sync.as<shk::BandSync>(),
-                                (uint32_t)(c->host_step + done), (uint32_t)chunk, st));
+                                (uint32_t)c->host_step, (uint32_t)chunk, st));
     c->launches++;
     shk::BandSync h{};
     CU(cudaMemcpyAsync(&h, c->band_sync.p, sizeof(h), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
-    if (h.err != 0u)
-      return fail(SHAKEN_E_TIMEOUT, "banded run: a grid barrier wait ran out; state undefined");
+    if (h.err != 0u) {
+      // the blocks returned before writing the chunk back: the state is the one
+      // before the chunk, and the step counter says so
+      TRY(push_cd(c));
+      return fail(SHAKEN_E_TIMEOUT,
+                  "banded run: a grid barrier wait ran out; the chunk was not applied");
+    }
+    c->host_step += chunk;
     done += chunk;
   }
-  c->host_step += n_steps;
   return push_cd(c);  // the device step counter follows the host's
 }
 
@@ -1518,6 +1527,12 @@ shaken_status shaken_sync(shaken_ctx* ctx) {
 shaken_status shaken_debug_exact_always(shaken_ctx* ctx, int on) {
   if (!ctx) return fail(SHAKEN_E_INVAL, "ctx is NULL");
   ctx->exact_always = on ? 1 : 0;
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_debug_band_stall(shaken_ctx* ctx) {
+  if (!ctx) return fail(SHAKEN_E_INVAL, "ctx is NULL");
+  ctx->band_stall = true;
   return SHAKEN_OK;
 }
 

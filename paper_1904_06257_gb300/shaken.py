@@ -80,6 +80,7 @@ def _load():
         "shaken_load": [vp, vp, sz],
         "shaken_debug_fields": [vp, ctypes.c_int, vp],
         "shaken_debug_exact_always": [vp, ctypes.c_int],
+        "shaken_debug_band_stall": [vp],
         "shaken_launch_count": [vp, ctypes.POINTER(u64)],
         "shaken_sync": [vp],
         "shaken_batch_create": [ctypes.POINTER(vp), vp],
@@ -274,6 +275,11 @@ def shaken_debug_fields(ctx, half: int, replicas: int, sites: int):
 
 def shaken_debug_exact_always(ctx, on: bool):
     _check(_lib.shaken_debug_exact_always(ctx, int(bool(on))))
+
+
+def shaken_debug_band_stall(ctx):
+    """The next banded chunk's grid barrier never completes (timeout-path test)."""
+    _check(_lib.shaken_debug_band_stall(ctx))
 
 
 def shaken_launch_count(ctx) -> int:

@@ -240,3 +240,24 @@ def test_banded_path_agrees_with_oracle(S, enc, L, frozen, order):
     assert abs(obs["magnetization"][0] - ref["m"]) < 1e-12
     assert abs(obs["pair_energy"][0] - ref["pair"]) < 1e-9
     S.shaken_free(ctx)
+
+
+def test_banded_barrier_timeout_leaves_state(S):
+    """Failure path of a banded run without a GPU fault: the diagnostic presets the
+    grid barrier so that it never completes; every block's bounded wait runs out
+    (about a second), the call returns E_TIMEOUT, sigma and the step counter are
+    those before the call, and the context keeps stepping exactly as the oracle."""
+    L, J, q, lam, beta, seed = 512, 1.0, 1.0, 0.0, 0.44, 606
+    ctx = S.shaken_init(lattice_problem(S, S.PACKED, L, 1, beta, J, q, lam), seed)
+    s0 = S.shaken_get_spins(ctx, 1, L * L)
+    S.shaken_debug_band_stall(ctx)
+    with pytest.raises(S.ShakenError) as err:
+        S.shaken_step(ctx, 8)
+    assert err.value.status == -4  # SHAKEN_E_TIMEOUT
+    assert np.array_equal(S.shaken_get_spins(ctx, 1, L * L), s0)
+    assert S.shaken_get_step(ctx) == 0
+    S.shaken_step(ctx, 8)
+    o = core.lattice_init(L, 1, seed, core.MODE_SINGLE, 0)
+    o, _ = core.lattice_run(o, J, q, lam, beta, seed, 0, 8, core.MODE_SINGLE)
+    assert np.array_equal(S.shaken_get_spins(ctx, 1, L * L).reshape(1, L, L), o)
+    S.shaken_free(ctx)
