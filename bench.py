@@ -204,10 +204,12 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
-    if args.only_graphs or args.only_serving or args.only_small:
+    if args.only_graphs or args.only_serving or args.only_small or args.only_plain:
         if rank == 0:
             if args.only_small:
                 part = run_small(S, stream)
+            elif args.only_plain:
+                part = run_plain(S, stream, torch)
             elif args.only_graphs:
                 part = run_graphs(S, stream, torch, args)
             else:
@@ -341,22 +343,7 @@ def run_ours(args, rank, world, local_rank):
                    "flush"}
 
     # ---- plain single-lattice kernel: L = 4096, one replica, int8 and bit-packed
-    Lp = 4096
-    plain = {}
-    for name, enc in (("int8", S.INT8), ("packed", S.PACKED)):
-        pp = S.Problem(S.LATTICE, enc, 1, 0.4407, Q, L=Lp, J=J, lambda_const=LAM)
-        cp = S.shaken_init(pp, W.BASE_SEED + 7, stream)
-        S.shaken_step(cp, 128)  # warm-up; also captures the step graph timed below
-        S.shaken_sync(cp)
-        pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
-            pe0.record(stream)
-        S.shaken_step(cp, 128)
-        with torch.cuda.stream(stream):
-            pe1.record(stream)
-        stream.synchronize()
-        plain[name] = 2.0 * Lp * Lp * 128 / (pe0.elapsed_time(pe1) * 1e-3)
-        S.shaken_free(cp)
+    plain = run_plain(S, stream, torch)
     plain_rate = plain["int8"]
 
     # ---- small lattice: L = 64 int8, one replica, beta = 0.40, 10^4 steps with m and H per step
@@ -507,6 +494,30 @@ def committed_traffic(kernel: str):
     if not rec or rec.get("source_hash") != kernel_source_hash():
         return None
     return rec.get("bytes_per_launch")
+
+
+# ------------------------------------------------------------------------ plain lattice
+def run_plain(S, stream, torch, L=4096, steps=512):
+    """The plain single-lattice kernel: one L = 4096 replica (beta = 0.4407, q = J = 1,
+    lambda = 0), int8 and bit-packed, `steps` full steps timed with CUDA events after
+    a warm-up call of the same length (the banded kernel: one cooperative launch per
+    call)."""
+    plain = {}
+    for name, enc in (("int8", S.INT8), ("packed", S.PACKED)):
+        pp = S.Problem(S.LATTICE, enc, 1, 0.4407, Q, L=L, J=J, lambda_const=LAM)
+        cp = S.shaken_init(pp, W.BASE_SEED + 7, stream)
+        S.shaken_step(cp, steps)  # warm-up
+        S.shaken_sync(cp)
+        pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            pe0.record(stream)
+        S.shaken_step(cp, steps)
+        with torch.cuda.stream(stream):
+            pe1.record(stream)
+        stream.synchronize()
+        plain[name] = 2.0 * L * L * steps / (pe0.elapsed_time(pe1) * 1e-3)
+        S.shaken_free(cp)
+    return plain
 
 
 # ------------------------------------------------------------------------ small lattice
@@ -816,6 +827,8 @@ def main():
     ap.add_argument("--only-serving", action="store_true", help="run the serving section only")
     ap.add_argument("--only-small", action="store_true",
                     help="run the small-lattice section only (profiling runs)")
+    ap.add_argument("--only-plain", action="store_true",
+                    help="run the plain single-lattice section only (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="fixed lattice launch-shape rule instead of timed trials (profiling)")
     ap.add_argument("--graph-anneal-steps", type=int, default=5000)
