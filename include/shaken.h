@@ -133,7 +133,14 @@ void shaken_free(shaken_ctx* ctx);
  * buffer: tau_x = +1 with probability e^{beta h_x} / (2 cosh(beta h_x)), decided
  * exactly as u < floor(2^32 / (1 + e^{-2 beta h})) with u the replica's 32-bit
  * Philox draw for (seed, replica, step, half, site).  Asynchronous on the
- * context's stream.  E_STATE if the context is owned by a batch. */
+ * context's stream, except whole-run paths that synchronise at the end of the
+ * call: small lattices (<= 4096 lane words per replica, n >= 4) run in one
+ * launch per 65536 steps with the state in shared memory; one mid-size
+ * INT8/PACKED lattice (one replica, n >= 8, no tracking or anneal) runs in one
+ * cooperative launch per 65536 steps holding row bands in shared memory, and
+ * returns E_TIMEOUT if a grid-barrier wait ran out (the chunk is then not
+ * applied: sigma, sigma' and the step counter stay as before it).  Every path
+ * gives the same trajectory.  E_STATE if the context is owned by a batch. */
 shaken_status shaken_step(shaken_ctx* ctx, uint64_t n_steps);
 
 /* Annealing (the optimisation use of Sec. 6 / Thm 6.1): n_steps full steps,
