@@ -261,3 +261,22 @@ def test_banded_barrier_timeout_leaves_state(S):
     o, _ = core.lattice_run(o, J, q, lam, beta, seed, 0, 8, core.MODE_SINGLE)
     assert np.array_equal(S.shaken_get_spins(ctx, 1, L * L).reshape(1, L, L), o)
     S.shaken_free(ctx)
+
+
+@pytest.mark.parametrize("enc,L", [("INT8", 4096), ("PACKED", 8192)])
+def test_banded_path_equals_tiled_path_at_full_size(S, enc, L):
+    """At the plain-lattice size (4096^2, the bench's configuration) and at 8192^2
+    (one band block per SM), 8 steps in one banded launch equal 8 single steps of the
+    per-half-step tiled kernels, which the oracle pins at smaller sizes."""
+    e = getattr(S, enc)
+    J, q, lam, beta, seed = 1.0, 1.0, 0.0, 0.4407, 0x5348414B + L
+    a = S.shaken_init(lattice_problem(S, e, L, 1, beta, J, q, lam), seed)
+    b = S.shaken_init(lattice_problem(S, e, L, 1, beta, J, q, lam), seed)
+    l0 = S.shaken_launch_count(a)
+    S.shaken_step(a, 8)
+    assert S.shaken_launch_count(a) - l0 == 1  # the banded path ran
+    for _ in range(8):
+        S.shaken_step(b, 1)
+    assert np.array_equal(S.shaken_get_spins(a, 1, L * L), S.shaken_get_spins(b, 1, L * L))
+    S.shaken_free(a)
+    S.shaken_free(b)
