@@ -5,7 +5,9 @@
   J^o = J/2 is the symmetric PCA), fed as an oriented edge list: the GPU chain's
   law against the exact transition matrix (chi-square);
 * the triangular lattice of Sec. 4 (three right / three left neighbours) through
-  the graph path, bit-exact against the oracle."""
+  the graph path, bit-exact against the oracle; at q = J its pair (sigma, sigma')
+  is the square-lattice Ising model (Thm 4.1 and the figure of Sec. 4), so the pair
+  energy per site and |m| follow Onsager on both sides of beta_c = 0.4407."""
 import numpy as np
 import pytest
 from scipy import stats
@@ -116,3 +118,35 @@ def test_triangular_lattice_bit_exact(S):
     o, _ = core.graph_run(o, tail, head, J.astype(np.float64), True, 0.0, 0.6,
                           W.beta_grid(R, 0.1, 0.6, 16), seed, 0, 5)
     assert np.array_equal(got, o)
+
+
+@pytest.mark.parametrize("beta", [0.35, 0.48])
+def test_triangular_at_q_equal_J_follows_onsager(S, beta):
+    """Triangular lattice, J = q = 1, lambda = 0: the pair Hamiltonian lives on a
+    square lattice of 2 L^2 sites, so the stationary pair energy per site is Onsager's
+    u(beta) and, in the ordered phase (beta = 0.48 > 0.4407), E|m| is the spontaneous
+    magnetisation (1 - sinh^-4(2 beta))^(1/8) = 0.8775.  64 replicas of a 96 x 96
+    torus; finite-size corrections are exponentially small this far from beta_c."""
+    L, R = 96, 64
+    u, v = W.triangular_lattice_as_graph(L)
+    J = np.ones(u.size, dtype=np.float32)
+    ctx = S.shaken_init(graph_problem(S, L * L, u, v, J, R, beta, q=1.0, lam_c=0.0,
+                                      orientation=S.ORIENT_GIVEN, init=1), 77)
+    S.shaken_step(ctx, 300)
+    e, m = [], []
+    for _ in range(40):
+        S.shaken_step(ctx, 10)
+        o = S.shaken_observables(ctx, R)
+        e.append(o["pair_energy"] / (2 * L * L))
+        m.append(np.abs(o["magnetization"]))
+    S.shaken_free(ctx)
+    e, m = np.array(e).mean(axis=0), np.array(m).mean(axis=0)  # per replica
+    u_ref = exact.onsager_energy_per_site(beta)
+    se = e.std(ddof=1) / np.sqrt(R)
+    assert abs(e.mean() - u_ref) < 4 * se + 2e-3, (e.mean(), u_ref, se)
+    if beta > 0.4407:
+        m_ref = (1.0 - np.sinh(2 * beta) ** -4) ** 0.125
+        sem = m.std(ddof=1) / np.sqrt(R)
+        assert abs(m.mean() - m_ref) < 4 * sem + 5e-3, (m.mean(), m_ref, sem)
+    else:
+        assert m.mean() < 0.05
