@@ -24,6 +24,8 @@ _LIB = None
 INIT_STEP = 0xFFFFFFFF
 MODE_SINGLE = 0  # lane word = 32 consecutive sites of one replica (int8, packed)
 MODE_MULTISPIN = 1  # lane word = one site of 32 consecutive replicas
+DRAW_DIRECT = 0  # graph lane k draws u_k = W_k
+DRAW_PLANE = 1  # graph lane k draws its bits from the 32 words W_j (bit k of W_j = bit 31-j)
 
 
 def build(force: bool = False) -> str:
@@ -125,10 +127,21 @@ def _open(path: str):
     L.orc_lattice_sums.argtypes = [vp, vp, i64, vp]
     L.orc_orient.argtypes = [i64, vp, vp, ctypes.c_int, vp, vp]
     L.orc_graph_half.argtypes = [vp, vp, i64, i64, vp, vp, vp, ctypes.c_int, vp, vp, d,
-                                 vp, i64, u64, u32, ctypes.c_int]
+                                 vp, i64, u64, u32, ctypes.c_int, ctypes.c_int]
+    L.orc_incidence.argtypes = [i64, i64, vp, vp, ctypes.c_int, vp, vp]
+    L.orc_graph_field.argtypes = [vp, i64, vp, vp, vp, vp, vp, ctypes.c_int, vp, d,
+                                  ctypes.c_int]
+    L.orc_graph_field.restype = d
+    L.orc_graph_draw.argtypes = [u64, i64, i64, u32, ctypes.c_int, ctypes.c_int]
+    L.orc_graph_draw.restype = u32
+    L.orc_graph_site.argtypes = [vp, i64, vp, vp, vp, vp, vp, ctypes.c_int, vp, vp, d, d,
+                                 u64, u32, ctypes.c_int, ctypes.c_int, i64]
+    L.orc_graph_site.restype = ctypes.c_int
+    L.orc_graph_fields.argtypes = [vp, vp, i64, i64, vp, vp, vp, ctypes.c_int, vp, d, i64,
+                                   ctypes.c_int]
     L.orc_graph_init.argtypes = [vp, i64, i64, vp, u64, ctypes.c_int]
     L.orc_graph_run.argtypes = [vp, vp, i64, i64, vp, vp, vp, ctypes.c_int, vp, vp, d,
-                                vp, vp, i64, u64, u32, i64]
+                                vp, vp, i64, u64, u32, i64, ctypes.c_int]
     L.orc_graph_sums.argtypes = [vp, vp, i64, i64, vp, vp, vp, vp, vp]
     return L
 
@@ -264,7 +277,8 @@ def graph_init(n, R, seed, kind=0, frozen=None):
     return s
 
 
-def graph_half(s, tail, head, J, integer_J, lam, q, beta, seed, t, half, frozen=None):
+def graph_half(s, tail, head, J, integer_J, lam, q, beta, seed, t, half, frozen=None,
+               draw=DRAW_DIRECT):
     s = np.ascontiguousarray(s, dtype=np.int8)
     R, n = s.shape
     out = np.empty_like(s)
@@ -275,12 +289,61 @@ def graph_half(s, tail, head, J, integer_J, lam, q, beta, seed, t, half, frozen=
     b = np.ascontiguousarray(np.broadcast_to(np.asarray(beta, dtype=np.float64), (R,)))
     f = _frozen(frozen, n)
     lib().orc_graph_half(_ptr(s), _ptr(out), n, tail.size, _ptr(tail), _ptr(head), _ptr(Jd),
-                         int(integer_J), _ptr(f), _ptr(ld), q, _ptr(b), R, seed, t, half)
+                         int(integer_J), _ptr(f), _ptr(ld), q, _ptr(b), R, seed, t, half,
+                         int(draw))
     return out
 
 
+def graph_fields(s, tail, head, J, integer_J, lam, q, half):
+    """Fields h[R][n] (fp64) of one half step on the configurations s [R][n]."""
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    R, n = s.shape
+    h = np.empty((R, n), dtype=np.float64)
+    tail = np.ascontiguousarray(tail, dtype=np.int32)
+    head = np.ascontiguousarray(head, dtype=np.int32)
+    Jd = np.ascontiguousarray(J, dtype=np.float64)
+    ld = np.ascontiguousarray(np.broadcast_to(np.asarray(lam, dtype=np.float64), (n,)))
+    lib().orc_graph_fields(_ptr(s), _ptr(h), n, tail.size, _ptr(tail), _ptr(head), _ptr(Jd),
+                           int(integer_J), _ptr(ld), q, R, half)
+    return h
+
+
+class Incidence:
+    """Incidence lists of one half step (orc_incidence) with the per-vertex oracle
+    routines that use them: the field, the draw and the decision of one (x, r)."""
+
+    def __init__(self, n, tail, head, J, integer_J, lam, q, half, frozen=None):
+        self.n, self.half, self.q, self.integer_J = n, half, float(q), int(integer_J)
+        self.tail = np.ascontiguousarray(tail, dtype=np.int32)
+        self.head = np.ascontiguousarray(head, dtype=np.int32)
+        self.J = np.ascontiguousarray(J, dtype=np.float64)
+        self.lam = np.ascontiguousarray(np.broadcast_to(np.asarray(lam, dtype=np.float64), (n,)))
+        self.frozen = _frozen(frozen, n)
+        self.start = np.zeros(n + 1, dtype=np.int64)
+        self.list = np.zeros(max(self.tail.size, 1), dtype=np.int64)
+        lib().orc_incidence(n, self.tail.size, _ptr(self.tail), _ptr(self.head), half,
+                            _ptr(self.start), _ptr(self.list))
+
+    def field(self, sr, x):
+        sr = np.ascontiguousarray(sr, dtype=np.int8)
+        return lib().orc_graph_field(_ptr(sr), int(x), _ptr(self.start), _ptr(self.list),
+                                     _ptr(self.tail), _ptr(self.head), _ptr(self.J),
+                                     self.integer_J, _ptr(self.lam), self.q, self.half)
+
+    def site(self, sr, x, r, beta, seed, t, draw=DRAW_DIRECT):
+        sr = np.ascontiguousarray(sr, dtype=np.int8)
+        return lib().orc_graph_site(_ptr(sr), int(x), _ptr(self.start), _ptr(self.list),
+                                    _ptr(self.tail), _ptr(self.head), _ptr(self.J),
+                                    self.integer_J, _ptr(self.frozen), _ptr(self.lam), self.q,
+                                    float(beta), seed, t, self.half, int(draw), int(r))
+
+
+def graph_draw(seed, x, r, t, half, draw) -> int:
+    return int(lib().orc_graph_draw(seed, int(x), int(r), t, half, int(draw)))
+
+
 def graph_run(s, tail, head, J, integer_J, lam, q, beta, seed, t0, n_steps, beta_sched=None,
-              frozen=None):
+              frozen=None, draw=DRAW_DIRECT):
     s = np.array(s, dtype=np.int8, order="C", copy=True)
     R, n = s.shape
     sp = s.copy()
@@ -295,7 +358,7 @@ def graph_run(s, tail, head, J, integer_J, lam, q, beta, seed, t0, n_steps, beta
     f = _frozen(frozen, n)
     lib().orc_graph_run(_ptr(s), _ptr(sp), n, tail.size, _ptr(tail), _ptr(head), _ptr(Jd),
                         int(integer_J), _ptr(f), _ptr(ld), q, _ptr(b), _ptr(bs), R, seed, t0,
-                        n_steps)
+                        n_steps, int(draw))
     return s, sp
 
 

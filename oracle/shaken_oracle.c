@@ -122,9 +122,10 @@ double orc_field(double Jc, int64_t s, double q, int sigma, double lambda) {
 
 /* ------------------------------------------------------------------------- */
 /* Draws.  A lane word is 32 decisions that share counter words (a, b):      */
-/*   plane draws (lattice encodings): W_j = Philox(key, (a, b, t, half +     */
-/*     2*(j>>2)))[j&3], j = 0..31, and u_k = sum_j bit_k(W_j) 2^(31-j).      */
-/*   direct draws (graphs):           u_k = W_k.                             */
+/*   plane draws (lattice encodings; graphs with draw = 1): W_j = Philox(key, */
+/*     (a, b, t, half + 2*(j>>2)))[j&3], j = 0..31, u_k = sum_j bit_k(W_j)   */
+/*     2^(31-j).                                                             */
+/*   direct draws (graphs with draw = 0): u_k = W_k.                         */
 /* ------------------------------------------------------------------------- */
 static void orc_key(uint64_t seed, uint32_t key[2]) {
   key[0] = (uint32_t)(seed & 0xFFFFFFFFu);
@@ -315,58 +316,106 @@ void orc_orient(int64_t m, const int32_t* u, const int32_t* v, int rule, int32_t
   }
 }
 
-/* One half step on a graph for all R replicas.  Spins int8 [R][n].
- * half 0 (1->2): h_x = sum_{e: head(e)=x} J_e sigma_tail(e) + q sigma_x + lambda_x
- * half 1 (2->1): h_x = sum_{e: tail(e)=x} J_e sigma_head(e) + q sigma_x + lambda_x
- * integer_J != 0: J_e in {-1,+1}, the sum is an integer and h is rounded as
- * (s + q sigma) + lambda.  Otherwise the sum is accumulated in fp64 in edge
- * order.  Lane words: a = x, b = r / 32, k = r % 32, direct draws. */
-void orc_graph_half(const int8_t* in, int8_t* out, int64_t n, int64_t m, const int32_t* tail,
-                    const int32_t* head, const double* J, int integer_J, const uint8_t* frozen,
-                    const double* lambda, double q, const double* beta, int64_t R, uint64_t seed,
-                    uint32_t t, int half) {
-  /* incidence lists built by counting (plain, O(n + m)) */
-  int64_t* start = (int64_t*)calloc((size_t)(n + 1), sizeof(int64_t));
-  int64_t* list = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+/* Incidence lists of a half step on a graph (Sec. 2, doubling graph): for
+ * half 0 (1->2) the list of x holds the oriented edges (y -> x), whose tails
+ * are the in-neighbours feeding h^{1->2}_x; for half 1 (2->1) the edges
+ * (x -> y), whose heads are the out-neighbours feeding h^{2->1}_x.  Built by
+ * counting: the edges of x are list[start[x] .. start[x+1]) in edge order. */
+void orc_incidence(int64_t n, int64_t m, const int32_t* tail, const int32_t* head, int half,
+                   int64_t* start, int64_t* list) {
+  for (int64_t x = 0; x <= n; ++x) start[x] = 0;
   for (int64_t e = 0; e < m; ++e) start[(half == 0 ? head[e] : tail[e]) + 1]++;
   for (int64_t x = 0; x < n; ++x) start[x + 1] += start[x];
   int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
   memcpy(fill, start, sizeof(int64_t) * (size_t)(n + 1));
   for (int64_t e = 0; e < m; ++e) list[fill[half == 0 ? head[e] : tail[e]]++] = e;
-  for (int64_t r = 0; r < R; ++r) {
-    const int8_t* sr = in + r * n;
-    for (int64_t x = 0; x < n; ++x) {
-      if (frozen && frozen[x]) {
-        out[r * n + x] = 1;
-        continue;
-      }
-      double h;
-      if (integer_J) {
-        int64_t s = 0;
-        for (int64_t p = start[x]; p < start[x + 1]; ++p) {
-          int64_t e = list[p];
-          int32_t y = half == 0 ? tail[e] : head[e];
-          s += (J[e] > 0 ? 1 : -1) * (int64_t)sr[y];
-        }
-        h = orc_field(1.0, s, q, sr[x], lambda[x]);
-      } else {
-        double acc = 0.0;
-        for (int64_t p = start[x]; p < start[x + 1]; ++p) {
-          int64_t e = list[p];
-          int32_t y = half == 0 ? tail[e] : head[e];
-          acc += J[e] * (double)sr[y];
-        }
-        h = (acc + q * (double)sr[x]) + lambda[x];
-      }
-      uint64_t T = orc_threshold(h, beta[r]);
-      uint32_t u = orc_draw_direct(seed, (uint32_t)x, (uint32_t)(r >> 5), t, (uint32_t)half,
-                                   (int)(r & 31));
-      out[r * n + x] = ((uint64_t)u < T) ? 1 : -1;
+  free(fill);
+}
+
+/* Local field of x in the configuration sr [n] of one replica (the fields
+ * below Eq. (ham21), Sec. 2):
+ *   half 0: h_x = sum_{e: head(e)=x} J_e sigma_tail(e) + q sigma_x + lambda_x
+ *   half 1: h_x = sum_{e: tail(e)=x} J_e sigma_head(e) + q sigma_x + lambda_x
+ * integer_J != 0: J_e in {-1,+1}, the sum is an integer and h is rounded as
+ * (s + q sigma) + lambda.  Otherwise the sum is accumulated in fp64 in edge
+ * order.  start/list: orc_incidence of the same half. */
+double orc_graph_field(const int8_t* sr, int64_t x, const int64_t* start, const int64_t* list,
+                       const int32_t* tail, const int32_t* head, const double* J, int integer_J,
+                       const double* lambda, double q, int half) {
+  double h;
+  if (integer_J) {
+    int64_t s = 0;
+    for (int64_t p = start[x]; p < start[x + 1]; ++p) {
+      int64_t e = list[p];
+      int32_t y = half == 0 ? tail[e] : head[e];
+      s += (J[e] > 0 ? 1 : -1) * (int64_t)sr[y];
     }
+    h = orc_field(1.0, s, q, sr[x], lambda[x]);
+  } else {
+    double acc = 0.0;
+    for (int64_t p = start[x]; p < start[x + 1]; ++p) {
+      int64_t e = list[p];
+      int32_t y = half == 0 ? tail[e] : head[e];
+      acc += J[e] * (double)sr[y];
+    }
+    h = (acc + q * (double)sr[x]) + lambda[x];
   }
+  return h;
+}
+
+/* Draw of replica r at vertex x: lane word (a, b) = (x, r / 32), lane k = r % 32;
+ * draw 0: direct (u = W_k), draw 1: bit planes (u_k = sum_j bit_k(W_j) 2^(31-j)). */
+uint32_t orc_graph_draw(uint64_t seed, int64_t x, int64_t r, uint32_t t, int half, int draw) {
+  if (draw == 1)
+    return orc_draw_plane(seed, (uint32_t)x, (uint32_t)(r >> 5), t, (uint32_t)half, (int)(r & 31));
+  return orc_draw_direct(seed, (uint32_t)x, (uint32_t)(r >> 5), t, (uint32_t)half, (int)(r & 31));
+}
+
+/* One update of vertex x of replica r on a graph: tau_x = +1 iff u < T(h_x, beta)
+ * (heat-bath law of the half steps, Sec. 2); frozen vertices stay +1. */
+int orc_graph_site(const int8_t* sr, int64_t x, const int64_t* start, const int64_t* list,
+                   const int32_t* tail, const int32_t* head, const double* J, int integer_J,
+                   const uint8_t* frozen, const double* lambda, double q, double beta,
+                   uint64_t seed, uint32_t t, int half, int draw, int64_t r) {
+  if (frozen && frozen[x]) return 1;
+  double h = orc_graph_field(sr, x, start, list, tail, head, J, integer_J, lambda, q, half);
+  uint64_t T = orc_threshold(h, beta);
+  uint32_t u = orc_graph_draw(seed, x, r, t, half, draw);
+  return ((uint64_t)u < T) ? 1 : -1;
+}
+
+/* One half step on a graph for all R replicas.  Spins int8 [R][n]; half 0
+ * (1->2) reads the in-neighbours, half 1 (2->1) the out-neighbours (see
+ * orc_graph_field); draw selects the lane layout of orc_graph_draw. */
+void orc_graph_half(const int8_t* in, int8_t* out, int64_t n, int64_t m, const int32_t* tail,
+                    const int32_t* head, const double* J, int integer_J, const uint8_t* frozen,
+                    const double* lambda, double q, const double* beta, int64_t R, uint64_t seed,
+                    uint32_t t, int half, int draw) {
+  int64_t* start = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  int64_t* list = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+  orc_incidence(n, m, tail, head, half, start, list);
+  for (int64_t r = 0; r < R; ++r)
+    for (int64_t x = 0; x < n; ++x)
+      out[r * n + x] = (int8_t)orc_graph_site(in + r * n, x, start, list, tail, head, J, integer_J,
+                                              frozen, lambda, q, beta[r], seed, t, half, draw, r);
   free(start);
   free(list);
-  free(fill);
+}
+
+/* Fields h_x of every replica and vertex for one half step into h[R][n]
+ * (orc_graph_field). */
+void orc_graph_fields(const int8_t* in, double* h, int64_t n, int64_t m, const int32_t* tail,
+                      const int32_t* head, const double* J, int integer_J, const double* lambda,
+                      double q, int64_t R, int half) {
+  int64_t* start = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  int64_t* list = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+  orc_incidence(n, m, tail, head, half, start, list);
+  for (int64_t r = 0; r < R; ++r)
+    for (int64_t x = 0; x < n; ++x)
+      h[r * n + x] = orc_graph_field(in + r * n, x, start, list, tail, head, J, integer_J, lambda,
+                                     q, half);
+  free(start);
+  free(list);
 }
 
 void orc_graph_init(int8_t* s, int64_t n, int64_t R, const uint8_t* frozen, uint64_t seed,
@@ -391,17 +440,17 @@ void orc_graph_init(int8_t* s, int64_t n, int64_t R, const uint8_t* frozen, uint
 }
 
 /* Full steps on a graph; beta_sched != NULL gives one beta per step (anneal)
- * and overrides beta. */
+ * and overrides beta; draw is the lane layout of orc_graph_draw. */
 void orc_graph_run(int8_t* s, int8_t* sp, int64_t n, int64_t m, const int32_t* tail,
                    const int32_t* head, const double* J, int integer_J, const uint8_t* frozen,
                    const double* lambda, double q, const double* beta, const double* beta_sched,
-                   int64_t R, uint64_t seed, uint32_t t0, int64_t n_steps) {
+                   int64_t R, uint64_t seed, uint32_t t0, int64_t n_steps, int draw) {
   double* b = (double*)malloc(sizeof(double) * (size_t)R);
   for (int64_t st = 0; st < n_steps; ++st) {
     for (int64_t r = 0; r < R; ++r) b[r] = beta_sched ? beta_sched[st] : beta[r];
     uint32_t t = t0 + (uint32_t)st;
-    orc_graph_half(s, sp, n, m, tail, head, J, integer_J, frozen, lambda, q, b, R, seed, t, 0);
-    orc_graph_half(sp, s, n, m, tail, head, J, integer_J, frozen, lambda, q, b, R, seed, t, 1);
+    orc_graph_half(s, sp, n, m, tail, head, J, integer_J, frozen, lambda, q, b, R, seed, t, 0, draw);
+    orc_graph_half(sp, s, n, m, tail, head, J, integer_J, frozen, lambda, q, b, R, seed, t, 1, draw);
   }
   free(b);
 }

@@ -33,10 +33,16 @@ MUTANTS = {
                                    "    u |= ((w >> k) & 1u) << j;"),
     "lattice_decision_inverted": ("  return ((uint64_t)u < T) ? 1 : -1;",
                                   "  return ((uint64_t)u >= T) ? 1 : -1;"),
-    "graph_coupling_sign_dropped": ("          s += (J[e] > 0 ? 1 : -1) * (int64_t)sr[y];",
-                                    "          s += (int64_t)sr[y];"),
-    "graph_real_drops_q": ("        h = (acc + q * (double)sr[x]) + lambda[x];",
-                           "        h = acc + lambda[x];"),
+    "graph_coupling_sign_dropped": ("      s += (J[e] > 0 ? 1 : -1) * (int64_t)sr[y];",
+                                    "      s += (int64_t)sr[y];"),
+    "graph_real_drops_q": ("    h = (acc + q * (double)sr[x]) + lambda[x];",
+                           "    h = acc + lambda[x];"),
+    "graph_plane_draw_wrong_group": (
+        "    return orc_draw_plane(seed, (uint32_t)x, (uint32_t)(r >> 5), t, (uint32_t)half, (int)(r & 31));",
+        "    return orc_draw_plane(seed, (uint32_t)x, (uint32_t)r, t, (uint32_t)half, (int)(r & 31));"),
+    "graph_field_reads_wrong_end": (
+        "      int32_t y = half == 0 ? tail[e] : head[e];\n      acc += J[e] * (double)sr[y];",
+        "      int32_t y = half == 0 ? head[e] : head[e];\n      acc += J[e] * (double)sr[y];"),
     "graph_pair_sum_uses_sigma": (
         "    out[3] += J[e] * (double)(s[tail[e]] * sp[head[e]]);",
         "    out[3] += J[e] * (double)(s[tail[e]] * s[head[e]]);"),
@@ -61,8 +67,13 @@ def _pins():
         ("lattice_sums", pins.test_lattice_sums_match_numpy_hamiltonians),
         ("graph_sums", pins.test_graph_sums_match_numpy_hamiltonians),
         ("lattice_law", lambda: pins.test_lattice_chain_follows_exact_law(core.MODE_SINGLE, None)),
-        ("graph_law_int", lambda: pins.test_graph_chain_follows_exact_law(True)),
-        ("graph_law_real", lambda: pins.test_graph_chain_follows_exact_law(False)),
+        ("graph_law_int", lambda: pins.test_graph_chain_follows_exact_law(True,
+                                                                          core.DRAW_DIRECT)),
+        ("graph_law_real", lambda: pins.test_graph_chain_follows_exact_law(False,
+                                                                           core.DRAW_DIRECT)),
+        ("graph_law_plane", lambda: pins.test_graph_chain_follows_exact_law(True,
+                                                                            core.DRAW_PLANE)),
+        ("graph_fields_dense", pins.test_graph_fields_match_dense_form),
         ("philox_independent", pins.test_philox_matches_independent_implementation),
     ]
 

@@ -121,6 +121,34 @@ def test_draw_layouts_match_definition():
             u |= ((int(W[j]) >> k) & 1) << (31 - j)
         assert core.draw_plane(seed, a, b, t, half, k) == u
         assert core.draw_direct(seed, a, b, t, half, k) == int(W[k])
+        # graph lane words: vertex a, replica 32 b + k
+        assert core.graph_draw(seed, a, 32 * b + k, t, half, core.DRAW_PLANE) == u
+        assert core.graph_draw(seed, a, 32 * b + k, t, half, core.DRAW_DIRECT) == int(W[k])
+
+
+def test_graph_fields_match_dense_form():
+    # the per-vertex field sums (incidence lists, edge order) against the dense
+    # oriented coupling matrix of oracle/exact.py: J^{oT} sigma (half 0) and
+    # J^o sigma (half 1), plus q sigma + lambda (Sec. 2, fields below Eq. (ham21))
+    g = np.random.default_rng(12)
+    n, m = 40, 150
+    u = g.integers(0, n, m).astype(np.int32)
+    v = ((u + 1 + g.integers(0, n - 1, m)) % n).astype(np.int32)
+    for integer_J in (True, False):
+        J = np.where(g.random(m) < 0.5, -1.0, 1.0) if integer_J else g.standard_normal(m)
+        lam = 0.3 * g.standard_normal(n)
+        q = 0.7
+        for rule in (0, 2):
+            tail, head = core.orient(u, v, rule)
+            Jo = exact.oriented_matrix(n, tail, head, J)
+            s = np.where(g.random((5, n)) < 0.5, -1, 1).astype(np.int8)
+            for half in (0, 1):
+                h = core.graph_fields(s, tail, head, J, integer_J, lam, q, half)
+                ref = exact.fields(s.astype(np.float64), Jo, lam, q, half)
+                assert np.abs(h - ref).max() < 1e-12
+                inc = core.Incidence(n, tail, head, J, integer_J, lam, q, half)
+                for x in (0, 7, n - 1):
+                    assert inc.field(s[2], x) == h[2, x]
 
 
 def test_philox_output_is_uniform():
@@ -292,8 +320,9 @@ def test_lattice_chain_follows_exact_law(mode, frozen):
         assert _chi2_pvalue(counts, exact.evolve(mu0, P, t), R) > 1e-4
 
 
-@pytest.mark.parametrize("integer_J", [True, False])
-def test_graph_chain_follows_exact_law(integer_J):
+@pytest.mark.parametrize("integer_J,draw", [(True, core.DRAW_DIRECT), (False, core.DRAW_DIRECT),
+                                            (True, core.DRAW_PLANE)])
+def test_graph_chain_follows_exact_law(integer_J, draw):
     n, R = 6, 6400
     u = np.array([0, 1, 2, 3, 4, 5, 0, 2], dtype=np.int32)
     v = np.array([1, 2, 3, 4, 5, 0, 3, 5], dtype=np.int32)
@@ -311,7 +340,7 @@ def test_graph_chain_follows_exact_law(integer_J):
     s = np.broadcast_to(s0, (R, n)).copy()
     for t in (1, 2):
         st, _ = core.graph_run(s, tail, head, J, integer_J, lam, q, beta, seed=77 + t, t0=3,
-                               n_steps=t)
+                               n_steps=t, draw=draw)
         counts = np.bincount(exact.state_index(st), minlength=S.shape[0]).astype(float)
         assert _chi2_pvalue(counts, exact.evolve(mu0, P, t), R) > 1e-4
 
