@@ -174,6 +174,13 @@ shaken_status shaken_observables(shaken_ctx* ctx, shaken_obs* out);
  * Synchronises. */
 shaken_status shaken_get_spins(shaken_ctx* ctx, int8_t* out);
 
+/* Copy sigma' -- the configuration after the first half step of the last full
+ * step (Sec. 2: sigma^(2) of the pair (sigma^(1), sigma^(2)) the half steps
+ * alternate; before any step sigma' = sigma) -- to host out[R][n] as int8
+ * +1/-1.  With the default order sigma' = P^{1->2} applied to the previous
+ * sigma; reversed order (shaken_set_order): P^{2->1}.  Synchronises. */
+shaken_status shaken_get_spins_prime(shaken_ctx* ctx, int8_t* out);
+
 /* Replace sigma (and sigma') by host in[R][n] (+1/-1; frozen sites must be
  * +1, else E_INVAL).  Does not change the step counter. */
 shaken_status shaken_set_spins(shaken_ctx* ctx, const int8_t* in);
@@ -217,10 +224,20 @@ shaken_status shaken_debug_exact_always(shaken_ctx* ctx, int on);
  * cooperative grid with a grid barrier per half step): the next banded chunk
  * starts with its barrier's arrival count preset so that no block is ever the
  * last to arrive.  Every block's wait then runs out after its bounded spin
- * (about a second), the blocks return without writing the chunk back, and the
- * stepping call returns SHAKEN_E_TIMEOUT with sigma, sigma' and the step counter
- * as before the chunk; the context stays usable. */
+ * (one second on the GPU's global timer), the blocks return without writing the
+ * chunk back, and the stepping call returns SHAKEN_E_TIMEOUT with sigma, sigma'
+ * and the step counter as before the chunk; the context stays usable.
+ * The outcome of a banded chunk is settled by one atomic decision: either every
+ * block passed the last barrier and the chunk is written back whole (the call
+ * succeeds), or a block gave up first and no block writes anything back. */
 shaken_status shaken_debug_band_stall(shaken_ctx* ctx);
+
+/* Diagnostics for the same failure path: in the next banded chunk, block `block`
+ * (0 <= block < grid; no effect if larger) gives up its wait at the last barrier
+ * at once instead of after one second.  Depending on whether the other blocks had
+ * all arrived, the call then either succeeds with the chunk applied or returns
+ * SHAKEN_E_TIMEOUT with the state as before the chunk -- never a mixture. */
+shaken_status shaken_debug_band_hurry(shaken_ctx* ctx, int block);
 
 /* Number of kernel launches this context has issued (all kinds). */
 shaken_status shaken_launch_count(shaken_ctx* ctx, uint64_t* count);

@@ -134,6 +134,7 @@ def _open(path: str):
     L.orc_graph_field.restype = d
     L.orc_graph_draw.argtypes = [u64, i64, i64, u32, ctypes.c_int, ctypes.c_int]
     L.orc_graph_draw.restype = u32
+    L.orc_graph_draws.argtypes = [vp, i64, i64, u64, u32, ctypes.c_int, ctypes.c_int]
     L.orc_graph_site.argtypes = [vp, i64, vp, vp, vp, vp, vp, ctypes.c_int, vp, vp, d, d,
                                  u64, u32, ctypes.c_int, ctypes.c_int, i64]
     L.orc_graph_site.restype = ctypes.c_int
@@ -340,6 +341,13 @@ class Incidence:
 
 def graph_draw(seed, x, r, t, half, draw) -> int:
     return int(lib().orc_graph_draw(seed, int(x), int(r), t, half, int(draw)))
+
+
+def graph_draws(seed, n, R, t, half, draw):
+    """u[R][n]: the draw of every (replica, vertex) of one half step."""
+    u = np.empty((R, n), dtype=np.uint32)
+    lib().orc_graph_draws(_ptr(u), n, R, seed, t, half, int(draw))
+    return u
 
 
 def graph_run(s, tail, head, J, integer_J, lam, q, beta, seed, t0, n_steps, beta_sched=None,

@@ -371,6 +371,13 @@ uint32_t orc_graph_draw(uint64_t seed, int64_t x, int64_t r, uint32_t t, int hal
   return orc_draw_direct(seed, (uint32_t)x, (uint32_t)(r >> 5), t, (uint32_t)half, (int)(r & 31));
 }
 
+/* Draws of every replica and vertex of one half step into u[R][n]. */
+void orc_graph_draws(uint32_t* u, int64_t n, int64_t R, uint64_t seed, uint32_t t, int half,
+                     int draw) {
+  for (int64_t r = 0; r < R; ++r)
+    for (int64_t x = 0; x < n; ++x) u[r * n + x] = orc_graph_draw(seed, x, r, t, half, draw);
+}
+
 /* One update of vertex x of replica r on a graph: tau_x = +1 iff u < T(h_x, beta)
  * (heat-bath law of the half steps, Sec. 2); frozen vertices stay +1. */
 int orc_graph_site(const int8_t* sr, int64_t x, const int64_t* start, const int64_t* list,

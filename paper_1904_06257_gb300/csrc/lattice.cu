@@ -1065,15 +1065,27 @@ __global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* _
 // four words per thread, eight planes, a per-warp queue for the words still
 // undecided), so the trajectory is the same.
 
-constexpr uint32_t kBandSpinLimit = 1u << 19;  // barrier polls: about a second (two L2 atomics each)
+constexpr uint64_t kBandWaitNs = 1000000000ull;  // a barrier wait gives up after 1 s (%globaltimer)
+constexpr uint32_t kBandPollLimit = 1u << 26;      // and after this many polls in any case
 constexpr int kBandMinBlocks = 2;  // blocks per SM: 126 registers, no spills (3: spills, slower)
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 // Grid barrier of a cooperative launch in two phases, so a block can compute
 // between announcing its rows and needing its neighbours'.  band_arrive: every
 // thread fences its global writes (the published rows), then thread 0 counts the
 // block in; the last block resets the count and advances the generation.
-// band_wait: thread 0 polls the generation; a wait that runs out, or that sees
-// another block's error, sets the error flag.  Returns false once the flag is set.
+// band_wait: thread 0 polls the generation until a deadline of kBandWaitNs on the
+// global timer (and at most kBandPollLimit polls); a wait that runs out, or that
+// sees another block's error, sets the error flag and then settles the run's
+// outcome with one compare-and-swap on `commit`: 0 -> 2 (aborted) unless the last
+// barrier has already been passed by every block and the run committed (1), in
+// which case this block still writes its band back.  Returns 0 to go on, 1 to
+// return without writing, 2 to write back (only possible at the last barrier).
 __device__ __forceinline__ void band_arrive(BandSync* bs, uint32_t gen) {
   __threadfence();
   __syncthreads();
@@ -1086,22 +1098,26 @@ __device__ __forceinline__ void band_arrive(BandSync* bs, uint32_t gen) {
   }
 }
 
-__device__ __forceinline__ bool band_wait(BandSync* bs, uint32_t& gen, uint32_t* s_flag) {
+__device__ __forceinline__ uint32_t band_wait(BandSync* bs, uint32_t& gen, uint32_t* s_flag,
+                                              bool last) {
   if (threadIdx.x == 0) {
-    uint32_t spins = 0;
+    const uint64_t limit = (last && bs->hurry == blockIdx.x) ? 0ull : kBandWaitNs;
+    const uint64_t t0 = global_ns();
+    uint32_t polls = 0, f = 0u;
     while (atomicAdd(&bs->gen, 0u) == gen) {
-      if (++spins > kBandSpinLimit || atomicAdd(&bs->err, 0u) != 0u) {
+      if (atomicAdd(&bs->err, 0u) != 0u || global_ns() - t0 > limit || ++polls > kBandPollLimit) {
         atomicExch(&bs->err, 1u);
         break;
       }
-      __nanosleep(32);
+      __nanosleep(64);
     }
     __threadfence();
-    *s_flag = atomicAdd(&bs->err, 0u);
+    if (atomicAdd(&bs->err, 0u) != 0u) f = atomicCAS(&bs->commit, 0u, 2u) == 1u ? 2u : 1u;
+    *s_flag = f;
   }
   gen += 1u;
   __syncthreads();
-  return *s_flag == 0u;
+  return *s_flag;
 }
 
 // S, V, H of local word l (column c) of a band buffer (packed rows of wpr words;
@@ -1273,6 +1289,7 @@ __global__ void __launch_bounds__(kTile, kBandMinBlocks) lattice_band_kernel(
   uint32_t* buf[2] = {smem, smem + n_loc};  // sigma (A), sigma' (B)
   const uint32_t order = J.cd->order;
   uint32_t gen = 0;
+  bool write_back = false;  // the run was committed while this block was giving up
   if (threadIdx.x == 0) gen = atomicAdd(&bs->gen, 0u);
   // sigma's rows r0 - 1 .. r1 (wrapping) and the table
   for (uint32_t l = threadIdx.x; l < n_loc; l += blockDim.x) {
@@ -1310,7 +1327,12 @@ __global__ void __launch_bounds__(kTile, kBandMinBlocks) lattice_band_kernel(
       }
       band_arrive(bs, gen);
       band_decide(J, stab, in, out, Ri, w_first, wpr, typ, K, P, q, calls);
-      if (!band_wait(bs, gen, &s_flag)) return;
+      const uint32_t w = band_wait(bs, gen, &s_flag, st + 1u == n_steps && pos == 1u);
+      if (w == 1u) return;
+      if (w == 2u) {
+        write_back = true;
+        break;
+      }
       const uint32_t* above = xch + ((size_t)pos * G + (b + G - 1u) % G) * 2u * wpr + wpr;
       const uint32_t* below = xch + ((size_t)pos * G + (b + 1u) % G) * 2u * wpr;
       for (uint32_t c = threadIdx.x; c < wpr; c += blockDim.x) {
@@ -1319,6 +1341,14 @@ __global__ void __launch_bounds__(kTile, kBandMinBlocks) lattice_band_kernel(
       }
       __syncthreads();
     }
+    if (write_back) break;
+  }
+  if (!write_back) {
+    // every block passed the last barrier: commit (0 -> 1) unless a block that gave
+    // up has already aborted the run (2); the chunk is written back only if committed
+    if (threadIdx.x == 0) s_flag = atomicCAS(&bs->commit, 0u, 1u) == 2u ? 1u : 0u;
+    __syncthreads();
+    if (s_flag != 0u) return;
   }
   for (uint32_t o = threadIdx.x; o < n_own; o += blockDim.x) {
     resident_store<ENC>(J, J.A, w_first + o, buf[0][wpr + o]);

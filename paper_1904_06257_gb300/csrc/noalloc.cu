@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 #include <mutex>
 
 #include "../../include/shaken.h"
@@ -216,6 +217,11 @@ extern "C" shaken_status shaken_lattice_observables_noalloc(
     shaken_internal_set_error(m);
     return SHAKEN_E_INVAL;
   };
+  auto cuda_fail = [](const char* what, cudaError_t e) {
+    const std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    shaken_internal_set_error(m.c_str());
+    return SHAKEN_E_CUDA;
+  };
   if (!sigma_dev || !sigma_prime_dev || !out_host) return bad("NULL argument");
   if ((reinterpret_cast<uintptr_t>(sigma_dev) | reinterpret_cast<uintptr_t>(sigma_prime_dev)) & 15u)
     return bad("spin buffers must be 16-byte aligned");
@@ -232,8 +238,8 @@ extern "C" shaken_status shaken_lattice_observables_noalloc(
     shaken_internal_set_error("cudaGetSymbolAddress of the scratch array failed");
     return SHAKEN_E_CUDA;
   }
-  if (cudaMemsetAsync(p.sums, 0, sizeof(double) * kNumSums * (size_t)replicas, st) != cudaSuccess)
-    return SHAKEN_E_CUDA;
+  cudaError_t e = cudaMemsetAsync(p.sums, 0, sizeof(double) * kNumSums * (size_t)replicas, st);
+  if (e != cudaSuccess) return cuda_fail("clearing the scratch sums", e);
   const uint32_t Lu = (uint32_t)L;
   const int jobs = encoding == SHAKEN_MULTISPIN ? replicas / 32 : replicas;
   const uint32_t nwords = encoding == SHAKEN_MULTISPIN ? Lu * Lu : Lu * (Lu / 32u);
@@ -248,10 +254,12 @@ extern "C" shaken_status shaken_lattice_observables_noalloc(
                                                                 p.sums);
   noalloc_finish_kernel<<<(replicas + 127) / 128, 128, 0, st>>>(
       p.sums, replicas, (double)L * (double)L, J, q, lambda_const, p.obs);
-  if (cudaGetLastError() != cudaSuccess) return SHAKEN_E_CUDA;
-  if (cudaMemcpyAsync(out_host, p.obs, sizeof(shaken_obs) * (size_t)replicas,
-                      cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    return SHAKEN_E_CUDA;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return SHAKEN_E_CUDA;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail("observables launch", e);
+  e = cudaMemcpyAsync(out_host, p.obs, sizeof(shaken_obs) * (size_t)replicas,
+                      cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail("copy of the observables to the host", e);
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail("stream synchronisation", e);
   return SHAKEN_OK;
 }

@@ -232,6 +232,7 @@ struct shaken_ctx {
   DevMem in_ptr, in_col, in_J, out_ptr, out_col, out_J, lam_dev;
   DevMem band_xch, band_sync;  // banded runs: row exchange area and grid barrier
   bool band_stall = false;     // diagnostics: the next banded run's barrier never completes
+  int band_hurry = -1;         // diagnostics: block that gives up the next run's last wait at once
   CtxDev hcd{};
   uint64_t host_step = 0;
   bool tracking = false;
@@ -1013,8 +1014,10 @@ static shaken_status run_band(shaken_ctx* c, uint64_t n_steps, int grid, size_t 
   while (done < n_steps) {
     const uint64_t chunk = std::min<uint64_t>(n_steps - done, 1u << 16);
     shk::BandSync h0{};
+    h0.hurry = c->band_hurry >= 0 ? (unsigned)c->band_hurry : ~0u;
     if (c->band_stall) h0.count = (unsigned)grid;  // no block is ever the last to arrive
     c->band_stall = false;
+    c->band_hurry = -1;
     CU(cudaMemcpyAsync(c->band_sync.p, &h0, sizeof(h0), cudaMemcpyHostToDevice, st));
     CU(shk::launch_lattice_band(F.enc, F.jobs.as<LatJob>(), grid, smem,
                                 c->band_xch.as<uint32_t>(), c->band_sync.as<shk::BandSync>(),
@@ -1023,9 +1026,9 @@ static shaken_status run_band(shaken_ctx* c, uint64_t n_steps, int grid, size_t 
     shk::BandSync h{};
     CU(cudaMemcpyAsync(&h, c->band_sync.p, sizeof(h), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
-    if (h.err != 0u) {
-      // the blocks returned before writing the chunk back: the state is the one
-      // before the chunk, and the step counter says so
+    if (h.commit != 1u) {
+      // the run was aborted before any block wrote the chunk back: the state is the
+      // one before the chunk, and the step counter says so
       TRY(push_cd(c));
       return fail(SHAKEN_E_TIMEOUT,
                   "banded run: a grid barrier wait ran out; the chunk was not applied");
@@ -1374,6 +1377,16 @@ shaken_status shaken_get_spins(shaken_ctx* ctx, int8_t* out) {
   return SHAKEN_OK;
 }
 
+shaken_status shaken_get_spins_prime(shaken_ctx* ctx, int8_t* out) {
+  if (!ctx || !out) return fail(SHAKEN_E_INVAL, "NULL argument");
+  std::vector<uint8_t> buf(ctx->spin_bytes);
+  cudaStream_t st = ctx_stream(ctx);
+  CU(cudaMemcpyAsync(buf.data(), ctx->B.p, buf.size(), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  decode_spins(ctx, buf, out);
+  return SHAKEN_OK;
+}
+
 shaken_status shaken_set_spins(shaken_ctx* ctx, const int8_t* in) {
   if (!ctx || !in) return fail(SHAKEN_E_INVAL, "NULL argument");
   const int64_t N = ctx->sites();
@@ -1527,6 +1540,12 @@ shaken_status shaken_sync(shaken_ctx* ctx) {
 shaken_status shaken_debug_exact_always(shaken_ctx* ctx, int on) {
   if (!ctx) return fail(SHAKEN_E_INVAL, "ctx is NULL");
   ctx->exact_always = on ? 1 : 0;
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_debug_band_hurry(shaken_ctx* ctx, int block) {
+  if (!ctx || block < 0) return fail(SHAKEN_E_INVAL, "bad argument");
+  ctx->band_hurry = block;
   return SHAKEN_OK;
 }
 

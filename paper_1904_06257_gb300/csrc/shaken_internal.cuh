@@ -235,10 +235,12 @@ struct CtxDev {
 // error flag set by a block whose wait ran out (the launch then stops early and
 // the host reports a timeout).
 struct BandSync {
-  unsigned int count;
-  unsigned int gen;
-  unsigned int err;
-  unsigned int pad;
+  unsigned int count;   // blocks arrived at the current barrier
+  unsigned int gen;     // barrier generation
+  unsigned int err;     // a block gave up a wait
+  unsigned int commit;  // 0 undecided, 1 every block finished (write back), 2 aborted
+  unsigned int hurry;   // diagnostics: block that gives up its last wait at once (~0u: none)
+  unsigned int pad[3];
 };
 
 // One member of a batch for the batched state and observables copies: its state

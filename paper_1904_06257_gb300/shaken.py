@@ -74,6 +74,7 @@ def _load():
         "shaken_step_record": [vp, u64, vp, vp],
         "shaken_observables": [vp, vp],
         "shaken_get_spins": [vp, vp],
+        "shaken_get_spins_prime": [vp, vp],
         "shaken_set_spins": [vp, vp],
         "shaken_get_step": [vp, ctypes.POINTER(u64)],
         "shaken_save": [vp, vp, ctypes.POINTER(sz)],
@@ -81,6 +82,7 @@ def _load():
         "shaken_debug_fields": [vp, ctypes.c_int, vp],
         "shaken_debug_exact_always": [vp, ctypes.c_int],
         "shaken_debug_band_stall": [vp],
+        "shaken_debug_band_hurry": [vp, ctypes.c_int],
         "shaken_launch_count": [vp, ctypes.POINTER(u64)],
         "shaken_sync": [vp],
         "shaken_batch_create": [ctypes.POINTER(vp), vp],
@@ -243,6 +245,12 @@ def shaken_get_spins(ctx, replicas: int, sites: int):
     return out
 
 
+def shaken_get_spins_prime(ctx, replicas: int, sites: int):
+    out = np.zeros((replicas, sites), dtype=np.int8)
+    _check(_lib.shaken_get_spins_prime(ctx, _ptr(out)))
+    return out
+
+
 def shaken_set_spins(ctx, spins):
     s = np.ascontiguousarray(spins, dtype=np.int8)
     _check(_lib.shaken_set_spins(ctx, _ptr(s)))
@@ -280,6 +288,10 @@ def shaken_debug_exact_always(ctx, on: bool):
 def shaken_debug_band_stall(ctx):
     """The next banded chunk's grid barrier never completes (timeout-path test)."""
     _check(_lib.shaken_debug_band_stall(ctx))
+
+
+def shaken_debug_band_hurry(ctx, block: int):
+    _check(_lib.shaken_debug_band_hurry(ctx, int(block)))
 
 
 def shaken_launch_count(ctx) -> int:

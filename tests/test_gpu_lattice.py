@@ -263,6 +263,39 @@ def test_banded_barrier_timeout_leaves_state(S):
     S.shaken_free(ctx)
 
 
+def test_banded_timeout_at_last_barrier_is_all_or_nothing(S):
+    """A block that gives up its wait at the last barrier while the other blocks are
+    arriving or already through: the chunk's outcome is settled by one atomic
+    decision, so the call either succeeds with the whole chunk applied (equal to the
+    oracle's trajectory) or returns E_TIMEOUT with sigma, sigma' and the step counter
+    exactly as before -- never a partly written chunk.  No wait is unbounded: the
+    hurried block's deadline is zero, everyone else's one second."""
+    L, J, q, lam, beta, seed = 512, 1.0, 1.0, 0.0, 0.44, 607
+    ctx = S.shaken_init(lattice_problem(S, S.PACKED, L, 1, beta, J, q, lam), seed)
+    o = core.lattice_init(L, 1, seed, core.MODE_SINGLE, 0)
+    t = 0
+    outcomes = set()
+    for block in (0, 1, 5, 40, 100, 303, 0, 1):
+        before = S.shaken_get_spins(ctx, 1, L * L)
+        before_p = S.shaken_get_spins_prime(ctx, 1, L * L)
+        S.shaken_debug_band_hurry(ctx, block)
+        try:
+            S.shaken_step(ctx, 8)
+            outcomes.add("ok")
+            o, op = core.lattice_run(o, J, q, lam, beta, seed, t, 8, core.MODE_SINGLE)
+            t += 8
+            assert np.array_equal(S.shaken_get_spins(ctx, 1, L * L).reshape(1, L, L), o)
+            assert np.array_equal(S.shaken_get_spins_prime(ctx, 1, L * L).reshape(1, L, L), op)
+        except S.ShakenError as err:
+            assert err.status == -4  # SHAKEN_E_TIMEOUT
+            outcomes.add("timeout")
+            assert np.array_equal(S.shaken_get_spins(ctx, 1, L * L), before)
+            assert np.array_equal(S.shaken_get_spins_prime(ctx, 1, L * L), before_p)
+        assert S.shaken_get_step(ctx) == t
+    S.shaken_free(ctx)
+    assert outcomes  # at least one chunk ran; which outcomes occur depends on timing
+
+
 @pytest.mark.parametrize("enc,L", [("INT8", 4096), ("PACKED", 8192)])
 def test_banded_path_equals_tiled_path_at_full_size(S, enc, L):
     """At the plain-lattice size (4096^2, the bench's configuration) and at 8192^2

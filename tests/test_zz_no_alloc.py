@@ -30,6 +30,11 @@ def device_state(S, ctx):
     ("INT8", 96, 3, 1.0, 0.5, 0.01),
     ("PACKED", 64, 2, -0.7, 1.0, -0.2),
     ("MULTISPIN", 64, 64, 1.0, 1.0, 0.0),
+    # the grid's x dimension at its cap of 1024 blocks: a grid-stride loop, and
+    # several blocks adding into the same replica's sums
+    ("INT8", 4096, 1, 1.0, 1.0, 0.0),
+    # the scratch's replica limit exactly (128 multispin groups)
+    ("MULTISPIN", 32, 4096, 1.0, 0.8, 0.05),
 ])
 def test_noalloc_observables_match_regular_entry(enc, L, R, J, q, lam):
     require_cuda()
