@@ -224,6 +224,80 @@ def onsager_energy_per_site(beta: float, J: float = 1.0) -> float:
                                   * ellipk(k * k))
 
 
+def shaken_triangular_couplings(beta: float, J: float, q: float):
+    """(K1, K2) of the anisotropic triangular Ising model that the lambda = 0 shaken
+    measure on the square lattice equals (see ``triangular_gibbs_lambda0``)."""
+    K, Q = beta * J, beta * q
+    K1 = 0.25 * np.log(np.cosh(2 * K + Q) / np.cosh(2 * K - Q))
+    K2 = 0.25 * np.log(np.cosh(2 * K + Q) * np.cosh(2 * K - Q) / np.cosh(Q) ** 2)
+    return K1, K2
+
+
+def triangular_free_energy(Ka: float, Kb: float, Kc: float, n: int = 1 << 15) -> float:
+    """-beta f per site of the Ising model on the triangular lattice with couplings
+    Ka, Kb, Kc on its three bond directions (one bond of each per site), Houtappel's
+    solution: -beta f = ln 2 + (1/8 pi^2) int int ln D(t1, t2) dt1 dt2 over [0, 2 pi]^2,
+    D = ca cb cc + sa sb sc - sa cos t1 - sb cos t2 - sc cos(t1 + t2), c = cosh 2K,
+    s = sinh 2K.  For fixed t1, D = A - R cos(t2 - phi) with A = ca cb cc + sa sb sc -
+    sa cos t1 and R^2 = sb^2 + sc^2 + 2 sb sc cos t1, and the t2 integral is
+    2 pi ln[(A + sqrt(A^2 - R^2)) / 2]; the remaining t1 integral of a smooth periodic
+    function is taken by the midpoint rule on n points.  Kc = 0 is Onsager's square
+    lattice."""
+    ca, cb, cc = np.cosh(2 * Ka), np.cosh(2 * Kb), np.cosh(2 * Kc)
+    sa, sb, sc = np.sinh(2 * Ka), np.sinh(2 * Kb), np.sinh(2 * Kc)
+    t = (np.arange(n) + 0.5) * (2.0 * np.pi / n)
+    A = ca * cb * cc + sa * sb * sc - sa * np.cos(t)
+    R2 = sb * sb + sc * sc + 2.0 * sb * sc * np.cos(t)
+    g = np.log(0.5 * (A + np.sqrt(np.maximum(A * A - R2, 0.0))))
+    return float(np.log(2.0) + 0.5 * g.mean())
+
+
+def triangular_bond_correlations(Ka: float, Kb: float, Kc: float, h: float = 1e-5):
+    """Nearest-neighbour correlations <s s> on the three bond directions,
+    d(-beta f)/dK_a, by central differences of ``triangular_free_energy``."""
+    out = []
+    for d in ((h, 0, 0), (0, h, 0), (0, 0, h)):
+        fp = triangular_free_energy(Ka + d[0], Kb + d[1], Kc + d[2])
+        fm = triangular_free_energy(Ka - d[0], Kb - d[1], Kc - d[2])
+        out.append((fp - fm) / (2.0 * h))
+    return tuple(out)
+
+
+def triangular_modulus(Ka: float, Kb: float, Kc: float) -> float:
+    """Elliptic modulus k of the ferromagnetic triangular Ising model with couplings
+    Ka, Kb, Kc (v = tanh K):
+    k = (1 - va^2)(1 - vb^2)(1 - vc^2) / (4 sqrt[(1 + va vb vc)(va + vb vc)(vb + va vc)(vc + va vb)]);
+    k = 1 at criticality, k < 1 in the ordered phase.  Kc = 0 gives the square
+    lattice's k = 1 / (sinh 2Ka sinh 2Kb)."""
+    va, vb, vc = np.tanh(Ka), np.tanh(Kb), np.tanh(Kc)
+    num = (1 - va * va) * (1 - vb * vb) * (1 - vc * vc)
+    den = 4.0 * np.sqrt((1 + va * vb * vc) * (va + vb * vc) * (vb + va * vc) * (vc + va * vb))
+    return float(num / den)
+
+
+def triangular_magnetization(Ka: float, Kb: float, Kc: float) -> float:
+    """Spontaneous magnetisation (1 - k^2)^(1/8) in the ordered phase (k < 1), else 0."""
+    k = triangular_modulus(Ka, Kb, Kc)
+    return float((1.0 - k * k) ** 0.125) if k < 1.0 else 0.0
+
+
+def shaken_lattice_equilibrium(beta: float, J: float, q: float):
+    """Stationary energy per site H(sigma)/|V| = -J (<s_x s_down> + <s_x s_left>) and
+    spontaneous |m| of the lattice shaken chain at lambda = 0, from the exact
+    anisotropic triangular Gibbs measure it equals (reading of Sec. 3, Thm 2.1)."""
+    K1, K2 = shaken_triangular_couplings(beta, J, q)
+    ea, eb, _ = triangular_bond_correlations(K1, K1, K2)
+    return -J * (ea + eb), triangular_magnetization(K1, K1, K2)
+
+
+def shaken_lattice_beta_c(J: float, q: float) -> float:
+    """Critical beta of the lattice shaken chain (its doubling graph is hexagonal):
+    tanh^2(beta J) + 2 tanh(beta J) tanh(beta q) = 1."""
+    from scipy.optimize import brentq
+    return float(brentq(lambda b: np.tanh(b * J) ** 2 + 2 * np.tanh(b * J) * np.tanh(b * q) - 1,
+                        1e-6, 50.0))
+
+
 def triangular_heat_bath(L: int, J: float, q: float, beta: float, sweeps: int, burn: int,
                          seed: int, start_plus: bool = False):
     """Single-spin heat bath on the anisotropic triangular Ising model that the

@@ -222,3 +222,80 @@ def test_triangular_critical_curve_reduces_to_square_at_q_equal_J():
     f = lambda x: 1 + np.tanh(x) ** 4 - 3 * np.tanh(x) ** 2 - 3 * np.tanh(x) ** 2
     Jc = brentq(f, 0.1, 1.0)
     assert abs(np.tanh(Jc) - (np.sqrt(2) - 1)) < 1e-12
+
+
+# --------------------------------------------------------------------------- large-lattice references
+def test_triangular_free_energy_reduces_to_onsager():
+    # Kc = 0 is the square lattice: -(<ss>_a + <ss>_b) equals Onsager's closed form
+    # (complete elliptic integral) on both sides of beta_c
+    for b in (0.2, 0.35, 0.42, 0.46, 0.55, 0.8):
+        ea, eb, _ = exact.triangular_bond_correlations(b, b, 0.0)
+        assert abs(-(ea + eb) - exact.onsager_energy_per_site(b)) < 1e-8
+    # anisotropic square lattice: the two correlations differ and swap with the couplings
+    ea, eb, _ = exact.triangular_bond_correlations(0.3, 0.6, 0.0)
+    eb2, ea2, _ = exact.triangular_bond_correlations(0.6, 0.3, 0.0)
+    assert ea < eb and abs(ea - ea2) < 1e-10 and abs(eb - eb2) < 1e-10
+
+
+def test_triangular_references_at_known_points():
+    # isotropic triangular lattice at criticality (e^{4K} = 3): <ss> = 2/3 on every bond
+    Kc = np.log(3.0) / 4.0
+    for e in exact.triangular_bond_correlations(Kc, Kc, Kc):
+        assert abs(e - 2.0 / 3.0) < 1e-6
+    # high-temperature series: <ss>_a = t_a + 2 t_b t_c + O(t^3) (each bond lies in two
+    # triangles), t = tanh K
+    for K in (0.005, 0.01):
+        ea, _, _ = exact.triangular_bond_correlations(K, 1.3 * K, 0.7 * K)
+        ta, tb, tc = np.tanh(K), np.tanh(1.3 * K), np.tanh(0.7 * K)
+        assert abs(ea - (ta + 2 * tb * tc)) < 10 * K ** 3
+
+
+def test_triangular_magnetization_special_cases():
+    # square lattice (Kc = 0): Onsager-Yang (1 - sinh^-4 2K)^(1/8), anisotropic form
+    for Ka, Kb in ((0.45, 0.45), (0.5, 0.6), (0.7, 0.35)):
+        ref = (1.0 - (np.sinh(2 * Ka) * np.sinh(2 * Kb)) ** -2) ** 0.125
+        assert abs(exact.triangular_magnetization(Ka, Kb, 0.0) - ref) < 1e-12
+    # isotropic triangular lattice (Potts): M^8 = 1 - 16 x^3 / ((1 + 3x)(1 - x)^3), x = e^{-4K}
+    for K in (0.3, 0.35, 0.45):
+        x = np.exp(-4 * K)
+        ref = (1.0 - 16 * x ** 3 / ((1 + 3 * x) * (1 - x) ** 3)) ** 0.125
+        assert abs(exact.triangular_magnetization(K, K, K) - ref) < 1e-12
+    assert exact.triangular_magnetization(0.2, 0.2, 0.2) == 0.0  # disordered
+
+
+def test_triangular_modulus_is_one_on_the_critical_surface():
+    # criticality of the triangular model: sum over pairs sinh 2Ki sinh 2Kj = 1
+    g = np.random.default_rng(4)
+    for _ in range(20):
+        a, b = g.uniform(0.05, 0.6, 2)
+        sa, sb = np.sinh(2 * a), np.sinh(2 * b)
+        sc = (1.0 - sa * sb) / (sa + sb)
+        if sc <= 0:
+            continue
+        assert abs(exact.triangular_modulus(a, b, np.arcsinh(sc) / 2.0) - 1.0) < 1e-12
+
+
+def test_shaken_critical_line_maps_to_triangular_criticality():
+    # the honeycomb line tanh^2 K + 2 tanh K tanh Q = 1 of the doubling graph and the
+    # triangular couplings (K1, K1, K2) of the lambda = 0 shaken measure give k = 1,
+    # and beta_c tends to Onsager's 0.4407 as q grows (Thm 3.1)
+    prev = None
+    for q in (0.5, 1.0, 2.0, 4.0, 8.0, 16.0):
+        bc = exact.shaken_lattice_beta_c(1.0, q)
+        K1, K2 = exact.shaken_triangular_couplings(bc, 1.0, q)
+        assert abs(exact.triangular_modulus(K1, K1, K2) - 1.0) < 1e-9
+        if prev is not None:
+            assert bc < prev
+        prev = bc
+    assert abs(prev - np.arctanh(np.sqrt(2.0) - 1.0)) < 1e-5
+
+
+def test_shaken_equilibrium_matches_triangular_heat_bath():
+    # the exact energy of the lambda = 0 shaken measure against an independent single-spin
+    # heat bath of the same triangular model (paramagnetic point, 4 standard errors)
+    beta, J, q = 0.45, 1.0, 1.0
+    E_ref, m_ref = exact.shaken_lattice_equilibrium(beta, J, q)
+    E, M = exact.triangular_heat_bath(48, J, q, beta, sweeps=600, burn=200, seed=3)
+    se = exact.batch_means_se(E)
+    assert m_ref == 0.0
+    assert abs(E.mean() - E_ref) < 4 * se + 2e-3, (E.mean(), E_ref, se)
