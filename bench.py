@@ -204,10 +204,13 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
-    if args.only_graphs or args.only_serving or args.only_small or args.only_plain:
+    if (args.only_graphs or args.only_serving or args.only_small or args.only_plain
+            or args.only_config2):
         if rank == 0:
             if args.only_small:
                 part = run_small(S, stream)
+            elif args.only_config2:
+                part = run_config2(S, stream, torch)
             elif args.only_plain:
                 part = run_plain(S, stream, torch)
             elif args.only_graphs:
@@ -346,6 +349,9 @@ def run_ours(args, rank, world, local_rank):
     plain = run_plain(S, stream, torch)
     plain_rate = plain["int8"]
 
+    # ---- plain-lattice sweep: L = 4096, lambda x q x beta x encoding x start, 2000 steps each
+    config2 = None if args.skip_config2 else run_config2(S, stream, torch)
+
     # ---- small lattice: L = 64 int8, one replica, beta = 0.40, 10^4 steps with m and H per step
     small = run_small(S, stream)
 
@@ -422,6 +428,7 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clocks,
             "graphs": graphs,
             "small_lattice": small,
+            "config2": config2,
             "metastability": meta,
             "serving": serving,
             "batched_vs_plain": {
@@ -519,6 +526,94 @@ def run_plain(S, stream, torch, L=4096, steps=512):
         plain[name] = 2.0 * L * L * steps / (pe0.elapsed_time(pe1) * 1e-3)
         S.shaken_free(cp)
     return plain
+
+
+# ------------------------------------------------------------------------ plain-lattice sweep
+C2_L, C2_STEPS, C2_BURN, C2_CHUNK = 4096, 2000, 1000, 50
+C2_BETAS = (0.40, 0.4407, 0.48)
+C2_QS = (0.5, 1.0, 2.0)
+C2_ONSAGER_QS = (4.0, 8.0, 16.0)
+REFERENCE_FILE = os.path.join(ROOT, "tests", "golden", "lattice_references.json")
+
+
+def run_config2(S, stream, torch, L=C2_L, steps=C2_STEPS, burn=C2_BURN, chunk=C2_CHUNK):
+    """The plain single-lattice sweep: L x L torus, J = 1, one replica, lambda in {0, 0.01},
+    q in {0.5, 1, 2} (and q in {4, 8, 16} at lambda = 0 for the q -> infinity limit of
+    Thm 3.1), beta in {0.40, 0.4407, 0.48}, int8 and bit-packed spins, all-plus and
+    random starts, `steps` full steps each.  Per run: site-updates/s of the first
+    `burn` steps (one stepping call, CUDA events), then the energy per site and |m|
+    sampled every `chunk` steps over the rest.  At lambda = 0 they are compared with
+    the exact stationary values of the shaken chain (the anisotropic triangular Ising
+    measure it equals, tests/golden/lattice_references.json, written from the oracle's
+    exact module): energy within 4 standard errors + 1e-3 wherever the run can reach
+    equilibrium (not within 3% of beta_c; from random starts only in the disordered
+    phase), |m| < 5e-3 in the disordered phase and within 4 standard errors + 2e-3 of
+    the spontaneous magnetisation from the all-plus start in the ordered phase.  At
+    lambda = 0.01 (no closed form) the magnetisation must exceed the lambda = 0 run's.
+    Both encodings share seeds, so their trajectories (and observables) are identical."""
+    with open(REFERENCE_FILE) as f:
+        refs = {(r["q"], r["beta"]): r for r in json.load(f)["points"]}
+    cases = [(lam, q) for lam in (0.0, 0.01) for q in C2_QS] + [(0.0, q) for q in C2_ONSAGER_QS]
+    runs, n_checked, failures = [], 0, []
+    mags = {}
+    idx = 0
+    for lam, q in cases:
+        for beta in C2_BETAS:
+            for start in ("plus", "random"):
+                seed = W.BASE_SEED + 4000 + idx
+                idx += 1
+                for name, enc in (("int8", S.INT8), ("packed", S.PACKED)):
+                    p = S.Problem(S.LATTICE, enc, 1, beta, q, L=L, J=1.0, lambda_const=lam,
+                                  init=1 if start == "plus" else 0)
+                    c = S.shaken_init(p, seed, stream)
+                    dt = _timed(torch, stream, lambda: S.shaken_step(c, burn))
+                    E, M = [], []
+                    for _ in range((steps - burn) // chunk):
+                        S.shaken_step(c, chunk)
+                        o = S.shaken_observables(c, 1)
+                        E.append(float(o["energy"][0]) / (L * L))
+                        M.append(float(o["magnetization"][0]))
+                    S.shaken_free(c)
+                    E, M = np.array(E), np.array(M)
+                    se_e = E.std(ddof=1) / math.sqrt(E.size)
+                    se_m = np.abs(M).std(ddof=1) / math.sqrt(M.size)
+                    row = {"enc": name, "lambda": lam, "q": q, "beta": beta, "start": start,
+                           "updates_per_s": 2.0 * L * L * burn / dt,
+                           "energy_per_site": float(E.mean()), "energy_se": float(se_e),
+                           "abs_m": float(np.abs(M).mean()), "m": float(M.mean()),
+                           "abs_m_se": float(se_m)}
+                    if lam == 0.0:
+                        r = refs[(q, beta)]
+                        bc = r["beta_c"]
+                        near = abs(beta / bc - 1.0) < 0.03
+                        ordered = beta > bc
+                        row.update({"energy_exact": r["energy_per_site"], "abs_m_exact": r["abs_m"],
+                                    "beta_c": bc, "near_critical": near})
+                        checks = []
+                        if not near and (start == "plus" or not ordered):
+                            checks.append(abs(E.mean() - r["energy_per_site"]) < 4 * se_e + 1e-3)
+                        if not near and not ordered:
+                            checks.append(np.abs(M).mean() < 5e-3)
+                        if not near and ordered and start == "plus":
+                            checks.append(abs(np.abs(M).mean() - r["abs_m"]) < 4 * se_m + 2e-3)
+                        row["compared"] = len(checks)
+                        row["in_tolerance"] = bool(all(checks)) if checks else None
+                        n_checked += len(checks)
+                        if checks and not all(checks):
+                            failures.append(row)
+                    mags[(name, lam, q, beta, start)] = float(M.mean())
+                    runs.append(row)
+    order_ok = [mags[(n, 0.01, q, b, st)] > mags[(n, 0.0, q, b, st)]
+                for (n, lam, q, b, st) in mags if lam == 0.0 and (n, 0.01, q, b, st) in mags]
+    same = all(abs(a["energy_per_site"] - b["energy_per_site"]) < 1e-12
+               and a["m"] == b["m"] for a, b in zip(runs[0::2], runs[1::2]))
+    rates = {e: [r["updates_per_s"] for r in runs if r["enc"] == e] for e in ("int8", "packed")}
+    return {"L": L, "steps": steps, "timed_steps": burn, "sample_every": chunk,
+            "runs": runs, "checks": n_checked, "failures": len(failures),
+            "lambda_0p01_raises_m": f"{sum(order_ok)}/{len(order_ok)}",
+            "int8_equals_packed": bool(same),
+            "updates_per_s_median": {e: float(np.median(v)) for e, v in rates.items()},
+            "updates_per_s_min": {e: float(np.min(v)) for e, v in rates.items()}}
 
 
 # ------------------------------------------------------------------------ small lattice
@@ -673,7 +768,8 @@ def run_graphs(S, stream, torch, args):
 # ------------------------------------------------------------------------ serving
 def _serving_pool(args):
     """Pre-generated +-1 Erdos-Renyi graphs of the serving distribution (n log-uniform in
-    [1e3, 1e6], mean degree uniform in [3, 16])."""
+    [1e3, 1e6], mean degree uniform in [3, 16]); only the literal 200 jobs/s stream uses
+    them (its thousands of jobs cannot each get a fresh graph in time)."""
     g = W.rng(W.BASE_SEED + 77)
     pool = []
     for k in range(args.serve_pool):
@@ -686,15 +782,24 @@ def _serving_pool(args):
     return pool
 
 
-def _serve(S, stream, pool, jobs, args, step_scale, window_s=None):
-    """Submit `jobs` at their arrival times (job k anneals pool graph k mod |pool|, beta
-    0.1 -> 3.0), then drain -- or, with window_s, stop after window_s seconds and cancel
-    what is left.  Latency = completion - arrival of the completed jobs."""
+def _job_graph(jb):
+    """A fresh +-1 Erdos-Renyi graph with the job's own n and mean degree."""
+    u, v = W.erdos_renyi(jb["n"], jb["mean_degree"], jb["seed"] + 17)
+    return jb["n"], u, v, W.couplings_pm1(u.size, jb["seed"] + 29)
+
+
+def _serve(S, stream, jobs, graphs, args, step_scale, window_s=None):
+    """Submit `jobs` at their arrival times (job k anneals graphs[k] -- or graphs[k mod
+    len(graphs)] for a pool --, beta 0.1 -> 3.0), then drain -- or, with window_s, stop
+    after window_s seconds and cancel what is left.  Latency = completion - arrival of
+    the completed jobs.  The server admits by the device-memory budget and the work cap
+    (site updates per step of the running set), in arrival order, first fit."""
     srv = S.shaken_server_create(int(args.serve_budget_gb * 2**30), 64, stream)
+    S.shaken_server_set_policy(srv, args.serve_work_cap, 0)
     t0 = time.perf_counter()
     ids, meta, lags = [], [], []
     for k, jb in enumerate(jobs):
-        n, u, v, J = pool[k % len(pool)]
+        n, u, v, J = graphs[k % len(graphs)]
         steps = max(1, int(round(jb["steps"] * step_scale)))
         R = jb["replicas"]
         p = S.Problem(S.GRAPH, S.MULTISPIN, R, 0.1, 1.0, n=n, u=u, v=v, J_edge=J,
@@ -713,6 +818,7 @@ def _serve(S, stream, pool, jobs, args, step_scale, window_s=None):
             time.sleep(rest)
     wall = time.perf_counter() - t0
     upd, launches, done = S.shaken_server_stats(srv)
+    queued, running = S.shaken_server_queue(srv)
     lat, states = [], [0, 0, 0]
     for jid, (arr, n, R, steps) in zip(ids, meta):
         st = S.shaken_server_poll(srv, jid)
@@ -722,38 +828,42 @@ def _serve(S, stream, pool, jobs, args, step_scale, window_s=None):
             lat.append(td - arr)
     S.shaken_server_free(srv)
     work = sum(2.0 * n * R * st for _, n, R, st in meta)
-    return {"jobs": len(ids), "completed": int(done), "queued_at_end": states[0],
-            "running_at_end": states[1], "wall_s": wall,
+    return {"jobs": len(ids), "completed": int(done), "queued_at_end": int(queued),
+            "running_at_end": int(running), "wall_s": wall,
             "offered_updates": work, "served_updates_per_s": upd / wall,
             "latency_p50_s": float(np.percentile(lat, 50)) if lat else None,
             "latency_p99_s": float(np.percentile(lat, 99)) if lat else None,
+            "latency_max_s": float(max(lat)) if lat else None,
             "submit_lag_max_s": float(max(lags) if lags else 0.0),
             "launches": int(launches)}
 
 
 def run_serving(S, stream, args):
     """Continuous batching of annealing jobs through the server (Poisson arrivals of
-    +-1 Erdos-Renyi anneals, replicas log-uniform over multiples of 32 in [32, 1024],
-    steps uniform in [1000, 20000] x step_scale):
+    +-1 Erdos-Renyi anneals, n log-uniform in [1e3, 1e6], mean degree U[3, 16], a fresh
+    graph per job, replicas log-uniform over multiples of 32 in [32, 1024], steps
+    uniform in [1000, 20000] x step_scale):
     * capacity: a burst of jobs submitted at once, served updates/s over the makespan;
     * load sweep: Poisson streams at 50 / 70 / 90 % of that capacity -> p50 / p99
-      latency (completion - arrival);
-    * the literal stream (200 jobs/s, full step counts) for a fixed window: it offers
-      ~100x the capacity, so the queue grows; completed jobs, queue depth and served
-      rate are reported and the rest is cancelled."""
-    pool = _serving_pool(args)
+      latency (completion - arrival), every job drained to completion;
+    * the literal stream (200 jobs/s, full step counts, pool graphs) for a fixed
+      window: it offers hundreds of times the capacity, so the queue grows while the
+      work cap keeps jobs completing; completions, queue depth and served rate are
+      reported and the rest is cancelled."""
     scale = args.serve_step_scale
-    out = {"step_scale": scale, "graph_pool": len(pool), "budget_gb": args.serve_budget_gb}
+    out = {"step_scale": scale, "budget_gb": args.serve_budget_gb,
+           "work_cap_updates_per_step": args.serve_work_cap, "admission": "arrival order, first fit",
+           "graphs": "fresh per job (load sweep, capacity); literal stream: "
+                     f"{args.serve_pool} pre-generated"}
     # expected work per job of the stream distribution (large sample, no GPU)
     sample = W.serving_stream(1000.0, 10.0, W.BASE_SEED + 9)
-    mean_work = float(np.mean([2.0 * pool[k % len(pool)][0] * jb["replicas"] *
-                               max(1, int(round(jb["steps"] * scale)))
-                               for k, jb in enumerate(sample)]))
+    mean_work = float(np.mean([2.0 * jb["n"] * jb["replicas"] *
+                               max(1, int(round(jb["steps"] * scale))) for jb in sample]))
     # capacity
     burst = W.serving_stream(1000.0, 10.0, W.BASE_SEED + 4, max_jobs=args.serve_burst)
     for jb in burst:
         jb["arrival"] = 0.0
-    cap = _serve(S, stream, pool, burst, args, scale)
+    cap = _serve(S, stream, burst, [_job_graph(jb) for jb in burst], args, scale)
     capacity = cap["offered_updates"] / cap["wall_s"]
     out["capacity"] = {"jobs": cap["jobs"], "makespan_s": cap["wall_s"],
                        "updates_per_s": capacity}
@@ -762,14 +872,15 @@ def run_serving(S, stream, args):
     for frac in (0.5, 0.7, 0.9):
         rate = frac * capacity / mean_work
         jobs = W.serving_stream(rate, args.serve_horizon, W.BASE_SEED + 3)
-        r = _serve(S, stream, pool, jobs, args, scale)
+        r = _serve(S, stream, jobs, [_job_graph(jb) for jb in jobs], args, scale)
         r.update({"load": frac, "arrival_rate_per_s": rate, "horizon_s": args.serve_horizon,
                   "offered_updates_per_s": r["offered_updates"] / args.serve_horizon})
         sweep.append(r)
     out["load_sweep"] = sweep
     # literal stream
+    pool = _serving_pool(args)
     lit = W.serving_stream(200.0, args.serve_literal_horizon, W.BASE_SEED + 3)
-    r = _serve(S, stream, pool, lit, args, 1.0, window_s=args.serve_literal_window)
+    r = _serve(S, stream, lit, pool, args, 1.0, window_s=args.serve_literal_window)
     r.update({"arrival_rate_per_s": 200.0, "horizon_s": args.serve_literal_horizon,
               "window_s": args.serve_literal_window,
               "offered_updates_per_s": r["offered_updates"] / args.serve_literal_horizon})
@@ -830,6 +941,9 @@ def main():
                     help="run the small-lattice section only (profiling runs)")
     ap.add_argument("--only-plain", action="store_true",
                     help="run the plain single-lattice section only (profiling runs)")
+    ap.add_argument("--only-config2", action="store_true",
+                    help="run the plain-lattice sweep (L = 4096) only")
+    ap.add_argument("--skip-config2", action="store_true", help="skip the plain-lattice sweep")
     ap.add_argument("--no-autotune", action="store_true",
                     help="fixed lattice launch-shape rule instead of timed trials (profiling)")
     ap.add_argument("--graph-anneal-steps", type=int, default=5000)
@@ -845,6 +959,8 @@ def main():
                     help="steps per job = U[1000, 20000] x this factor")
     ap.add_argument("--serve-pool", type=int, default=12, help="pre-generated graphs")
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
+    ap.add_argument("--serve-work-cap", type=float, default=1.5e9,
+                    help="site updates per step of the server's running set")
     ap.add_argument("--serve-timeout", type=float, default=120.0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

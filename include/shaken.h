@@ -349,8 +349,29 @@ shaken_status shaken_server_create(shaken_server** out, size_t hbm_budget_bytes,
 shaken_status shaken_server_submit(shaken_server* s, const shaken_problem* p, uint64_t seed,
                                    const double* beta_schedule, uint64_t n_steps,
                                    int64_t* job_id);
+/* Admission policy (no counterpart in the paper; serving is this library's own
+ * use of the anneal).  Besides the memory budget, a queued job is admitted only
+ * while the running jobs' work per full step -- the sum of 2 n R site updates --
+ * stays at or below max_step_updates (default 1.5e9); a job larger than the cap
+ * runs when nothing else does.  Bounding the work in flight keeps the GPU's rate
+ * on the running jobs, so under overload jobs keep completing while the queue
+ * grows.  order 0 (default): arrival order, first fit -- a job that does not fit
+ * is passed over by later jobs that do, at most 8 times, then admission waits for
+ * it; order 1: shortest total work (2 n R steps) first.  keep_states != 0: the
+ * final raw state of every finished job is kept on the host for
+ * shaken_server_result_state.  E_INVAL for max_step_updates <= 0 or another order.
+ * Takes effect at the next admission. */
+shaken_status shaken_server_set_policy(shaken_server* s, double max_step_updates, int order,
+                                       int keep_states);
 /* *state: 0 queued, 1 running, 2 done. */
 shaken_status shaken_server_poll(shaken_server* s, int64_t job_id, int* state);
+/* Jobs waiting for admission and jobs running now (either may be NULL). */
+shaken_status shaken_server_queue(shaken_server* s, int64_t* queued, int64_t* running);
+/* Final raw state (sigma in the job's encoding, as shaken_get_state_raw) of a
+ * finished job into host_words; bytes must equal its shaken_state_bytes.
+ * E_STATE if the job is not finished or states are not kept (set_policy). */
+shaken_status shaken_server_result_state(shaken_server* s, int64_t job_id, void* host_words,
+                                         size_t bytes);
 /* Observables of a finished job into out[R]; also its admission and completion
  * times (seconds since server creation, host steady clock) if non-NULL. */
 shaken_status shaken_server_result(shaken_server* s, int64_t job_id, shaken_obs* out,

@@ -1737,10 +1737,16 @@ const char* shaken_version(void) { return "libshaken 0.1 (sm_103a)"; }
 
 // ============================================================================ server
 // Continuous batching of annealing jobs.  A worker thread owns every device
-// call of the server: it admits queued jobs in arrival order while their
-// device state fits the budget, steps all running jobs together in chunks of
-// chunk_steps (each job stops exactly at its own last step: the kernels skip a
-// context once its step reaches t_end), and retires finished jobs.
+// call of the server: it admits queued jobs while their device state fits the
+// budget and the running set's work per step (site updates, 2 n R per job) stays
+// under a cap, steps all running jobs together in chunks of chunk_steps (each
+// job stops exactly at its own last step: the kernels skip a context once its
+// step reaches t_end), and retires finished jobs.  The cap bounds the work in
+// flight, so under overload the queue grows while jobs keep completing at the
+// GPU's rate instead of every admitted job slowing down together.  Admission
+// order: arrival order, first fit (a job that does not fit is passed over by
+// later ones that do, at most kServerMaxSkips times, then the queue waits for
+// it), or shortest total work first.
 struct ServerJob {
   int64_t id = 0;
   std::unique_ptr<shaken_ctx> prepared;  // host-prepared context (device set-up in the worker)
@@ -1748,15 +1754,24 @@ struct ServerJob {
   std::vector<double> sched;
   uint64_t seed = 0, n_steps = 0;
   size_t bytes = 0;
+  double step_work = 0.0;  // site updates per full step: 2 n R
+  int skips = 0;           // times a later job was admitted before this one
   int state = 0;  // 0 queued, 1 running, 2 done, 3 failed
+  std::vector<uint8_t> final_state;  // raw sigma at retirement (keep_states)
   shaken_ctx* ctx = nullptr;
   double t_submit = 0, t_admit = 0, t_done = 0;
   std::vector<shaken_obs> result;
   std::string error;
 };
 
+static constexpr int kServerMaxSkips = 8;
+
 struct shaken_server {
   size_t budget = 0, used = 0;
+  double work_cap = 1.5e9;  // site updates per step of the running set
+  double work = 0.0;        // of the running jobs
+  int order = 0;            // 0 arrival order (first fit, aging), 1 shortest total work first
+  bool keep_states = false;
   uint32_t chunk = 64;
   cudaStream_t stream = nullptr;
   std::mutex mu;
@@ -1789,14 +1804,44 @@ static size_t job_bytes(const shaken_problem* p) {
   return b + 4096;
 }
 
+// Next queued job to admit (an iterator into s->queue), or end() if none fits now.
+static std::deque<int64_t>::iterator server_pick(shaken_server* s) {
+  auto fits = [&](const ServerJob* j) {
+    if (s->running.empty()) return true;  // a job larger than the caps runs alone
+    return s->used + j->bytes <= s->budget && s->work + j->step_work <= s->work_cap;
+  };
+  auto& Q = s->queue;
+  if (s->order == 1) {  // shortest total work first
+    auto best = Q.end();
+    double bw = 0.0;
+    for (auto it = Q.begin(); it != Q.end(); ++it) {
+      const ServerJob* j = s->jobs[*it].get();
+      const double w = j->step_work * (double)j->n_steps;
+      if (fits(j) && (best == Q.end() || w < bw)) {
+        best = it;
+        bw = w;
+      }
+    }
+    return best;
+  }
+  for (auto it = Q.begin(); it != Q.end(); ++it) {  // arrival order, first fit
+    const ServerJob* j = s->jobs[*it].get();
+    if (fits(j)) return it;
+    if (j->skips >= kServerMaxSkips) return Q.end();  // the queue waits for this job
+  }
+  return Q.end();
+}
+
 static void server_loop(shaken_server* s) {
   std::unique_lock<std::mutex> lk(s->mu);
   while (true) {
     // admit
     while (!s->queue.empty()) {
-      ServerJob* j = s->jobs[s->queue.front()].get();
-      if (s->used + j->bytes > s->budget && !s->running.empty()) break;
-      s->queue.pop_front();
+      auto it = server_pick(s);
+      if (it == s->queue.end()) break;
+      for (auto jt = s->queue.begin(); jt != it; ++jt) s->jobs[*jt]->skips++;
+      ServerJob* j = s->jobs[*it].get();
+      s->queue.erase(it);
       lk.unlock();
       shaken_ctx* c = j->prepared.release();
       c->stream = s->stream;
@@ -1824,6 +1869,7 @@ static void server_loop(shaken_server* s) {
       j->state = 1;
       j->t_admit = s->now();
       s->used += j->bytes;
+      s->work += j->step_work;
       s->running.push_back(j);
       s->batch.plan.members.push_back(c);
       s->batch.plan.invalidate();
@@ -1853,8 +1899,13 @@ static void server_loop(shaken_server* s) {
       s->updates += 2.0 * (double)(c->host_step - before) * (double)c->R * (double)c->sites();
       if (st != SHAKEN_OK || c->host_step >= j->n_steps) {
         j->result.resize(c->R);
+        const bool keep = s->keep_states;
         lk.unlock();
         shaken_status so = st == SHAKEN_OK ? shaken_observables(c, j->result.data()) : st;
+        if (so == SHAKEN_OK && keep) {
+          j->final_state.resize(c->spin_bytes);
+          so = shaken_get_state_raw(c, j->final_state.data(), c->spin_bytes);
+        }
         lk.lock();
         j->state = so == SHAKEN_OK ? 2 : 3;
         if (so != SHAKEN_OK) j->error = g_last_error;
@@ -1866,6 +1917,7 @@ static void server_loop(shaken_server* s) {
         shaken_free(c);
         j->ctx = nullptr;
         s->used -= j->bytes;
+        s->work -= j->step_work;
         s->n_done++;
         s->done_cv.notify_all();
       } else {
@@ -1909,6 +1961,7 @@ shaken_status shaken_server_submit(shaken_server* s, const shaken_problem* p, ui
   j->seed = seed;
   j->n_steps = n_steps;
   j->bytes = job_bytes(p);
+  j->step_work = 2.0 * (double)j->prepared->R * (double)j->prepared->sites();
   if (j->bytes > s->budget) return fail(SHAKEN_E_BUDGET, "job exceeds the device-memory budget");
   std::lock_guard<std::mutex> lk(s->mu);
   j->id = s->next_id++;
@@ -1917,6 +1970,40 @@ shaken_status shaken_server_submit(shaken_server* s, const shaken_problem* p, ui
   s->queue.push_back(j->id);
   s->jobs[j->id] = std::move(j);
   s->cv.notify_all();
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_server_set_policy(shaken_server* s, double max_step_updates, int order,
+                                       int keep_states) {
+  if (!s || !(max_step_updates > 0.0) || (order != 0 && order != 1))
+    return fail(SHAKEN_E_INVAL, "bad argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->work_cap = max_step_updates;
+  s->order = order;
+  s->keep_states = keep_states != 0;
+  s->cv.notify_all();
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_server_queue(shaken_server* s, int64_t* queued, int64_t* running) {
+  if (!s) return fail(SHAKEN_E_INVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (queued) *queued = (int64_t)s->queue.size();
+  if (running) *running = (int64_t)s->running.size();
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_server_result_state(shaken_server* s, int64_t job_id, void* host_words,
+                                         size_t bytes) {
+  if (!s || !host_words) return fail(SHAKEN_E_INVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(job_id);
+  if (it == s->jobs.end()) return fail(SHAKEN_E_INVAL, "unknown job");
+  ServerJob* j = it->second.get();
+  if (j->state != 2) return fail(SHAKEN_E_STATE, "job not finished");
+  if (j->final_state.empty()) return fail(SHAKEN_E_STATE, "final states are not kept");
+  if (bytes != j->final_state.size()) return fail(SHAKEN_E_INVAL, "state size mismatch");
+  std::memcpy(host_words, j->final_state.data(), bytes);
   return SHAKEN_OK;
 }
 

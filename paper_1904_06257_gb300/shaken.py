@@ -113,6 +113,9 @@ def _load():
         "shaken_server_submit": [vp, ctypes.POINTER(shaken_problem), u64, vp, u64,
                                  ctypes.POINTER(i64)],
         "shaken_server_poll": [vp, i64, ctypes.POINTER(ctypes.c_int)],
+        "shaken_server_set_policy": [vp, d, ctypes.c_int, ctypes.c_int],
+        "shaken_server_queue": [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)],
+        "shaken_server_result_state": [vp, i64, vp, sz],
         "shaken_server_result": [vp, i64, vp, ctypes.POINTER(d), ctypes.POINTER(d)],
         "shaken_server_drain": [vp, d],
         "shaken_server_stats": [vp, ctypes.POINTER(d), ctypes.POINTER(u64), ctypes.POINTER(i64)],
@@ -452,6 +455,24 @@ def shaken_server_poll(server, job_id: int) -> int:
     st = ctypes.c_int()
     _check(_lib.shaken_server_poll(server, job_id, ctypes.byref(st)))
     return st.value
+
+
+def shaken_server_set_policy(server, max_step_updates: float = 1.5e9, order: int = 0,
+                             keep_states: bool = False):
+    _check(_lib.shaken_server_set_policy(server, float(max_step_updates), int(order),
+                                         int(bool(keep_states))))
+
+
+def shaken_server_queue(server):
+    q, r = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.shaken_server_queue(server, ctypes.byref(q), ctypes.byref(r)))
+    return q.value, r.value
+
+
+def shaken_server_result_state(server, job_id: int, nbytes: int):
+    out = np.zeros(nbytes, dtype=np.uint8)
+    _check(_lib.shaken_server_result_state(server, job_id, _ptr(out), nbytes))
+    return out
 
 
 def shaken_server_result(server, job_id: int, replicas: int):

@@ -87,3 +87,31 @@ def test_small_field_magnetisation_matches_oracle_chain(S):
     o = _oracle_m(L, 16, q, lam, beta, 0x5348414B + 99, 50, 30, 6)
     se = np.hypot(g.std(ddof=1) / np.sqrt(g.size), o.std(ddof=1) / np.sqrt(o.size))
     assert abs(g.mean() - o.mean()) < 4 * se, (g.mean(), o.mean(), se)
+
+
+@pytest.mark.parametrize("q,beta", [(0.5, 0.48), (2.0, 0.40), (4.0, 0.48), (8.0, 0.48),
+                                    (16.0, 0.48)])
+def test_plain_lattice_matches_exact_stationary_values(S, q, beta):
+    """One int8 lattice (1024 x 1024 torus, the whole-run banded path) started at +1,
+    lambda = 0: the energy per site and |m| after 1500 steps against the exact
+    stationary values of the shaken chain -- the anisotropic triangular Ising measure
+    it equals at lambda = 0 (Houtappel's free energy and the elliptic modulus, in
+    oracle/exact.py) -- within 4 standard errors + 1e-3 (energy) and 2e-3 (|m|)."""
+    L = 1024
+    E_ref, m_ref = exact.shaken_lattice_equilibrium(beta, 1.0, q)
+    ctx = S.shaken_init(lattice_problem(S, S.INT8, L, 1, beta, 1.0, q, 0.0, init=1), 31 + int(q))
+    S.shaken_step(ctx, 1500)
+    E, M = [], []
+    for _ in range(20):
+        S.shaken_step(ctx, 25)
+        o = S.shaken_observables(ctx, 1)
+        E.append(o["energy"][0] / (L * L))
+        M.append(abs(o["magnetization"][0]))
+    S.shaken_free(ctx)
+    E, M = np.array(E), np.array(M)
+    se_e, se_m = E.std(ddof=1) / np.sqrt(E.size), M.std(ddof=1) / np.sqrt(M.size)
+    assert abs(E.mean() - E_ref) < 4 * se_e + 1e-3, (E.mean(), E_ref, se_e)
+    if m_ref == 0.0:
+        assert M.mean() < 1e-2, M.mean()
+    else:
+        assert abs(M.mean() - m_ref) < 4 * se_m + 2e-3, (M.mean(), m_ref, se_m)

@@ -7,7 +7,7 @@ import pytest
 
 from oracle import core
 from paper_1904_06257_gb300 import workloads as W
-from tests.gpu_util import graph_problem, lattice_problem, lib, require_cuda
+from tests.gpu_util import graph_problem, graph_spins_from_raw, lattice_problem, lib, require_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -172,17 +172,74 @@ def test_server_results_equal_alone(S):
         alone.append((S.shaken_get_spins(c, R, n), S.shaken_observables(c, R)))
         S.shaken_free(c)
     srv = S.shaken_server_create(1 << 30, 16)
+    S.shaken_server_set_policy(srv, 1.5e9, 0, keep_states=True)
     ids = [S.shaken_server_submit(srv, p, seed, sched) for p, seed, sched, n, R in jobs]
     S.shaken_server_drain(srv, 120.0)
     for jid, (p, seed, sched, n, R), (spins, obs) in zip(ids, jobs, alone):
         assert S.shaken_server_poll(srv, jid) == 2
         res, ta, td = S.shaken_server_result(srv, jid, R)
         assert td >= ta
+        raw = S.shaken_server_result_state(srv, jid, R * n // 8)
+        assert np.array_equal(graph_spins_from_raw(raw, n, R), spins)
         assert np.allclose(res["energy"], obs["energy"], rtol=0, atol=1e-9)
         # best energies are fp32 block sums added in a run-dependent order: equal to ~1e-6
         assert np.allclose(res["best_energy"], obs["best_energy"], rtol=1e-6, atol=1e-6)
     upd, launches, done = S.shaken_server_stats(srv)
     assert done == len(jobs) and launches > 0
+    S.shaken_server_free(srv)
+
+
+def test_server_work_cap_completes_jobs_under_overload(S):
+    """Overload: twelve jobs at once, a work cap that admits about two at a time.  Jobs
+    complete while others still wait (the queue is non-empty when the first results
+    exist), every job completes, and each result equals the job run alone.  With
+    shortest-work-first admission a small job submitted behind large ones finishes
+    before them."""
+    import time
+    n = 3000
+    u, v = W.erdos_renyi(n, 6.0, 71)
+    J = W.couplings_pm1(u.size, 72)
+    big = graph_problem(S, n, u, v, J, 64, 1.0)
+    sched = W.linear_schedule(0.2, 2.5, 200)
+    step_work = 2.0 * n * 64
+    srv = S.shaken_server_create(1 << 30, 8)
+    S.shaken_server_set_policy(srv, 2.5 * step_work, 0)
+    ids = [S.shaken_server_submit(srv, big, 500 + k, sched) for k in range(12)]
+    saw_queue_with_done = False
+    t_end = time.perf_counter() + 120.0
+    while time.perf_counter() < t_end:
+        _, _, done = S.shaken_server_stats(srv)
+        queued, running = S.shaken_server_queue(srv)
+        assert running <= 2
+        if done > 0 and queued > 0:
+            saw_queue_with_done = True
+        if done == len(ids):
+            break
+        time.sleep(0.002)
+    S.shaken_server_drain(srv, 60.0)
+    assert saw_queue_with_done
+    c = S.shaken_init(big, 500)
+    S.shaken_anneal(c, sched)
+    ref = S.shaken_observables(c, 64)
+    S.shaken_free(c)
+    res, _, _ = S.shaken_server_result(srv, ids[0], 64)
+    assert np.allclose(res["energy"], ref["energy"], rtol=0, atol=1e-9)
+    S.shaken_server_free(srv)
+    # shortest total work first: the small job overtakes the queued large ones
+    small_n = 400
+    su, sv = W.erdos_renyi(small_n, 4.0, 73)
+    small = graph_problem(S, small_n, su, sv, W.couplings_pm1(su.size, 74), 32, 1.0)
+    srv = S.shaken_server_create(1 << 30, 8)
+    S.shaken_server_set_policy(srv, step_work, 1)  # one large job at a time
+    large_ids = [S.shaken_server_submit(srv, big, 600 + k, sched) for k in range(4)]
+    small_id = S.shaken_server_submit(srv, small, 700, W.linear_schedule(0.2, 2.5, 50))
+    S.shaken_server_drain(srv, 120.0)
+    t_small = S.shaken_server_result(srv, small_id, 32)[2]
+    t_large = [S.shaken_server_result(srv, i, 64)[2] for i in large_ids]
+    # done before every large job but the one that may already have been running
+    assert t_small < sorted(t_large)[1]
+    with pytest.raises(S.ShakenError):
+        S.shaken_server_set_policy(srv, 0.0, 0)
     S.shaken_server_free(srv)
 
 
