@@ -546,11 +546,16 @@ def run_config2(S, stream, torch, L=C2_L, steps=C2_STEPS, burn=C2_BURN, chunk=C2
     the exact stationary values of the shaken chain (the anisotropic triangular Ising
     measure it equals, tests/golden/lattice_references.json, written from the oracle's
     exact module): energy within 4 standard errors + 1e-3 wherever the run can reach
-    equilibrium (not within 3% of beta_c; from random starts only in the disordered
-    phase), |m| < 5e-3 in the disordered phase and within 4 standard errors + 2e-3 of
+    equilibrium (not within 5% below or 3% above beta_c; from random starts only in the disordered
+    phase), |m| < 5e-3 in the disordered phase from random starts (from +1 it decays
+    over ~10^4 steps at large q) and within 4 standard errors + 2e-3 of
     the spontaneous magnetisation from the all-plus start in the ordered phase.  At
     lambda = 0.01 (no closed form) the magnetisation must exceed the lambda = 0 run's.
-    Both encodings share seeds, so their trajectories (and observables) are identical."""
+    Both encodings share seeds, so their trajectories (and observables) are identical.
+    The q in {4, 8, 16} rows run int8 only and longer: an aligned spin flips with
+    probability about e^{-2 beta (q - 2J)} per half step, so the run is `steps` times
+    max(1, e^{2 beta (q - 4J)}) where that time scale is at most 1000 half steps; q = 16
+    (e^{2 beta (q - 2J)} ~ 10^5 - 10^6) runs `steps` and is reported, not compared."""
     with open(REFERENCE_FILE) as f:
         refs = {(r["q"], r["beta"]): r for r in json.load(f)["points"]}
     cases = [(lam, q) for lam in (0.0, 0.01) for q in C2_QS] + [(0.0, q) for q in C2_ONSAGER_QS]
@@ -558,15 +563,24 @@ def run_config2(S, stream, torch, L=C2_L, steps=C2_STEPS, burn=C2_BURN, chunk=C2
     mags = {}
     idx = 0
     for lam, q in cases:
+        extension = q in C2_ONSAGER_QS
+        encs = (("int8", S.INT8),) if extension else (("int8", S.INT8), ("packed", S.PACKED))
         for beta in C2_BETAS:
+            # an aligned spin flips with probability ~ e^{-2 beta (q - 2J)} per half step:
+            # large q needs proportionally longer runs (q = 16 is out of reach)
+            tau0 = math.exp(2.0 * beta * max(q - 2.0, 0.0))
+            reachable = tau0 <= 1000.0
+            n_steps = int(steps * max(1.0, math.exp(2.0 * beta * (q - 4.0)))) if reachable \
+                else steps
+            n_burn = n_steps - (steps - burn)
             for start in ("plus", "random"):
                 seed = W.BASE_SEED + 4000 + idx
                 idx += 1
-                for name, enc in (("int8", S.INT8), ("packed", S.PACKED)):
+                for name, enc in encs:
                     p = S.Problem(S.LATTICE, enc, 1, beta, q, L=L, J=1.0, lambda_const=lam,
                                   init=1 if start == "plus" else 0)
                     c = S.shaken_init(p, seed, stream)
-                    dt = _timed(torch, stream, lambda: S.shaken_step(c, burn))
+                    dt = _timed(torch, stream, lambda: S.shaken_step(c, n_burn))
                     E, M = [], []
                     for _ in range((steps - burn) // chunk):
                         S.shaken_step(c, chunk)
@@ -578,23 +592,27 @@ def run_config2(S, stream, torch, L=C2_L, steps=C2_STEPS, burn=C2_BURN, chunk=C2
                     se_e = E.std(ddof=1) / math.sqrt(E.size)
                     se_m = np.abs(M).std(ddof=1) / math.sqrt(M.size)
                     row = {"enc": name, "lambda": lam, "q": q, "beta": beta, "start": start,
-                           "updates_per_s": 2.0 * L * L * burn / dt,
+                           "steps": n_steps, "updates_per_s": 2.0 * L * L * n_burn / dt,
                            "energy_per_site": float(E.mean()), "energy_se": float(se_e),
                            "abs_m": float(np.abs(M).mean()), "m": float(M.mean()),
                            "abs_m_se": float(se_m)}
                     if lam == 0.0:
                         r = refs[(q, beta)]
                         bc = r["beta_c"]
-                        near = abs(beta / bc - 1.0) < 0.03
                         ordered = beta > bc
+                        # critical slowing down: within 5% below beta_c (3% above, where a
+                        # run from +1 stays in its phase) 2000 steps do not equilibrate
+                        near = (beta / bc - 1.0) < 0.03 if ordered else (1.0 - beta / bc) < 0.05
                         row.update({"energy_exact": r["energy_per_site"], "abs_m_exact": r["abs_m"],
-                                    "beta_c": bc, "near_critical": near})
+                                    "beta_c": bc, "near_critical": near,
+                                    "relaxation_reachable": reachable})
                         checks = []
-                        if not near and (start == "plus" or not ordered):
+                        ok_run = reachable and not near
+                        if ok_run and (start == "plus" or not ordered):
                             checks.append(abs(E.mean() - r["energy_per_site"]) < 4 * se_e + 1e-3)
-                        if not near and not ordered:
+                        if ok_run and not ordered and start == "random":
                             checks.append(np.abs(M).mean() < 5e-3)
-                        if not near and ordered and start == "plus":
+                        if ok_run and ordered and start == "plus":
                             checks.append(abs(np.abs(M).mean() - r["abs_m"]) < 4 * se_m + 2e-3)
                         row["compared"] = len(checks)
                         row["in_tolerance"] = bool(all(checks)) if checks else None
@@ -605,13 +623,16 @@ def run_config2(S, stream, torch, L=C2_L, steps=C2_STEPS, burn=C2_BURN, chunk=C2
                     runs.append(row)
     order_ok = [mags[(n, 0.01, q, b, st)] > mags[(n, 0.0, q, b, st)]
                 for (n, lam, q, b, st) in mags if lam == 0.0 and (n, 0.01, q, b, st) in mags]
-    same = all(abs(a["energy_per_site"] - b["energy_per_site"]) < 1e-12
-               and a["m"] == b["m"] for a, b in zip(runs[0::2], runs[1::2]))
+    pairs = [(a, b) for a, b in zip(runs, runs[1:])
+             if a["enc"] == "int8" and b["enc"] == "packed"
+             and all(a[k] == b[k] for k in ("lambda", "q", "beta", "start"))]
+    same = all(a["energy_per_site"] == b["energy_per_site"] and a["m"] == b["m"]
+               for a, b in pairs)
     rates = {e: [r["updates_per_s"] for r in runs if r["enc"] == e] for e in ("int8", "packed")}
     return {"L": L, "steps": steps, "timed_steps": burn, "sample_every": chunk,
             "runs": runs, "checks": n_checked, "failures": len(failures),
             "lambda_0p01_raises_m": f"{sum(order_ok)}/{len(order_ok)}",
-            "int8_equals_packed": bool(same),
+            "int8_equals_packed": bool(same), "int8_packed_pairs": len(pairs),
             "updates_per_s_median": {e: float(np.median(v)) for e, v in rates.items()},
             "updates_per_s_min": {e: float(np.min(v)) for e, v in rates.items()}}
 

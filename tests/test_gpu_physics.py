@@ -89,21 +89,27 @@ def test_small_field_magnetisation_matches_oracle_chain(S):
     assert abs(g.mean() - o.mean()) < 4 * se, (g.mean(), o.mean(), se)
 
 
-@pytest.mark.parametrize("q,beta", [(0.5, 0.48), (2.0, 0.40), (4.0, 0.48), (8.0, 0.48),
-                                    (16.0, 0.48)])
+@pytest.mark.parametrize("q,beta", [(0.5, 0.48), (2.0, 0.40), (4.0, 0.48), (8.0, 0.40),
+                                    (8.0, 0.48)])
 def test_plain_lattice_matches_exact_stationary_values(S, q, beta):
-    """One int8 lattice (1024 x 1024 torus, the whole-run banded path) started at +1,
-    lambda = 0: the energy per site and |m| after 1500 steps against the exact
-    stationary values of the shaken chain -- the anisotropic triangular Ising measure
-    it equals at lambda = 0 (Houtappel's free energy and the elliptic modulus, in
-    oracle/exact.py) -- within 4 standard errors + 1e-3 (energy) and 2e-3 (|m|)."""
+    """One int8 lattice (1024 x 1024 torus, the whole-run banded path), lambda = 0,
+    started at +1 in the ordered phase and from random spins in the disordered one
+    (where |m| would otherwise still be decaying from 1 at large q): the energy per site and |m| against the exact stationary values of the
+    shaken chain -- the anisotropic triangular Ising measure it equals at lambda = 0
+    (Houtappel's free energy and the elliptic modulus, in oracle/exact.py) -- within 4
+    standard errors + 1e-3 (energy) and 2e-3 (|m|).  Large q slows the chain: an
+    aligned spin flips with probability about e^{-2 beta (q - 2J)} per half step, so
+    the run is 1500 steps times max(1, e^{2 beta (q - 4J)})."""
     L = 1024
     E_ref, m_ref = exact.shaken_lattice_equilibrium(beta, 1.0, q)
-    ctx = S.shaken_init(lattice_problem(S, S.INT8, L, 1, beta, 1.0, q, 0.0, init=1), 31 + int(q))
-    S.shaken_step(ctx, 1500)
+    burn = int(1500 * max(1.0, np.exp(2 * beta * (q - 4.0))))
+    init = 1 if m_ref > 0.0 else 0
+    ctx = S.shaken_init(lattice_problem(S, S.INT8, L, 1, beta, 1.0, q, 0.0, init=init),
+                        31 + int(q))
+    S.shaken_step(ctx, burn)
     E, M = [], []
     for _ in range(20):
-        S.shaken_step(ctx, 25)
+        S.shaken_step(ctx, max(25, burn // 60))
         o = S.shaken_observables(ctx, 1)
         E.append(o["energy"][0] / (L * L))
         M.append(abs(o["magnetization"][0]))
