@@ -51,8 +51,9 @@ enum { SHAKEN_LATTICE = 0, SHAKEN_GRAPH = 1 };
 /* Spin encodings.
  *   INT8      lattice only: int8 [R][L][L] (+1/-1 bytes).
  *   PACKED    lattice only: uint32 [R][L][L/32], bit k of word (i, w) = site (i, 32w+k).
- *   MULTISPIN lattice: uint32 [R/32][L][L]; graph: uint32 [R/32][n]; bit k of a
- *             word = replica 32g+k.
+ *   MULTISPIN lattice: uint32 [R/32][L][L] (group g's lattice, then group g+1's);
+ *             graph: uint32 [n][R/32] (the group words of a vertex adjacent); bit k
+ *             of the word of group g = replica 32g+k.
  * INT8 and PACKED give bit-identical trajectories (same random stream). */
 enum { SHAKEN_INT8 = 0, SHAKEN_PACKED = 1, SHAKEN_MULTISPIN = 2 };
 

@@ -1,4 +1,4 @@
-// graph.cu -- half-step kernel of the shaken dynamics on an arbitrary graph
+// graph.cu -- half-step kernels of the shaken dynamics on an arbitrary graph
 // G = (V, E) (Sec. 2 of arXiv:1904.06257), multispin over replicas, and the
 // graph observables.
 //
@@ -6,25 +6,37 @@
 // half step 1 (P^{2->1}): h_x = sum_{y : (x -> y) in E^o} J_xy s'_y + q s'_x + lambda_x
 // (the fields below Eq. (ham21)); tau_x = +1 with probability e^{beta h} / 2cosh(beta h).
 //
-// Layout: spins uint32 [R/32][n], bit k of word x of group g = replica 32g+k.
-// In-CSR (sources of edges into x) for half 0, out-CSR (heads of edges out of
-// x) for half 1; with integer couplings the sign of J is bit 31 of the column.
-// One thread owns one (vertex, group) word and its 32 lanes.
+// Layout: spins uint32 [n][G], word x * G + g = vertex x of replicas 32 g .. 32 g + 31
+// (bit k = replica 32 g + k).  In-CSR (sources of edges into x) for half 0, out-CSR
+// (heads of edges out of x) for half 1; with integer couplings the sign of J is bit
+// 31 of the column.  One thread owns one (vertex, group) word and its 32 lanes; the
+// group words of a vertex are owned by adjacent threads, so they share the column
+// loads and the neighbours' words arrive in common sectors.
 //
-// Draws: lane k of word (x, g) uses u_k = W_k, the k-th of the 32 words
-// Philox(key, (x, g, t, half + 2(k>>2)))[k & 3].
-//
-// Decision, integer couplings (exact): tau_k = +1 iff u_k < T(h_k, beta_k)
-// with T = floor(2^32 / (1 + e^{-2 beta h})) in fp64 and h = (s + q sigma) +
-// lambda_x.  An fp32 evaluation of u (1 + e^{-2 beta h}) / 2^32 decides directly
-// when it is farther than its error bound from 1 (see decide_int); otherwise T is
-// computed in fp64.
-// Real couplings (fp32 sums): tau_k = +1 iff u_k (1 + e~) / 2^32 < 1 (statistical parity).
+// Integer couplings (exact).  Draws by bit planes: plane j of word (x, g) is
+// W_j = Philox(key, (x, g, t, half + 2(j>>2)))[j & 3], and lane k's draw has bit 31-j
+// equal to bit k of W_j.  Lane k is +1 iff u_k < T = floor(2^32 / (1 + e^{-2 beta h})).
+// With one beta on every lane of a job (anneals), the threshold depends on the lane
+// only through its class (a, sigma): a = number of in-neighbours with J s = +1, so
+// h = (2a - d) + q sigma + lambda_x.  The threads of a vertex compute the top byte of
+// T for each class of the vertex once (fp32 with a proven error bound; a class whose
+// top byte the bound does not fix is marked), the lanes pick theirs by byte permutes,
+// a bit transpose turns the 32 bytes into 8 threshold planes, and planes 0..7 (two
+// Philox calls) decide every lane whose draw differs from its threshold in the top
+// byte.  The rest (about 2^-8 of the lanes) is decided one lane at a time: more
+// planes against the fp32 bounds on T, and T in fp64 where even they do not decide.
+// Real couplings (fp32 sums): direct draws u_k = W_k and tau_k = +1 iff
+// u_k (1 + e~) / 2^32 < 1 (statistical parity).
+// Vertices of degree above 255 are done by a whole warp (edge list split over the
+// lanes, per-replica counts or fields combined by a butterfly of shuffles).
 #include <cstdint>
 
 #include "shaken_internal.cuh"
 
 namespace shk {
+
+constexpr int kTableDeg = 15;  // per-vertex class tables for degree <= 15
+constexpr int kHubDeg = 255;   // byte counters for degree <= 255; above: one warp per word
 
 // 2^x (PTX ex2.approx: relative error below 2^-22 over the range used here).
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -33,175 +45,382 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-// Exact decision for integer couplings (see the header): +1 iff u < T(h, beta).
-// With e~ = 2^(kb h~), kb = -2 beta log2(e), the condition u < 2^32 / (1 + e) is
-// tested as t1 = (u + 1) 2^-32 (1 + e~) < 1 - eps (certainly +1) or
-// t0 = u 2^-32 (1 + e~) > 1 + eps (certainly -1); eps = 2^-18 + 2^-18 beta B with
-// B >= |s| + |q| + |lambda| + 1 is at least three times the fp32 error of t
-// (rounding of h~, kb h~, ex2, the two products); in between, T is computed in fp64.
-// The fp64 threshold test, out of line: it is reached with probability about
-// 2^-17 (1 + beta B) per update, so it should not bloat the hot loop.
-__device__ __noinline__ bool decide_exact(uint32_t u, int s, int sigma, double q, float lam,
-                                          double beta) {
-  const double h = field_h(1.0, s, q, sigma, (double)lam);
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Bounds lo <= T <= hi on T = floor(2^32 / (1 + 2^x)), x = kb h, kb = -2 beta log2(e),
+// from the fp32 field hf.  hf carries at most four roundings of magnitude <= B
+// (B = d + |q| + |lambda| + 1), so kb hf is within |kb| B 2^-22 of kb h; with the
+// rounding of kb hf, ex2.approx (2^-22), 1 + e, the reciprocal and the product, T~ is
+// within min(T~, 2^32 - T~) eps + 2^8 of 2^32 p, eps = 2^-21 (2 + |x| + |kb| B)
+// bounding twice the relative error; the margin 1024 also covers the floor.
+__device__ __forceinline__ void t_bounds(float hf, float kb, float kbB, float& lo, float& hi) {
+  const float x = kb * hf;
+  const float e = ex2_approx(x);
+  const float T = 4294967296.0f * rcp_approx(1.0f + e);
+  const float m = fminf(T, 4294967296.0f - T);
+  const float eps = 4.76837158203125e-07f * (2.0f + fabsf(x) + kbB);
+  const float D = fmaf(m, eps, 1024.0f);
+  lo = fmaxf(T - D, 0.0f);
+  hi = fminf(T + D, 4294967296.0f);
+}
+
+// Top byte of a value in [0, 2^32] (2^32, i.e. T that always accepts, maps to 255: a
+// lane whose draw has top byte 255 is then left to the per-lane decision).
+__device__ __forceinline__ uint32_t top_byte(float v) {
+  const uint32_t b = __float2uint_rz(v * 5.9604644775390625e-08f);
+  return b > 255u ? 255u : b;
+}
+
+// Bit transpose: R[m] byte i = threshold byte of lane m + 8 i  ->  P[j] bit k = bit 7 - j
+// of the byte of lane k (plane j, most significant first).  Two 4 x 4 byte transposes
+// gather the 8 x 8 bit blocks of lanes 8 i .. 8 i + 7, a three-stage delta swap
+// transposes each block, two more byte transposes scatter the rows into planes.
+__device__ __forceinline__ void t44(uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d) {
+  const uint32_t t0 = __byte_perm(a, b, 0x5140), t1 = __byte_perm(a, b, 0x7362);
+  const uint32_t t2 = __byte_perm(c, d, 0x5140), t3 = __byte_perm(c, d, 0x7362);
+  a = __byte_perm(t0, t2, 0x5410);
+  b = __byte_perm(t0, t2, 0x7632);
+  c = __byte_perm(t1, t3, 0x5410);
+  d = __byte_perm(t1, t3, 0x7632);
+}
+
+__device__ __forceinline__ void t88(uint32_t& lo, uint32_t& hi) {
+  uint32_t t;
+  t = (lo ^ (lo >> 7)) & 0x00AA00AAu;
+  lo ^= t ^ (t << 7);
+  t = (hi ^ (hi >> 7)) & 0x00AA00AAu;
+  hi ^= t ^ (t << 7);
+  t = (lo ^ (lo >> 14)) & 0x0000CCCCu;
+  lo ^= t ^ (t << 14);
+  t = (hi ^ (hi >> 14)) & 0x0000CCCCu;
+  hi ^= t ^ (t << 14);
+  t = (lo ^ __funnelshift_r(lo, hi, 28)) & 0xF0F0F0F0u;
+  lo ^= t ^ (t << 28);
+  hi ^= t >> 4;
+}
+
+__device__ __forceinline__ void bytes_to_planes(uint32_t (&R)[8], uint32_t (&P)[8]) {
+  t44(R[0], R[1], R[2], R[3]);
+  t44(R[4], R[5], R[6], R[7]);
+  t88(R[0], R[4]);
+  t88(R[1], R[5]);
+  t88(R[2], R[6]);
+  t88(R[3], R[7]);
+  t44(R[0], R[1], R[2], R[3]);
+  t44(R[4], R[5], R[6], R[7]);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) P[j] = R[7 - j];
+}
+
+// Bits k of eight plane words, most significant first.
+__device__ __forceinline__ uint32_t lane_byte(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3,
+                                              uint32_t w4, uint32_t w5, uint32_t w6, uint32_t w7,
+                                              int k) {
+  return (((w0 >> k) & 1u) << 7) | (((w1 >> k) & 1u) << 6) | (((w2 >> k) & 1u) << 5) |
+         (((w3 >> k) & 1u) << 4) | (((w4 >> k) & 1u) << 3) | (((w5 >> k) & 1u) << 2) |
+         (((w6 >> k) & 1u) << 1) | ((w7 >> k) & 1u);
+}
+
+// Decision of one lane left undecided by the head (its draw's top byte u8 equals the
+// threshold's, or its class's top byte was not certain): planes 8..15 and then 16..31
+// against the fp32 bounds on T, and T in fp64 where the bounds do not decide
+// (force_exact: straight to fp64).  Out of line: reached by about 2^-8 of the lanes.
+__device__ __noinline__ bool decide_lane(uint32_t key0, uint32_t key1, uint32_t x, uint32_t g,
+                                         uint32_t t, uint32_t typ, int k, uint32_t u8, int a,
+                                         int d, int sig, float bp, float bm, double q, float lam,
+                                         float kb, float kbB, double beta, bool force_exact) {
+  float lo = 0.0f, hi = 4294967296.0f;
+  if (!force_exact) {
+    t_bounds(fmaf(2.0f, (float)a, sig ? bp : bm), kb, kbB, lo, hi);
+    if ((float)(u8 + 1u) * 16777216.0f <= lo) return true;  // u < (u8 + 1) 2^24 <= T
+    if ((float)u8 * 16777216.0f >= hi) return false;        // u >= u8 2^24 >= T
+  }
+  const PhKey K = ph_key(key0, key1);
+  const uint4 c2 = ph_call(K, x, g, t, typ + 4u), c3 = ph_call(K, x, g, t, typ + 6u);
+  const uint32_t u16 = (u8 << 8) | lane_byte(c2.x, c2.y, c2.z, c2.w, c3.x, c3.y, c3.z, c3.w, k);
+  if (!force_exact) {
+    if ((float)(u16 + 1u) * 65536.0f <= lo) return true;
+    if ((float)u16 * 65536.0f >= hi) return false;
+  }
+  const uint4 c4 = ph_call(K, x, g, t, typ + 8u), c5 = ph_call(K, x, g, t, typ + 10u);
+  const uint4 c6 = ph_call(K, x, g, t, typ + 12u), c7 = ph_call(K, x, g, t, typ + 14u);
+  const uint32_t u = (u16 << 16) |
+                     (lane_byte(c4.x, c4.y, c4.z, c4.w, c5.x, c5.y, c5.z, c5.w, k) << 8) |
+                     lane_byte(c6.x, c6.y, c6.z, c6.w, c7.x, c7.y, c7.z, c7.w, k);
+  if (!force_exact) {
+    if ((double)u < (double)lo) return true;
+    if ((double)u >= (double)hi) return false;
+  }
+  const double h = field_h(1.0, 2 * a - d, q, sig ? 1 : -1, (double)lam);
   return (unsigned long long)u < threshold_T(h, beta);
 }
 
-__device__ __forceinline__ bool decide_int(uint32_t u, int s, int sigma, float qf, double q,
-                                           float lam, float kb, float eps, double beta,
-                                           bool exact_always) {
-  const float hf = __fadd_rn(__fadd_rn((float)s, sigma > 0 ? qf : -qf), lam);
-  const float onep = 1.0f + ex2_approx(kb * hf);
-  const float uf = __uint2float_rn(u) * 2.3283064365386963e-10f;
-  if (!exact_always) {
-    if ((uf + 2.3283064365386963e-10f) * onep < 1.0f - eps) return true;
-    if (uf * onep > 1.0f + eps) return false;
+// Threshold bytes of lanes m, m + 8, m + 16, m + 24 one lane at a time (per-lane betas,
+// or a degree above the class tables): .x = bytes (byte i for lane m + 8 i), .y = the
+// lanes whose top byte is not certain (bit k).
+__device__ __noinline__ uint2 lane_bytes(uint32_t cnt, uint32_t S, int m, float bp, float bm,
+                                         float B, const double* __restrict__ beta_lane,
+                                         float kb_uni, bool uni) {
+  float kbl[4];
+  if (uni) {  // (kept out of the lane loop: an fp64 product per lane is slow here)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) kbl[i] = kb_uni;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) kbl[i] = (float)(-2.0 * beta_lane[m + 8 * i] * 1.4426950408889634);
   }
-  return decide_exact(u, s, sigma, q, lam, beta);
-}
-
-// Number of neighbours y with J_xy s_y = +1 on lane k (slow path, one lane).
-__device__ __noinline__ int lane_count(const uint32_t* __restrict__ src,
-                                       const uint32_t* __restrict__ col, int p0, int p1, int k) {
-  int cnt = 0;
-  for (int e = p0; e < p1; ++e) {
-    const uint32_t cv = col[e];
-    cnt += (int)(((src[cv & 0x7fffffffu] ^ (0u - (cv >> 31))) >> k) & 1u);
+  uint32_t r = 0u, am = 0u;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int k = m + 8 * i;
+    const int a = (int)((cnt >> (8 * i)) & 0xFFu);
+    float lo, hi;
+    t_bounds(fmaf(2.0f, (float)a, ((S >> k) & 1u) ? bp : bm), kbl[i], fabsf(kbl[i]) * B, lo, hi);
+    const uint32_t bl = top_byte(lo), bh = top_byte(hi);
+    r |= bh << (8 * i);
+    am |= (uint32_t)(bl != bh) << k;
   }
-  return cnt;
+  return make_uint2(r, am);
 }
 
-// u_k of lane k of word (x, b) (slow path, one lane).
-__device__ __noinline__ uint32_t lane_draw(uint32_t key0, uint32_t key1, uint32_t x, uint32_t b,
-                                           uint32_t t, uint32_t typ, int k) {
-  const uint4 w = ph_call(ph_key(key0, key1), x, b, t, typ + 2u * (uint32_t)(k >> 2));
-  const int i = k & 3;
-  return i == 0 ? w.x : i == 1 ? w.y : i == 2 ? w.z : w.w;
-}
-
-struct GraphShared;
-
-// Fast decisions of the 32 lanes of a word (integer couplings, byte counters C):
-// lane k = 8 c2 + m takes byte c2 of C[m] as its count and u_k from call k >> 2.
-// With e~ = 2^(kb h~) the lane is +1 if (u + 1)(1 + e~) < 2^32 (1 - eps) and -1 if
-// u (1 + e~) > 2^32 (1 + eps); otherwise its bit is set in `und` for the fp64 test.
-// eps = 2^-18 + 2^-18 beta B, B = d + |q| + |lambda| + 1, is at least five times the
-// fp32 error of the compared products (h~: three roundings of magnitude <= B;
-// kb h~ -- with one beta on all lanes kb (2 cnt) + kb base, kb base rounded once,
-// in one fused multiply-add, the same bound; ex2.approx, relative error 2^-22;
-// 1 + e~; u to float; the product).
+// Real couplings: the decisions of the 32 lanes from their fp32 fields h[k] (direct
+// draws u_k = W_k of calls k >> 2); UNI: one beta on every lane (no per-lane fp64).
 template <bool UNI>
-__device__ __forceinline__ void int_lanes(const uint32_t (&C)[8], uint32_t S, const PhKey& K,
-                                          uint32_t x, uint32_t b, uint32_t t, uint32_t typ,
-                                          float bp, float bm, float a0, float B,
-                                          const GraphShared& sh, bool fuse, float (*acc)[32],
-                                          int lane, uint32_t& res, uint32_t& und);
+__device__ __forceinline__ uint32_t real_lanes(const float (&h)[32], uint32_t S, float qf,
+                                               float lam, float kbu,
+                                               const double* __restrict__ beta_g,
+                                               const PhKey& K, const PhShared& ph, uint32_t x,
+                                               uint32_t typ, bool fuse, float (*acc)[32],
+                                               int lane) {
+  uint32_t res = 0u;
+  uint4 w = make_uint4(0, 0, 0, 0);
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    if ((k & 3) == 0) w = ph_call_shared(K, ph, x, typ + 2u * (uint32_t)(k >> 2));
+    const uint32_t u = (k & 3) == 0 ? w.x : (k & 3) == 1 ? w.y : (k & 3) == 2 ? w.z : w.w;
+    const bool up = (S >> k) & 1u;
+    const float kb = UNI ? kbu : (float)(-2.0 * beta_g[k] * 1.4426950408889634);
+    const float hk = __fadd_rn(__fadd_rn(h[k], up ? qf : -qf), lam);
+    const float onep = 1.0f + ex2_approx(kb * hk);
+    const float uf = __uint2float_rn(u) * 2.3283064365386963e-10f;
+    res |= (uint32_t)(uf * onep < 1.0f) << k;
+    if (fuse) {
+      const float a = h[k] + 2.0f * lam;
+      acc[k][lane] += up ? a : -a;
+    }
+  }
+  return res;
+}
 
-struct GraphShared {
-  float kb[32];   // -2 beta_k log2(e) per lane (anneal: the step's beta on every lane)
-  float epc[32];  // 2^-18 beta_k per lane
-  double beta[32];
-  PhShared ph;    // Philox rounds shared by every call of the job at this step
-  int uni;        // every lane has the same beta
-  float acc[kTile / 32][32][32];  // [warp][replica lane k][thread lane]: tracking sums
-  float red[kTile / 32][32];
+// Per-replica partial values v[0..31] of the 32 lanes of a warp -> lane k holds the
+// sum over the warp of v[k] in v[0] (each level halves the values a lane keeps).
+template <typename V>
+__device__ __forceinline__ V warp_transpose_sum(V (&v)[32], int lane) {
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool up = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const V send = up ? v[i] : v[i + s];
+      const V keep = up ? v[i + s] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  return v[0];
+}
+
+struct HubArgs {
+  uint32_t x, g, t, typ;
+  bool fuse, uni;
+  double beta_u;
 };
 
-template <bool UNI>
-__device__ __forceinline__ void int_lanes(const uint32_t (&C)[8], uint32_t S, const PhKey& K,
-                                          uint32_t x, uint32_t b, uint32_t t, uint32_t typ,
-                                          float bp, float bm, float a0, float B,
-                                          const GraphShared& sh, bool fuse, float (*acc)[32],
-                                          int lane, uint32_t& res, uint32_t& und) {
-  const float two32 = 4294967296.0f;
-  float kb2 = 0.0f, kbp = 0.0f, kbm = 0.0f, lo0 = 0.0f, hi0 = 0.0f;
-  if (UNI) {  // one beta: the exponent kb (2 cnt + base) is one fused multiply-add
-    const float kb0 = sh.kb[0];
-    kb2 = 2.0f * kb0;
-    kbp = kb0 * bp;
-    kbm = kb0 * bm;
-    const float eps = 3.814697265625e-06f + sh.epc[0] * B;
-    lo0 = two32 * (1.0f - eps);
-    hi0 = two32 * (1.0f + eps);
-  }
-#pragma unroll 1
-  for (uint32_t c2 = 0; c2 < 4u; ++c2) {
-    const uint4 w0 = ph_call_shared(K, sh.ph, x, typ + 4u * c2);       // call 2 c2
-    const uint4 w1 = ph_call_shared(K, sh.ph, x, typ + 4u * c2 + 2u);  // call 2 c2 + 1
-    const uint32_t uw[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-    const uint32_t selb = 0x7540u + c2;  // byte c2 of C[m] under the exponent byte 0x4B
-    const uint32_t s8 = S >> (8u * c2);  // sigma bits of lanes 8 c2 .. 8 c2 + 7
-    uint32_t r8 = 0u, u8 = 0u;           // their decisions and undecided flags
+// One word (x, g) of a vertex of degree above kHubDeg, done by the whole warp: lane l
+// takes the edges p0 + l, p0 + l + 32, ...; the per-replica counts (integer) or fields
+// (real) are combined across the warp so that lane k holds replica k's, and lane k
+// decides replica k (integer: T in fp64 and the plane-assembled draw; real: the fp32
+// test of the direct draw).  Returns the word (every lane).
+template <bool INTEGER>
+__device__ __noinline__ uint32_t hub_word(const GraphJob& J, HubArgs A, uint32_t half,
+                                          int lane) {
+  const uint32_t* src = half == 0u ? J.A : J.B;
+  const int32_t* ptr = A.typ == 0u ? J.in_ptr : J.out_ptr;
+  const uint32_t* col = A.typ == 0u ? J.in_col : J.out_col;
+  const float* Jr = A.typ == 0u ? J.in_J : J.out_J;
+  const int32_t p0 = ptr[A.x], p1 = ptr[A.x + 1];
+  const int d = p1 - p0;
+  const uint32_t G = J.G;
+  const uint32_t S = src[(size_t)A.x * G + A.g];
+  const uint32_t F = J.frozen != nullptr ? J.frozen[A.x] : 0u;
+  const float lam = J.lambda != nullptr ? J.lambda[A.x] : J.lambda_c;
+  const double beta = A.uni ? A.beta_u : J.beta_lane[32u * A.g + (uint32_t)lane];
+  const int sig = (int)((S >> lane) & 1u);
+  const PhKey K = ph_key(J.key0, J.key1);
+  bool tau;
+  float contrib;
+  if (INTEGER) {
+    uint32_t v[32];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int k = 8 * (int)c2 + m;
-      // count as a float: 2^23 + cnt exactly, minus 2^23
-      const float cf = __fsub_rn(__int_as_float((int)__byte_perm(C[m], 0x4B000000u, selb)),
-                                 8388608.0f);
-      const bool up = (s8 >> m) & 1u;
-      float x, lo = lo0, hi = hi0;
-      if (UNI) {
-        x = __fmaf_rn(kb2, cf, up ? kbp : kbm);
-      } else {
-        const float hf = __fmaf_rn(2.0f, cf, up ? bp : bm);
-        x = sh.kb[k] * hf;
-        const float eps = 3.814697265625e-06f + sh.epc[k] * B;
-        lo = two32 * (1.0f - eps);
-        hi = two32 * (1.0f + eps);
+    for (int k = 0; k < 32; ++k) v[k] = 0u;
+    // 16-bit counters (lanes m and m + 16), widened every 65535 edges of this lane
+    for (int e0 = p0; e0 < p1; e0 += 32 * 65535) {
+      const int e1 = min(p1, e0 + 32 * 65535);
+      uint32_t c16[16];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) c16[m] = 0u;
+      for (int e = e0 + lane; e < e1; e += 32) {
+        const uint32_t cv = __ldg(col + e);
+        const uint32_t w = __ldg(src + (size_t)(cv & 0x7fffffffu) * G + A.g) ^ (0u - (cv >> 31));
+#pragma unroll
+        for (int m = 0; m < 16; ++m) c16[m] += (w >> m) & 0x00010001u;
       }
-      const float onep = 1.0f + ex2_approx(x);
-      const float uf = __uint2float_rn(uw[m]);
-      const bool plus = __fmaf_rn(uf, onep, onep) < lo;
-      const bool minus = uf * onep > hi;
-      r8 |= (uint32_t)plus << m;
-      u8 |= (uint32_t)(!plus && !minus) << m;
-      if (fuse) {
-        const float a = __fmaf_rn(2.0f, cf, a0);
-        acc[k][lane] += up ? a : -a;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        v[m] += c16[m] & 0xFFFFu;
+        v[m + 16] += c16[m] >> 16;
       }
     }
-    res |= r8 << (8u * c2);
-    und |= u8 << (8u * c2);
+    const int a = (int)warp_transpose_sum(v, lane);
+    // planes: lane c < 8 makes call c, then lane k gathers bit k of each plane
+    const uint4 w = ph_call(K, A.x, A.g, A.t, A.typ + 2u * (uint32_t)(lane & 7));
+    uint32_t u = 0u;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const uint32_t c = (j & 3) == 0 ? w.x : (j & 3) == 1 ? w.y : (j & 3) == 2 ? w.z : w.w;
+      u |= ((__shfl_sync(0xffffffffu, c, j >> 2) >> lane) & 1u) << (31 - j);
+    }
+    const double h = field_h(1.0, 2 * a - d, J.q, sig ? 1 : -1, (double)lam);
+    tau = (unsigned long long)u < threshold_T(h, beta);
+    contrib = (float)(2 * a - d) + 2.0f * lam;
+  } else {
+    float v[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = 0.0f;
+    for (int e = p0 + lane; e < p1; e += 32) {
+      const uint32_t y = __ldg(col + e) & 0x7fffffffu;
+      const float Jv = __ldg(Jr + e);
+      const uint32_t wy = __ldg(src + (size_t)y * G + A.g);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] += ((wy >> k) & 1u) ? Jv : -Jv;
+    }
+    const float hs = warp_transpose_sum(v, lane);
+    const uint4 w = ph_call(K, A.x, A.g, A.t, A.typ + 2u * (uint32_t)(lane >> 2));
+    const uint32_t u = (lane & 3) == 0 ? w.x : (lane & 3) == 1 ? w.y : (lane & 3) == 2 ? w.z : w.w;
+    const float qf = (float)J.q;
+    const float hk = __fadd_rn(__fadd_rn(hs, sig ? qf : -qf), lam);
+    const float onep = 1.0f + ex2_approx((float)(-2.0 * beta * 1.4426950408889634) * hk);
+    tau = __uint2float_rn(u) * 2.3283064365386963e-10f * onep < 1.0f;
+    contrib = hs + 2.0f * lam;
   }
+  const uint32_t res = __ballot_sync(0xffffffffu, tau) | F;
+  if (A.fuse) {  // -H(sigma_t) share of replica (g, lane): sigma (field sum + 2 lambda)
+    const float c = sig ? contrib : -contrib;
+    if (c != 0.0f)
+      atomicAdd(J.sums + (size_t)(32u * A.g + (uint32_t)lane) * kNumSums + kSumE, (double)c);
+  }
+  return res;
 }
 
-// One thread owns one (vertex, group) word.  Each block walks a contiguous range
-// of tiles (one job per tile).  With tracking on, half 0 also accumulates per
-// replica sum_x sigma_x (s_x + 2 lambda_x), i.e. -H(sigma_t) (Eq. (ham1)), reduced
-// when the block leaves a job.
+// A lane left undecided by the head of its word, waiting in its warp's queue.
+struct Pend {
+  uint32_t x, g;
+  uint32_t info;  // lane k (bits 0..4) | sigma (5) | top byte of u (6..13) | fp64 only (14)
+  uint32_t pad;
+};
+
+constexpr int kQueue = 64;  // queue entries per warp
+
+struct RoundArgs {
+  const uint32_t* src;  // the half step's input configuration
+  uint32_t t, typ;
+  bool uni;
+  double beta_u;
+};
+
+struct GraphShared {
+  __align__(16) uint32_t tb[kTile][8];  // per vertex slot: top bytes of T by class (byte
+                                        // a + 16 sigma), read as two 16-byte vectors
+  GraphJob J;       // the current job's descriptor
+  RoundArgs ra;     // the current job's step: input, t, update type, beta
+  uint32_t* dst;    // the half step's output configuration
+  float kb_u;       // -2 beta_u log2(e)
+  uint32_t skip, fuse;
+  uint32_t amb[kTile];    // per vertex slot: classes whose top byte is not certain
+  Pend q[kTile / 32][kQueue];
+  uint32_t wp[kTile][8];  // planes 0..7 of a word with lanes waiting to be queued
+  float acc[kTile / 32][32][32];  // tracking sums [warp][replica lane k][thread lane]
+};
+
+// One round of queued lanes: lane i decides entry i (i < cnt) and sets its bit in the
+// stored word if it is +1.  The words were stored by their owners before the round.
+__device__ __forceinline__ void queue_round(const GraphJob& J, const Pend* q, int cnt,
+                                            uint32_t* dst, const RoundArgs& A, int lane) {
+  __syncwarp();
+  if (lane < cnt) {
+    const Pend e = q[lane];
+    const int k = (int)(e.info & 31u);
+    const int sig = (int)((e.info >> 5) & 1u);
+    const uint32_t u8 = (e.info >> 6) & 0xFFu;
+    const int32_t* ptr = A.typ == 0u ? J.in_ptr : J.out_ptr;
+    const uint32_t* col = A.typ == 0u ? J.in_col : J.out_col;
+    const int p0 = __ldg(ptr + e.x), d = __ldg(ptr + e.x + 1) - p0;
+    int a = 0;  // neighbours with J_xy s_y = +1 on lane k
+    for (int i = p0; i < p0 + d; ++i) {
+      const uint32_t cv = __ldg(col + i);
+      a += (int)(((__ldg(A.src + (size_t)(cv & 0x7fffffffu) * J.G + e.g) ^ (0u - (cv >> 31))) >>
+                  k) & 1u);
+    }
+    const float lam = J.lambda != nullptr ? __ldg(J.lambda + e.x) : J.lambda_c;
+    const float qf = (float)J.q;
+    const float lmd = __fadd_rn(lam, -(float)d);
+    const float bp = __fadd_rn(lmd, qf), bm = __fadd_rn(lmd, -qf);
+    const float B = (float)d + fabsf(qf) + fabsf(lam) + 1.0f;
+    const double beta = A.uni ? A.beta_u : J.beta_lane[32u * e.g + (uint32_t)k];
+    const float kb = (float)(-2.0 * beta * 1.4426950408889634);
+    if (decide_lane(J.key0, J.key1, e.x, e.g, A.t, A.typ, k, u8, a, d, sig, bp, bm, J.q, lam,
+                    kb, fabsf(kb) * B, beta, ((e.info >> 14) & 1u) != 0u))
+      atomicOr(dst + (size_t)e.x * J.G + e.g, 1u << k);
+  }
+  __syncwarp();
+}
+
+// One thread owns one (vertex, group) word.  Each block walks a contiguous range of
+// tiles (one job per tile, kTile / Gp vertices of the half step's degree order x Gp
+// threads).  Lanes the head leaves undecided wait in a per-warp queue and are decided
+// 32 at a time.  With tracking on, half 0 also accumulates per replica
+// sum_x sigma_x (s_x + 2 lambda_x), i.e. -H(sigma_t) (Eq. (ham1)), reduced when the
+// block leaves a job.
 template <bool INTEGER>
 __global__ void __launch_bounds__(kTile, 3) graph_half_kernel(const GraphJob* __restrict__ jobs,
                                                            const Tile* __restrict__ tiles,
                                                            int n_tiles, uint32_t half,
                                                            int exact_always) {
   __shared__ GraphShared sh;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tb = (int)(((long long)blockIdx.x * n_tiles) / gridDim.x);
   const int te = (int)(((long long)(blockIdx.x + 1) * n_tiles) / gridDim.x);
+  const GraphJob& J = sh.J;
   int cur_job = -1;
-  bool fuse = false, skip = false;
-  uint32_t t = 0, typ = 0;
-  double* fuse_dst = nullptr;
+  int qn = 0;  // entries in this warp's queue (the same in every lane)
+  Pend* q = sh.q[warp];
   float(*acc)[32] = sh.acc[warp];  // acc[k][lane]: this thread's sum for replica lane k
 #pragma unroll
   for (int k = 0; k < 32; ++k) acc[k][lane] = 0.0f;
 
   auto flush = [&]() {
-    // block totals per replica lane -> step sums of the job's 32 replicas
+    // per replica (group offset go', lane k): the sum over the threads of group go'
     __syncthreads();
-    {
-      const int k = threadIdx.x & 31, w = threadIdx.x >> 5;  // row (w, k) of the accumulators
+    const uint32_t Gj = J.Gj, Gp = J.Gp;
+    for (uint32_t o = (uint32_t)tid; o < 32u * Gj; o += kTile) {
+      const uint32_t gg = o >> 5, k = o & 31u;
       float v = 0.0f;
-#pragma unroll 8
-      for (int l = 0; l < 32; ++l) v += sh.acc[w][k][(l + k) & 31];
-      sh.red[w][k] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      float tot = 0.0f;
-#pragma unroll
-      for (int w = 0; w < kTile / 32; ++w) tot += sh.red[w][threadIdx.x];
-      if (tot != 0.0f) atomicAdd(fuse_dst + (size_t)threadIdx.x * kNumSums + kSumE, (double)tot);
+      for (uint32_t s = gg; s < (uint32_t)kTile; s += Gp) v += sh.acc[s >> 5][k][s & 31u];
+      if (v != 0.0f)
+        atomicAdd(J.sums + (size_t)(32u * (J.g0 + gg) + k) * kNumSums + kSumE, (double)v);
     }
     __syncthreads();
 #pragma unroll
@@ -210,145 +429,270 @@ __global__ void __launch_bounds__(kTile, 3) graph_half_kernel(const GraphJob* __
 
   for (int ti = tb; ti < te; ++ti) {
     const Tile tl = tiles[ti];
-    const GraphJob& J = jobs[tl.job];
     if ((int)tl.job != cur_job) {
-      if (fuse) flush();
-      __syncthreads();  // shared per-job constants are about to change
+      if (cur_job >= 0) {
+        if (qn > 0) queue_round(J, q, qn, sh.dst, sh.ra, lane);  // the old job's entries
+        qn = 0;
+        if (sh.fuse) flush();
+      }
+      __syncthreads();  // shared per-job values are about to change
+      if (tid < (int)(sizeof(GraphJob) / 4))
+        reinterpret_cast<uint32_t*>(&sh.J)[tid] =
+            reinterpret_cast<const uint32_t*>(jobs + tl.job)[tid];
+      __syncthreads();
       const CtxDev* cd = J.cd;
-      t = cd->step;
-      typ = half ^ cd->order;
-      skip = t >= cd->t_end;
-      fuse = !skip && half == 0u && cd->tracking && !cd->record && J.sums != nullptr;
-      fuse_dst = J.sums;
-      if (threadIdx.x < 32) {
-        double beta;
-        if (J.beta_sched != nullptr && cd->anneal_len != 0u) {
-          uint32_t k = t - cd->anneal_t0;
-          if (k >= cd->anneal_len) k = cd->anneal_len - 1u;
-          beta = J.beta_sched[k];
-        } else {
-          beta = J.beta_lane[threadIdx.x];
-        }
-        sh.beta[threadIdx.x] = beta;
-        sh.kb[threadIdx.x] = (float)(-2.0 * beta * 1.4426950408889634);
-        sh.epc[threadIdx.x] = (float)beta * 3.814697265625e-06f;
-        const double b0 = __shfl_sync(0xffffffffu, beta, 0);
-        const bool same = __all_sync(0xffffffffu, beta == b0);
-        if (threadIdx.x == 0) {
-          sh.uni = same ? 1 : 0;
-          sh.ph = ph_shared(ph_key(J.key0, J.key1), J.b, t);
-        }
+      const uint32_t t = cd->step;
+      // one beta on every replica of the job at this step?
+      const bool anneal = J.beta_sched != nullptr && cd->anneal_len != 0u;
+      double b0;
+      if (anneal) {
+        uint32_t k = t - cd->anneal_t0;
+        if (k >= cd->anneal_len) k = cd->anneal_len - 1u;
+        b0 = J.beta_sched[k];
+      } else {
+        b0 = J.beta_lane[32u * J.g0];
+      }
+      bool same = true;
+      if (!anneal)
+        for (uint32_t r = (uint32_t)tid; r < 32u * J.Gj; r += kTile)
+          same = same && J.beta_lane[32u * J.g0 + r] == b0;
+      const int uni = __syncthreads_and(same ? 1 : 0);
+      if (tid == 0) {
+        const bool skip = t >= cd->t_end;
+        sh.skip = skip ? 1u : 0u;
+        sh.fuse = (!skip && half == 0u && cd->tracking && !cd->record && J.sums != nullptr) ? 1u
+                                                                                           : 0u;
+        sh.ra.src = half == 0u ? J.A : J.B;
+        sh.dst = half == 0u ? J.B : J.A;
+        sh.ra.t = t;
+        sh.ra.typ = half ^ cd->order;
+        sh.ra.uni = uni != 0;
+        sh.ra.beta_u = b0;
+        sh.kb_u = (float)(-2.0 * b0 * 1.4426950408889634);
       }
       __syncthreads();
       cur_job = (int)tl.job;
     }
-    if (skip) continue;
-    const uint32_t x = tl.w0 + threadIdx.x;
-    if (x >= J.n) continue;
+    if (sh.skip) continue;
+    const uint32_t Gj = J.Gj, Gp = J.Gp;
+    const uint32_t go = (uint32_t)tid & (Gp - 1u), g = J.g0 + go;
+    const uint32_t t = sh.ra.t, typ = sh.ra.typ;
+    const bool uni = sh.ra.uni, fuse = sh.fuse != 0u;
+    const uint32_t vx = (uint32_t)tid / Gp;
+    const uint32_t slot = tl.w0 + vx;
+    const bool valid = go < Gj && slot < J.n;
     // `half` is the position in the step (buffers); typ the update type (neighbours, draws)
-    const uint32_t* src = half == 0u ? J.A : J.B;
-    uint32_t* dst = half == 0u ? J.B : J.A;
+    const uint32_t* src = sh.ra.src;
+    uint32_t* dst = sh.dst;
     const int32_t* ptr = typ == 0u ? J.in_ptr : J.out_ptr;
     const uint32_t* col = typ == 0u ? J.in_col : J.out_col;
-    const float* Jr = typ == 0u ? J.in_J : J.out_J;
-    const int32_t p0 = ptr[x], p1 = ptr[x + 1];
-    const int d = p1 - p0;
-    const uint32_t S = src[x];
-    const uint32_t F = J.frozen != nullptr ? J.frozen[x] : 0u;
-    const float lam = J.lambda != nullptr ? J.lambda[x] : J.lambda_c;
+    uint32_t x = 0;
+    int32_t p0 = 0;
+    int d = 0;
+    float lam = 0.0f;
+    if (valid) {
+      x = __ldg((typ == 0u ? J.in_perm : J.out_perm) + slot);
+      p0 = __ldg(ptr + x);
+      d = __ldg(ptr + x + 1) - p0;
+      lam = J.lambda != nullptr ? __ldg(J.lambda + x) : J.lambda_c;
+    }
     const float qf = (float)J.q;
-    const PhKey K = ph_key(J.key0, J.key1);
-    uint32_t res = F;
-    if (INTEGER) {
-      const float B = (float)d + fabsf(qf) + fabsf(lam) + 1.0f;
-      if (d <= 255) {
+    const float lmd = __fadd_rn(lam, -(float)d);
+    const float bp = __fadd_rn(lmd, qf), bm = __fadd_rn(lmd, -qf);  // h = 2a + (lambda - d +- q)
+    const float B = (float)d + fabsf(qf) + fabsf(lam) + 1.0f;
+    const bool table = INTEGER && uni && valid && d <= kTableDeg;
+    const float kbu = sh.kb_u;  // in registers: the loops below store to shared memory
+    const uint32_t G = J.G;
+    const double* beta_g = J.beta_lane + 32u * g;
+    uint32_t vamb = 0u;  // classes of this vertex whose top byte is not certain
+    if (INTEGER && uni) {
+      // class tables: the Gj threads of a vertex share its 2 (d + 1) classes (one warp
+      // when Gp <= 32, else the block)
+      uint32_t mine = 0u;
+      if (table) {
+        const float kb = kbu, kbB = fabsf(kb) * B;
+        uint8_t* tbytes = reinterpret_cast<uint8_t*>(sh.tb[vx]);
+        for (uint32_t i = go; i < 2u * (uint32_t)(d + 1); i += Gj) {
+          const uint32_t a = i >> 1, s2 = i & 1u;
+          float lo, hi;
+          t_bounds(fmaf(2.0f, (float)a, s2 ? bp : bm), kb, kbB, lo, hi);
+          const uint32_t bl = top_byte(lo), bh = top_byte(hi);
+          tbytes[a + 16u * s2] = (uint8_t)bh;
+          mine |= (uint32_t)(bl != bh) << (a + 16u * s2);
+        }
+      }
+      if (Gp <= 32u) {
+        for (uint32_t s2 = 1u; s2 < Gp; s2 <<= 1) mine |= __shfl_xor_sync(0xffffffffu, mine, s2);
+        vamb = mine;
+        __syncwarp();
+      } else {
+        if (go == 0u) sh.amb[vx] = 0u;
+        __syncthreads();
+        if (mine != 0u) atomicOr(&sh.amb[vx], mine);
+        __syncthreads();
+        vamb = sh.amb[vx];
+      }
+    }
+    uint32_t res = 0u;
+    const bool hub = valid && d > kHubDeg;
+    // lanes of a class above 7 need the second half of the tables (warp-wide choice)
+    const bool wide = __any_sync(0xffffffffu, table && d > 7);
+    uint32_t und = 0u;  // lanes left to the queue
+    uint32_t S = 0u;
+    if (valid && !hub) {
+      S = __ldg(src + (size_t)x * G + g);
+      const uint32_t F = J.frozen != nullptr ? __ldg(J.frozen + x) : 0u;
+      if (INTEGER) {
         // byte counters: byte i of C[m] = number of neighbours with J_xy s_y = +1 on
         // lane m + 8 i (at most d <= 255, so bytes never carry into each other)
         uint32_t C[8];
 #pragma unroll
         for (int m = 0; m < 8; ++m) C[m] = 0u;
-        for (int e = p0; e < p1; ++e) {
+        for (int e = p0; e < p0 + d; ++e) {
           const uint32_t cv = __ldg(col + e);
-          const uint32_t w = __ldg(src + (cv & 0x7fffffffu)) ^ (0u - (cv >> 31));
+          const uint32_t w = __ldg(src + (size_t)(cv & 0x7fffffffu) * G + g) ^ (0u - (cv >> 31));
 #pragma unroll
           for (int m = 0; m < 8; ++m) C[m] += (w >> m) & 0x01010101u;
         }
-        // h = 2 cnt + (lambda - d +- q): one rounding in the fused multiply-add
-        const float lmd = __fadd_rn(lam, -(float)d);
-        const float bp = __fadd_rn(lmd, qf), bm = __fadd_rn(lmd, -qf);
-        const float a0 = __fadd_rn(2.0f * lam, -(float)d);  // sigma (s + 2 lambda) = sigma (2 cnt + a0)
-        uint32_t und = 0u;
-        if (sh.uni)
-          int_lanes<true>(C, S, K, x, J.b, t, typ, bp, bm, a0, B, sh, fuse, acc, lane, res, und);
-        else
-          int_lanes<false>(C, S, K, x, J.b, t, typ, bp, bm, a0, B, sh, fuse, acc, lane, res, und);
-        while (und != 0u) {  // lanes inside the error bound of the fast test: fp64 threshold
-          const int k = __ffs(und) - 1;
-          und &= und - 1u;
-          const int cnt = lane_count(src, col, p0, p1, k);
-          const uint32_t u = lane_draw(J.key0, J.key1, x, J.b, t, typ, k);
-          const int sigma = ((S >> k) & 1u) ? 1 : -1;
-          res |= (uint32_t)decide_exact(u, 2 * cnt - d, sigma, J.q, lam, sh.beta[k]) << k;
-        }
-      } else {
-#pragma unroll 1
-        for (int k = 0; k < 32; ++k) {  // very high degree: one lane at a time
-          const int cnt = lane_count(src, col, p0, p1, k);
-          const uint32_t u = lane_draw(J.key0, J.key1, x, J.b, t, typ, k);
-          const int s = 2 * cnt - d;
-          const int sigma = ((S >> k) & 1u) ? 1 : -1;
-          const float eps = 3.814697265625e-06f + sh.epc[k] * B;
-          res |= (uint32_t)decide_int(u, s, sigma, qf, J.q, lam, sh.kb[k], eps, sh.beta[k],
-                                      exact_always != 0) << k;
-          if (fuse) {
-            const float a = (float)s + 2.0f * lam;
-            acc[k][lane] += sigma > 0 ? a : -a;
+        if (fuse) {  // sigma (s + 2 lambda) with s = 2a - d
+          const float a0 = __fadd_rn(2.0f * lam, -(float)d);
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            const float cf = __fsub_rn(
+                __int_as_float((int)__byte_perm(C[k & 7], 0x4B000000u, 0x7540u + (k >> 3))),
+                8388608.0f);
+            const float v = __fmaf_rn(2.0f, cf, a0);
+            acc[k][lane] += ((S >> k) & 1u) ? v : -v;
           }
         }
-      }
-      if (exact_always) {  // debugging aid: every lane through the fp64 threshold
-        res = F;
+        // threshold bytes R[m] (byte i: lane m + 8 i) and lanes of uncertain top byte
+        uint32_t R[8], amb = 0u;
+        if (table) {
+          const uint4 m0 = *reinterpret_cast<const uint4*>(&sh.tb[vx][0]);
+          const uint4 p4 = *reinterpret_cast<const uint4*>(&sh.tb[vx][4]);
+          if (vamb != 0u) {  // rare: lanes of the uncertain classes
 #pragma unroll 1
-        for (int k = 0; k < 32; ++k) {
-          const int cnt = lane_count(src, col, p0, p1, k);
-          const uint32_t u = lane_draw(J.key0, J.key1, x, J.b, t, typ, k);
-          const int sigma = ((S >> k) & 1u) ? 1 : -1;
-          res |= (uint32_t)decide_exact(u, 2 * cnt - d, sigma, J.q, lam, sh.beta[k]) << k;
+            for (int k = 0; k < 32; ++k) {
+              const uint32_t a = (C[k & 7] >> (8 * (k >> 3))) & 0xFFu;
+              amb |= ((vamb >> (a + 16u * ((S >> k) & 1u))) & 1u) << k;
+            }
+          }
+#pragma unroll
+          for (int m = 0; m < 8; ++m) {
+            const uint32_t cnt = C[m];
+            const uint32_t x7 = cnt & 0x07070707u;
+            const uint32_t sel = __byte_perm(x7 | (x7 >> 4), 0u, 0x0020);
+            const uint32_t ms = ((S >> m) & 0x01010101u) * 0xFFu;
+            uint32_t vm = __byte_perm(m0.x, m0.y, sel), vp = __byte_perm(p4.x, p4.y, sel);
+            if (wide) {
+              const uint32_t m8 = ((cnt >> 3) & 0x01010101u) * 0xFFu;
+              vm = (__byte_perm(m0.z, m0.w, sel) & m8) | (vm & ~m8);
+              vp = (__byte_perm(p4.z, p4.w, sel) & m8) | (vp & ~m8);
+            }
+            R[m] = (vp & ms) | (vm & ~ms);
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < 8; ++m) {
+            const uint2 rb = lane_bytes(C[m], S, m, bp, bm, B, beta_g, kbu, uni);
+            R[m] = rb.x;
+            amb |= rb.y;
+          }
         }
+        uint32_t P[8];
+        bytes_to_planes(R, P);
+        const PhKey K = ph_key(J.key0, J.key1);
+        const PhShared ph = ph_shared(K, g, t);
+        const uint4 w0 = ph_call_shared(K, ph, x, typ);
+        const uint4 w1 = ph_call_shared(K, ph, x, typ + 2u);
+        const uint32_t W[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+        und = exact_always ? 0u : ~(F | amb);
+        uint32_t r = 0u;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          r |= und & ~W[j] & P[j];   // draw bit 0, threshold bit 1: u < T
+          und &= ~(W[j] ^ P[j]);     // equal bits: not decided yet
+        }
+        // debugging aid (exact_always): every lane through the fp64 threshold
+        und = exact_always ? ~F : (und | (amb & ~F));
+        res = r | F;
+        if (und != 0u) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) sh.wp[tid][j] = W[j];
+        }
+      } else {
+        const PhKey K = ph_key(J.key0, J.key1);
+        const PhShared ph = ph_shared(K, g, t);
+        const float* Jr = typ == 0u ? J.in_J : J.out_J;
+        float h[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) h[k] = 0.0f;
+        for (int e = p0; e < p0 + d; ++e) {
+          const uint32_t y = __ldg(col + e) & 0x7fffffffu;
+          const float Jv = __ldg(Jr + e);
+          const uint32_t wy = __ldg(src + (size_t)y * G + g);
+#pragma unroll
+          for (int k = 0; k < 32; ++k) h[k] += ((wy >> k) & 1u) ? Jv : -Jv;
+        }
+        if (uni)
+          res = real_lanes<true>(h, S, qf, lam, kbu, beta_g, K, ph, x, typ, fuse, acc, lane);
+        else
+          res = real_lanes<false>(h, S, qf, lam, kbu, beta_g, K, ph, x, typ, fuse, acc, lane);
+        res |= F;
       }
-    } else {
-      float h[32];
-#pragma unroll
-      for (int k = 0; k < 32; ++k) h[k] = 0.0f;
-      for (int e = p0; e < p1; ++e) {
-        const uint32_t y = col[e] & 0x7fffffffu;
-        const float Jv = Jr[e];
-        const uint32_t wy = src[y];
-#pragma unroll
-        for (int k = 0; k < 32; ++k) h[k] += ((wy >> k) & 1u) ? Jv : -Jv;
-      }
-      uint4 w = make_uint4(0, 0, 0, 0);
-#pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        if ((k & 3) == 0) w = ph_call_shared(K, sh.ph, x, typ + 2u * (uint32_t)(k >> 2));
-        const uint32_t u = (k & 3) == 0 ? w.x : (k & 3) == 1 ? w.y : (k & 3) == 2 ? w.z : w.w;
-        const bool up = (S >> k) & 1u;
-        const float hk = __fadd_rn(__fadd_rn(h[k], up ? qf : -qf), lam);
-        const float onep = 1.0f + ex2_approx(sh.kb[k] * hk);
-        const float uf = __uint2float_rn(u) * 2.3283064365386963e-10f;
-        res |= (uint32_t)(uf * onep < 1.0f) << k;
-        if (fuse) {
-          const float a = h[k] + 2.0f * lam;
-          acc[k][lane] += up ? a : -a;
+    }
+    if (valid && !hub) dst[(size_t)x * G + g] = res;
+    if (INTEGER) {
+      // undecided lanes into the warp's queue (every lane of the warp takes part); a full
+      // queue is decided 32 at a time, after the words are stored
+      while (__any_sync(0xffffffffu, und != 0u)) {
+        const bool has = und != 0u;
+        const int k = has ? __ffs(und) - 1 : 0;
+        const unsigned ball = __ballot_sync(0xffffffffu, has);
+        if (has) {
+          und &= und - 1u;
+          const uint32_t* w = sh.wp[tid];
+          const uint32_t u8 = lane_byte(w[0], w[1], w[2], w[3], w[4], w[5], w[6], w[7], k);
+          q[qn + __popc(ball & ((1u << lane) - 1u))] =
+              Pend{x, g, (uint32_t)k | (((S >> k) & 1u) << 5) | (u8 << 6) |
+                             (exact_always ? (1u << 14) : 0u), 0u};
+        }
+        qn += __popc(ball);
+        if (qn >= 32) {
+          queue_round(J, q, 32, dst, sh.ra, lane);
+          qn -= 32;
+          if (lane < qn) q[lane] = q[32 + lane];
+          __syncwarp();
         }
       }
     }
-    dst[x] = res;
+    // vertices of degree above kHubDeg: one warp per word
+    unsigned hubs = __ballot_sync(0xffffffffu, hub);
+    while (hubs != 0u) {
+      const int srcl = __ffs(hubs) - 1;
+      hubs &= hubs - 1u;
+      HubArgs A;
+      A.x = __shfl_sync(0xffffffffu, x, srcl);
+      A.g = __shfl_sync(0xffffffffu, g, srcl);
+      A.t = t;
+      A.typ = typ;
+      A.fuse = fuse;
+      A.uni = uni;
+      A.beta_u = sh.ra.beta_u;
+      const uint32_t wres = hub_word<INTEGER>(J, A, half, lane);
+      if (lane == 0) dst[(size_t)A.x * J.G + A.g] = wres;
+    }
   }
-  if (fuse) flush();
+  if (cur_job >= 0) {
+    if (qn > 0) queue_round(J, q, qn, sh.dst, sh.ra, lane);
+    if (sh.fuse) flush();
+  }
 }
 
-// Fields h_x (float) of the next half step as the update kernel computes them.
+// ------------------------------------------------------------------ per-group kernels
+// Jobs of one group each (Gj = 1); tiles of kTile vertices.
+
+// Fields h_x (float) of the next half step, summed in edge order (a diagnostic).
 __global__ void __launch_bounds__(kTile) graph_fields_kernel(const GraphJob* __restrict__ jobs,
                                                              const Tile* __restrict__ tiles,
                                                              int n_tiles, uint32_t half,
@@ -358,11 +702,12 @@ __global__ void __launch_bounds__(kTile) graph_fields_kernel(const GraphJob* __r
     const GraphJob& J = jobs[tl.job];
     const uint32_t x = tl.w0 + threadIdx.x;
     if (x >= J.n) continue;
+    const uint32_t G = J.G, g = J.g0;
     const uint32_t* src = half == 0u ? J.A : J.B;
     const int32_t* ptr = half == 0u ? J.in_ptr : J.out_ptr;
     const uint32_t* col = half == 0u ? J.in_col : J.out_col;
     const float* Jr = half == 0u ? J.in_J : J.out_J;
-    const uint32_t S = src[x];
+    const uint32_t S = src[(size_t)x * G + g];
     const float lam = J.lambda != nullptr ? J.lambda[x] : J.lambda_c;
     const float qf = (float)J.q;
     for (int k = 0; k < 32; ++k) {
@@ -371,23 +716,25 @@ __global__ void __launch_bounds__(kTile) graph_fields_kernel(const GraphJob* __r
         int s = 0;
         for (int e = ptr[x]; e < ptr[x + 1]; ++e) {
           const uint32_t cv = col[e];
-          s += (((src[cv & 0x7fffffffu] ^ (0u - (cv >> 31))) >> k) & 1u) ? 1 : -1;
+          s += (((src[(size_t)(cv & 0x7fffffffu) * G + g] ^ (0u - (cv >> 31))) >> k) & 1u) ? 1
+                                                                                           : -1;
         }
         hk = __fadd_rn(__fadd_rn((float)s, ((S >> k) & 1u) ? qf : -qf), lam);
       } else {
         float a = 0.0f;
         for (int e = ptr[x]; e < ptr[x + 1]; ++e) {
           const float Jv = Jr[e];
-          a += ((src[col[e] & 0x7fffffffu] >> k) & 1u) ? Jv : -Jv;
+          a += ((src[(size_t)(col[e] & 0x7fffffffu) * G + g] >> k) & 1u) ? Jv : -Jv;
         }
         hk = __fadd_rn(__fadd_rn(a, ((S >> k) & 1u) ? qf : -qf), lam);
       }
-      out[(size_t)(J.rep0 + k) * J.n + x] = hk;
+      out[(size_t)(32u * g + (uint32_t)k) * J.n + x] = hk;
     }
   }
 }
 
-// Initial spins: lane k = +1 iff u_k < 2^31 (draw of step 0xFFFFFFFF, half 0).
+// Initial spins: lane k = +1 iff u_k < 2^31 with the direct draw u_k = W_k of step
+// 0xFFFFFFFF, half 0.
 __global__ void __launch_bounds__(kTile) graph_init_kernel(const GraphJob* __restrict__ jobs,
                                                            const Tile* __restrict__ tiles,
                                                            int n_tiles, int kind) {
@@ -406,14 +753,14 @@ __global__ void __launch_bounds__(kTile) graph_init_kernel(const GraphJob* __res
       uint4 w = make_uint4(0, 0, 0, 0);
 #pragma unroll
       for (int k = 0; k < 32; ++k) {
-        if ((k & 3) == 0) w = ph_call(K, x, J.b, kInitStep, 2u * (uint32_t)(k >> 2));
+        if ((k & 3) == 0) w = ph_call(K, x, J.g0, kInitStep, 2u * (uint32_t)(k >> 2));
         const uint32_t u = (k & 3) == 0 ? w.x : (k & 3) == 1 ? w.y : (k & 3) == 2 ? w.z : w.w;
         s |= (uint32_t)(u < 0x80000000u) << k;
       }
     }
     if (J.frozen != nullptr) s |= J.frozen[x];
-    J.A[x] = s;
-    J.B[x] = s;
+    J.A[(size_t)x * J.G + J.g0] = s;
+    J.B[(size_t)x * J.G + J.g0] = s;
   }
 }
 
@@ -428,6 +775,7 @@ __global__ void __launch_bounds__(kTile) graph_obs_kernel(const GraphJob* __rest
   for (int ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
     const Tile tl = tiles[ti];
     const GraphJob& J = jobs[tl.job];
+    const uint32_t G = J.G, g = J.g0;
     double acc[kNumSums];
 #pragma unroll
     for (int q = 0; q < kNumSums; ++q) acc[q] = 0.0;
@@ -436,14 +784,14 @@ __global__ void __launch_bounds__(kTile) graph_obs_kernel(const GraphJob* __rest
     for (uint32_t xi = 0; xi < 32u; ++xi) {
       const uint32_t x = xb + xi;
       if (x >= J.n) break;
-      const int sx = ((J.A[x] >> lane) & 1u) ? 1 : -1;
+      const int sx = ((J.A[(size_t)x * G + g] >> lane) & 1u) ? 1 : -1;
       const float lam = J.lambda != nullptr ? J.lambda[x] : J.lambda_c;
       im += sx;
       acc[kSumLS] += (double)(lam * (float)sx);
       float eacc = 0.0f;
       for (int e = J.in_ptr[x]; e < J.in_ptr[x + 1]; ++e) {
         const uint32_t cv = J.in_col[e];
-        const int sy = ((J.A[cv & 0x7fffffffu] >> lane) & 1u) ? 1 : -1;
+        const int sy = ((J.A[(size_t)(cv & 0x7fffffffu) * G + g] >> lane) & 1u) ? 1 : -1;
         icut += (sx != sy);
         if (J.integer) {
           iE += (cv >> 31) ? -sx * sy : sx * sy;
@@ -453,13 +801,13 @@ __global__ void __launch_bounds__(kTile) graph_obs_kernel(const GraphJob* __rest
       }
       acc[kSumE] += (double)eacc;
       if (full) {
-        const int s2 = ((J.B[x] >> lane) & 1u) ? 1 : -1;
+        const int s2 = ((J.B[(size_t)x * G + g] >> lane) & 1u) ? 1 : -1;
         iP2 += sx * s2;
         acc[kSumLS2] += (double)(lam * (float)s2);
         float pacc = 0.0f;
         for (int e = J.out_ptr[x]; e < J.out_ptr[x + 1]; ++e) {
           const uint32_t cv = J.out_col[e];
-          const int sy = ((J.B[cv & 0x7fffffffu] >> lane) & 1u) ? 1 : -1;
+          const int sy = ((J.B[(size_t)(cv & 0x7fffffffu) * G + g] >> lane) & 1u) ? 1 : -1;
           if (J.integer) {
             iP1 += (cv >> 31) ? -sx * sy : sx * sy;
           } else {
@@ -478,7 +826,7 @@ __global__ void __launch_bounds__(kTile) graph_obs_kernel(const GraphJob* __rest
     for (int q = 0; q < kNumSums; ++q) red[warp][lane][q] = acc[q];
     __syncthreads();
     if (threadIdx.x < 32) {
-      double* dst = (which ? J.obs : J.sums) + (size_t)threadIdx.x * kNumSums;
+      double* dst = (which ? J.obs : J.sums) + (size_t)(32u * g + threadIdx.x) * kNumSums;
 #pragma unroll
       for (int q = 0; q < kNumSums; ++q) {
         if (q == kSumM2) continue;

@@ -134,8 +134,10 @@ struct Family {
   int kind = 0;  // 0 lattice, 1 graph
   int enc = 0;   // lattice encoding; graph: 1 integer couplings, 0 real
   int wpt = 1;   // lattice: lane words per thread per tile (tile = 256 wpt words)
-  DevMem jobs, tiles;
+  DevMem jobs, tiles;  // graph: multi-group jobs and (vertex, group) pair tiles (half steps)
   int n_tiles = 0;
+  DevMem ojobs, otiles;  // graph: one job per group and vertex tiles (init, observables)
+  int n_otiles = 0;
 };
 
 struct Plan {
@@ -230,6 +232,7 @@ struct shaken_ctx {
   DevMem step_sums, obs_sums, best, best_step;
   DevMem series_m, series_H;
   DevMem in_ptr, in_col, in_J, out_ptr, out_col, out_J, lam_dev;
+  DevMem in_perm, out_perm;  // vertices by increasing in- / out-degree (half-step order)
   DevMem band_xch, band_sync;  // banded runs: row exchange area and grid barrier
   bool band_stall = false;     // diagnostics: the next banded run's barrier never completes
   int band_hurry = -1;         // diagnostics: block that gives up the next run's last wait at once
@@ -380,7 +383,9 @@ static shaken_status build_plan(Plan& P, cudaStream_t st) {
   P.fams.clear();
   P.drop_graph();
   std::vector<std::vector<LatJob>> ljobs(3);
-  std::vector<std::vector<GraphJob>> gjobs(2);  // 0 integer, 1 real
+  std::vector<std::vector<GraphJob>> gjobs(2);  // 0 integer, 1 real: half-step jobs
+  std::vector<std::vector<GraphJob>> ojobs(2);  // per-group jobs
+  std::vector<std::vector<Tile>> otiles(2);
   std::vector<std::vector<Tile>> tiles(5);
   std::vector<CtxDev*> cds;
   for (shaken_ctx* c : P.members) {
@@ -420,34 +425,51 @@ static shaken_status build_plan(Plan& P, cudaStream_t st) {
       }
     } else {
       const int fi = c->integer ? 0 : 1;
-      const int ng = c->R / 32;
-      for (int g = 0; g < ng; ++g) {
-        GraphJob J{};
-        J.A = c->A.as<uint32_t>() + (size_t)g * c->n;
-        J.B = c->B.as<uint32_t>() + (size_t)g * c->n;
-        J.in_ptr = c->in_ptr.as<int32_t>();
-        J.in_col = c->in_col.as<uint32_t>();
-        J.in_J = c->integer ? nullptr : c->in_J.as<float>();
-        J.out_ptr = c->out_ptr.as<int32_t>();
-        J.out_col = c->out_col.as<uint32_t>();
-        J.out_J = c->integer ? nullptr : c->out_J.as<float>();
-        J.lambda = c->has_lambda ? c->lam_dev.as<float>() : nullptr;
-        J.frozen = c->frozen_lanes.p ? c->frozen_lanes.as<uint32_t>() : nullptr;
-        J.beta_lane = c->beta_lanes.as<double>() + 32 * g;
-        J.beta_sched = c->anneal_sched.p ? c->anneal_sched.as<double>() : nullptr;
-        J.cd = cdp;
-        J.sums = c->step_sums.as<double>() + (size_t)32 * g * kNumSums;
-        J.obs = c->obs_sums.as<double>() + (size_t)32 * g * kNumSums;
-        J.q = c->q;
-        J.lambda_c = (float)c->lam_c;
-        J.n = (uint32_t)c->n;
-        J.b = (uint32_t)g;
-        J.key0 = key0;
-        J.key1 = key1;
-        J.integer = c->integer ? 1u : 0u;
-        J.rep0 = (uint32_t)(32 * g);
-        add_tiles(tiles[3 + fi], (uint32_t)gjobs[fi].size(), (uint64_t)c->n, (uint32_t)kTile);
-        gjobs[fi].push_back(J);
+      const uint32_t ng = (uint32_t)(c->R / 32);
+      GraphJob J{};
+      J.A = c->A.as<uint32_t>();
+      J.B = c->B.as<uint32_t>();
+      J.in_ptr = c->in_ptr.as<int32_t>();
+      J.in_col = c->in_col.as<uint32_t>();
+      J.in_J = c->integer ? nullptr : c->in_J.as<float>();
+      J.out_ptr = c->out_ptr.as<int32_t>();
+      J.out_col = c->out_col.as<uint32_t>();
+      J.out_J = c->integer ? nullptr : c->out_J.as<float>();
+      J.in_perm = c->in_perm.as<uint32_t>();
+      J.out_perm = c->out_perm.as<uint32_t>();
+      J.lambda = c->has_lambda ? c->lam_dev.as<float>() : nullptr;
+      J.frozen = c->frozen_lanes.p ? c->frozen_lanes.as<uint32_t>() : nullptr;
+      J.beta_lane = c->beta_lanes.as<double>();
+      J.beta_sched = c->anneal_sched.p ? c->anneal_sched.as<double>() : nullptr;
+      J.cd = cdp;
+      J.sums = c->step_sums.as<double>();
+      J.obs = c->obs_sums.as<double>();
+      J.q = c->q;
+      J.lambda_c = (float)c->lam_c;
+      J.n = (uint32_t)c->n;
+      J.G = ng;
+      J.key0 = key0;
+      J.key1 = key1;
+      J.integer = c->integer ? 1u : 0u;
+      // half steps: jobs of at most kTile groups; a vertex takes Gp threads (Gj rounded
+      // up to a power of two) and a tile kTile / Gp vertices
+      for (uint32_t g0 = 0; g0 < ng; g0 += (uint32_t)kTile) {
+        GraphJob H = J;
+        H.g0 = g0;
+        H.Gj = std::min<uint32_t>((uint32_t)kTile, ng - g0);
+        H.Gp = 1;
+        while (H.Gp < H.Gj) H.Gp <<= 1;
+        add_tiles(tiles[3 + fi], (uint32_t)gjobs[fi].size(), (uint64_t)c->n,
+                  (uint32_t)kTile / H.Gp);
+        gjobs[fi].push_back(H);
+      }
+      // init, observables, fields: one job per group, tiles of kTile vertices
+      for (uint32_t g = 0; g < ng; ++g) {
+        GraphJob O = J;
+        O.g0 = g;
+        O.Gj = 1;
+        add_tiles(otiles[fi], (uint32_t)ojobs[fi].size(), (uint64_t)c->n, (uint32_t)kTile);
+        ojobs[fi].push_back(O);
       }
     }
   }
@@ -476,6 +498,9 @@ static shaken_status build_plan(Plan& P, cudaStream_t st) {
     TRY(upload(F->jobs, gjobs[fi].data(), gjobs[fi].size() * sizeof(GraphJob), st));
     TRY(upload(F->tiles, tiles[3 + fi].data(), tiles[3 + fi].size() * sizeof(Tile), st));
     F->n_tiles = (int)tiles[3 + fi].size();
+    TRY(upload(F->ojobs, ojobs[fi].data(), ojobs[fi].size() * sizeof(GraphJob), st));
+    TRY(upload(F->otiles, otiles[fi].data(), otiles[fi].size() * sizeof(Tile), st));
+    F->n_otiles = (int)otiles[fi].size();
     P.fams.push_back(std::move(F));
   }
   TRY(upload(P.ctxlist, cds.data(), cds.size() * sizeof(CtxDev*), st));
@@ -506,7 +531,7 @@ static shaken_status plan_step_launch(Plan& P, cudaStream_t st, uint64_t* nl,
                                    F->n_tiles, 0, 0, st));
         ++count;
       } else if (F->kind == 1) {
-        CU(shk::launch_graph_obs(F->jobs.as<GraphJob>(), F->tiles.as<Tile>(), F->n_tiles, 0, 0,
+        CU(shk::launch_graph_obs(F->ojobs.as<GraphJob>(), F->otiles.as<Tile>(), F->n_otiles, 0, 0,
                                  st));
         ++count;
       }
@@ -645,10 +670,12 @@ static void encode_spins(const shaken_ctx* c, const int8_t* in, std::vector<uint
         if (in[(size_t)r * N + x] > 0) w[(size_t)r * words + (x >> 5)] |= 1u << (x & 31);
     return;
   }
+  const int G = c->R / 32;
+  const bool vmajor = c->kind == SHAKEN_GRAPH;  // graphs: [n][G]; lattices: [G][L][L]
   for (int r = 0; r < c->R; ++r) {
     const int g = r >> 5, k = r & 31;
     for (int64_t x = 0; x < N; ++x)
-      if (in[(size_t)r * N + x] > 0) w[(size_t)g * N + x] |= 1u << k;
+      if (in[(size_t)r * N + x] > 0) w[vmajor ? (size_t)x * G + g : (size_t)g * N + x] |= 1u << k;
   }
 }
 
@@ -666,9 +693,13 @@ static void decode_spins(const shaken_ctx* c, const std::vector<uint8_t>& in, in
         out[(size_t)r * N + x] = (w[(size_t)r * words + (x >> 5)] >> (x & 31)) & 1u ? 1 : -1;
     return;
   }
+  const int G = c->R / 32;
+  const bool vmajor = c->kind == SHAKEN_GRAPH;
   for (int r = 0; r < c->R; ++r) {
     const int g = r >> 5, k = r & 31;
-    for (int64_t x = 0; x < N; ++x) out[(size_t)r * N + x] = (w[(size_t)g * N + x] >> k) & 1u ? 1 : -1;
+    for (int64_t x = 0; x < N; ++x)
+      out[(size_t)r * N + x] =
+          (w[vmajor ? (size_t)x * G + g : (size_t)g * N + x] >> k) & 1u ? 1 : -1;
   }
 }
 
@@ -731,6 +762,7 @@ static shaken_status validate(const shaken_problem* p) {
 // set-up so that the server can prepare jobs on the submitting thread.
 struct HostPrep {
   std::vector<int32_t> iptr, optr;
+  std::vector<uint32_t> iperm, operm;  // vertices by increasing in- / out-degree
   std::vector<uint32_t> icol, ocol;
   std::vector<float> iJ, oJ;
   std::vector<uint32_t> frozen_lanes;
@@ -769,12 +801,27 @@ static void build_graph_host(shaken_ctx* c, const shaken_problem* p, HostPrep& h
   };
   csr(head, tail, hp.iptr, hp.icol, hp.iJ);
   csr(tail, head, hp.optr, hp.ocol, hp.oJ);
+  // visiting order of each half step: vertices by increasing degree (counting sort,
+  // stable), so a warp's words have nearly equal edge loops and take the same path
+  auto by_degree = [&](const std::vector<int32_t>& ptr, std::vector<uint32_t>& perm) {
+    int32_t dmax = 0;
+    for (int64_t x = 0; x < n; ++x) dmax = std::max(dmax, ptr[x + 1] - ptr[x]);
+    std::vector<int64_t> start((size_t)dmax + 2, 0);
+    for (int64_t x = 0; x < n; ++x) start[(size_t)(ptr[x + 1] - ptr[x]) + 1]++;
+    for (size_t k = 1; k < start.size(); ++k) start[k] += start[k - 1];
+    perm.assign((size_t)n, 0u);
+    for (int64_t x = 0; x < n; ++x) perm[(size_t)start[(size_t)(ptr[x + 1] - ptr[x])]++] = (uint32_t)x;
+  };
+  by_degree(hp.iptr, hp.iperm);
+  by_degree(hp.optr, hp.operm);
   c->sumJ = 0.0;
   for (int64_t e = 0; e < m; ++e) c->sumJ += (double)p->J_edge[e];
 }
 
 static shaken_status upload_graph(shaken_ctx* c, const HostPrep& hp, cudaStream_t st) {
   TRY(upload(c->in_ptr, hp.iptr.data(), hp.iptr.size() * 4, st));
+  TRY(upload(c->in_perm, hp.iperm.data(), hp.iperm.size() * 4, st));
+  TRY(upload(c->out_perm, hp.operm.data(), hp.operm.size() * 4, st));
   TRY(upload(c->out_ptr, hp.optr.data(), hp.optr.size() * 4, st));
   TRY(upload(c->in_col, hp.icol.data(), hp.icol.size() * 4, st));
   TRY(upload(c->out_col, hp.ocol.data(), hp.ocol.size() * 4, st));
@@ -801,7 +848,7 @@ static shaken_status ctx_init_spins(shaken_ctx* c, int kind, const int8_t* given
       CU(shk::launch_lattice_init(F->enc, F->wpt, F->jobs.as<LatJob>(), F->tiles.as<Tile>(),
                                   F->n_tiles, kind, st));
     else
-      CU(shk::launch_graph_init(F->jobs.as<GraphJob>(), F->tiles.as<Tile>(), F->n_tiles, kind,
+      CU(shk::launch_graph_init(F->ojobs.as<GraphJob>(), F->otiles.as<Tile>(), F->n_otiles, kind,
                                 st));
     c->launches++;
   }
@@ -1212,7 +1259,7 @@ static shaken_status obs_launch(Plan& P, cudaStream_t st, uint64_t* launches) {
       CU(shk::launch_lattice_obs(F->enc, F->wpt, F->jobs.as<LatJob>(), F->tiles.as<Tile>(),
                                  F->n_tiles, 1, 1, st));
     else
-      CU(shk::launch_graph_obs(F->jobs.as<GraphJob>(), F->tiles.as<Tile>(), F->n_tiles, 1, 1,
+      CU(shk::launch_graph_obs(F->ojobs.as<GraphJob>(), F->otiles.as<Tile>(), F->n_otiles, 1, 1,
                                st));
     ++*launches;
   }
@@ -1515,7 +1562,7 @@ shaken_status shaken_debug_fields(shaken_ctx* ctx, int half, float* out) {
   const size_t bytes = (size_t)ctx->R * ctx->n * sizeof(float);
   TRY(d.alloc(bytes));
   for (auto& F : ctx->solo.fams) {
-    CU(shk::launch_graph_fields(F->jobs.as<GraphJob>(), F->tiles.as<Tile>(), F->n_tiles,
+    CU(shk::launch_graph_fields(F->ojobs.as<GraphJob>(), F->otiles.as<Tile>(), F->n_otiles,
                                 (uint32_t)half, d.as<float>(), st));
     ctx->launches++;
   }

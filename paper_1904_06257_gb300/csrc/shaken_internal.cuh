@@ -292,30 +292,41 @@ struct LatJob {
   uint32_t wpr_shift;            // log2(wpr) when wpr is a power of two, else 0xffffffff
 };
 
-// One graph job: a 32-replica group of a graph context.
+// One graph job: the groups [g0, g0 + Gj) of a graph context (Gj <= kTile).  The
+// context's spins are uint32 [n][G]: word x * G + g holds vertex x of replicas
+// 32 g .. 32 g + 31 (bit k = replica 32 g + k), so the group words of a vertex
+// are adjacent.  A half-step tile holds kTile / Gp consecutive entries of the
+// vertex order of its half step (in_perm or out_perm: vertices by increasing
+// degree), each with Gp threads (Gp = Gj rounded up to a power of two), thread
+// g - g0 of a vertex owning word (x, g); per-group jobs (Gj = 1) serve the init,
+// observables and field kernels with tiles of kTile vertices in index order.
 struct GraphJob {
-  uint32_t* A;
-  uint32_t* B;
+  uint32_t* A;             // sigma, [n][G]
+  uint32_t* B;             // sigma', [n][G]
   const int32_t* in_ptr;   // in-CSR (sources y of (y -> x) in E^o)
   const uint32_t* in_col;  // bit 31: J < 0 (integer couplings)
   const float* in_J;       // real couplings (null for integer)
   const int32_t* out_ptr;  // out-CSR (heads y of (x -> y))
   const uint32_t* out_col;
   const float* out_J;
+  const uint32_t* in_perm;  // vertices by increasing in-degree (half-step order, h^{1->2})
+  const uint32_t* out_perm; // vertices by increasing out-degree (h^{2->1})
   const float* lambda;     // [n] or null (lambda_c)
   const uint32_t* frozen;  // [n] lane masks or null
-  const double* beta_lane; // [32] betas of this group
+  const double* beta_lane; // [R] betas of the context
   const double* beta_sched;// anneal schedule (index step - anneal_t0) or null
   CtxDev* cd;
-  double* sums;            // [32][8] step sums of the group's replicas (tracking)
-  double* obs;             // [32][8] on-demand observable sums
+  double* sums;            // [R][8] step sums of the context's replicas (tracking)
+  double* obs;             // [R][8] on-demand observable sums
   double q;
   float lambda_c;
   uint32_t n;
-  uint32_t b;
+  uint32_t G;              // groups of the context (words per vertex)
+  uint32_t g0;             // first group of this job
+  uint32_t Gj;             // groups of this job
+  uint32_t Gp;             // threads per vertex in half-step tiles (power of two >= Gj)
   uint32_t key0, key1;
   uint32_t integer;
-  uint32_t rep0;
 };
 
 struct Tile {

@@ -99,6 +99,23 @@ def erdos_renyi(n: int, mean_degree: float, seed: int):
     return (keys // n).astype(np.int32), (keys % n).astype(np.int32)
 
 
+def power_law(n: int, mean_degree: float, exponent: float, seed: int):
+    """Chung-Lu graph with a power-law degree sequence: vertex i has weight
+    w_i ~ (i + 1)^(-1/(exponent - 1)), scaled to the mean degree; m = n mean_degree / 2
+    edges are drawn with both ends chosen proportionally to the weights, and
+    self-loops and repeated pairs are dropped.  Vertices of small index are hubs."""
+    g = rng(seed)
+    w = (np.arange(n, dtype=np.float64) + 1.0) ** (-1.0 / (exponent - 1.0))
+    p = w / w.sum()
+    m = int(n * mean_degree / 2)
+    u = g.choice(n, size=m, p=p).astype(np.int64)
+    v = g.choice(n, size=m, p=p).astype(np.int64)
+    ok = u != v
+    a, b = np.minimum(u[ok], v[ok]), np.maximum(u[ok], v[ok])
+    keys = _unique_sorted(a * n + b)
+    return (keys // n).astype(np.int32), (keys % n).astype(np.int32)
+
+
 def couplings_pm1(m: int, seed: int) -> np.ndarray:
     """J_e = +-1 with probability 1/2 each (float32)."""
     return np.where(rng(seed).random(m) < 0.5, -1.0, 1.0).astype(np.float32)

@@ -33,9 +33,9 @@ def graph_problem(S, n, u, v, J, R, beta, q=1.0, lam=None, lam_c=0.0, integer=Tr
 
 
 def graph_spins_from_raw(raw, n, R):
-    """int8 [R][n] spins from a graph's raw MULTISPIN state (uint32 words, bit k of the
+    """int8 [R][n] spins from a graph's raw MULTISPIN state (uint32 [n][R/32], bit k of the
     word of vertex x in group g = replica 32 g + k; the layout of shaken_get_state_raw)."""
     words = np.frombuffer(np.ascontiguousarray(raw).tobytes(), dtype=np.uint32)
-    words = words.reshape(R // 32, n)
+    words = words.reshape(n, R // 32).T
     bits = (words[:, None, :] >> np.arange(32, dtype=np.uint32)[None, :, None]) & 1
     return np.where(bits.reshape(R, n) != 0, 1, -1).astype(np.int8)

@@ -29,7 +29,8 @@ def run_graph_both(S, n, u, v, J, R, beta, q, lam, steps, seed, integer=True, or
     tail, head = core.orient(u, v, orientation)
     o = core.graph_init(n, R, seed, init, frozen)
     o, _ = core.graph_run(o, tail, head, np.asarray(J, np.float64), integer,
-                          np.asarray(lam, np.float64), q, beta, seed, 0, steps, frozen=frozen)
+                          np.asarray(lam, np.float64), q, beta, seed, 0, steps, frozen=frozen,
+                          draw=core.DRAW_PLANE if integer else core.DRAW_DIRECT)
     return got, o
 
 
@@ -147,3 +148,64 @@ def test_large_lattice_sampled(S):
         for k, val in saved.items():
             s0[k] = val
         assert s1[i, j] == tau
+
+
+@pytest.mark.parametrize("integer", [True, False])
+def test_power_law_graph_with_hubs(S, integer):
+    """Chung-Lu power-law graph (n = 20000, mean degree 6, exponent 2.5): a dozen
+    vertices of degree above 255 (done by a whole warp), several hundred between 16
+    and 255 (per-lane thresholds), the rest through the class tables; both
+    orientations, so the hubs feed half 1 and then half 0.  Integer couplings:
+    bit-exact against the oracle; real couplings: see the field-band tests (here the
+    chain must only run and keep frozen vertices at +1)."""
+    n, R = 20000, 64
+    u, v = W.power_law(n, 6.0, 2.5, 3)
+    J = W.couplings_pm1(u.size, 4) if integer else W.couplings_normal(u.size, 4)
+    lam = W.fields_normal(n, 0.1, 5)
+    frozen = np.zeros(n, np.uint8)
+    frozen[1] = 1  # a hub
+    for orientation, (uu, vv) in ((0, (u, v)), (2, (v, u))):
+        if integer:
+            got, ref = run_graph_both(S, n, uu, vv, J, R, 0.6, 1.0, lam, 2, 61,
+                                      orientation=orientation, frozen=frozen)
+            assert np.array_equal(got, ref), orientation
+        else:
+            ctx = S.shaken_init(graph_problem(S, n, uu, vv, J, R, 0.6, q=1.0, lam=lam,
+                                              integer=False, orientation=orientation,
+                                              frozen=frozen), 61)
+            S.shaken_step(ctx, 3)
+            got = S.shaken_get_spins(ctx, R, n)
+            S.shaken_free(ctx)
+            assert np.all(got[:, 1] == 1) and np.abs(got).min() == 1
+
+
+@pytest.mark.parametrize("leaves", [1000, 100_000])
+def test_star_hub_sampled(S, leaves):
+    """A star with 10^3 or 10^5 leaves (centre 0, its degree far above what a byte
+    counter holds) and +-1 couplings, oriented so the centre's 10^3 / 10^5 neighbours
+    are its in-neighbours (half 0) and then its out-neighbours (half 1): every
+    replica's decision at the centre in both half steps, and sampled leaves, against
+    the oracle's single-vertex decisions (bit-plane draws, fp64 thresholds)."""
+    n, R, q, beta, seed = leaves + 1, 64, 0.5, 0.004, 91
+    hub_src = np.arange(1, n, dtype=np.int32)
+    J = W.couplings_pm1(leaves, 7)
+    lam = W.fields_normal(n, 0.2, 8)
+    for uu, vv in ((hub_src, np.zeros(leaves, np.int32)), (np.zeros(leaves, np.int32), hub_src)):
+        ctx = S.shaken_init(graph_problem(S, n, uu, vv, J, R, beta, q=q, lam=lam,
+                                          orientation=S.ORIENT_GIVEN), seed)
+        S.shaken_step(ctx, 1)
+        s0 = S.shaken_get_spins(ctx, R, n)
+        S.shaken_step(ctx, 1)
+        sp = S.shaken_get_spins_prime(ctx, R, n)
+        s1 = S.shaken_get_spins(ctx, R, n)
+        S.shaken_free(ctx)
+        tail, head = core.orient(uu, vv, 2)
+        Jd, ld = J.astype(np.float64), lam.astype(np.float64)
+        g = np.random.default_rng(5)
+        for typ, src, out in ((0, s0, sp), (1, sp, s1)):
+            inc = core.Incidence(n, tail, head, Jd, True, ld, q, typ)
+            xs = [0] + [int(x) for x in g.integers(1, n, 40)]
+            for x in xs:
+                for r in (range(R) if x == 0 else g.integers(0, R, 4)):
+                    tau = inc.site(src[int(r)], x, int(r), beta, seed, 1, core.DRAW_PLANE)
+                    assert out[int(r), x] == tau, (typ, x, int(r))

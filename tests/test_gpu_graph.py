@@ -41,7 +41,7 @@ def test_integer_graph_bit_exact(S, n, deg, R, orientation):
     s1 = S.shaken_get_spins(ctx, R, n)
     tail, head = core.orient(u, v, orientation)
     o1, osp = core.graph_run(o0, tail, head, J.astype(np.float64), True, lam.astype(np.float64),
-                             1.0, beta, seed, 0, 5)
+                             1.0, beta, seed, 0, 5, draw=core.DRAW_PLANE)
     assert np.array_equal(s1, o1)
     obs = S.shaken_observables(ctx, R)
     ref = core.graph_observables(o1, osp, tail, head, J.astype(np.float64),
@@ -80,7 +80,7 @@ def test_graph_anneal_bit_exact(S):
     tail, head = core.orient(u, v, 0)
     o = core.graph_init(n, R, seed, 0)
     o, _ = core.graph_run(o, tail, head, J.astype(np.float64), True, lam.astype(np.float64), 1.0,
-                          0.5, seed, 0, 0, beta_sched=sched)
+                          0.5, seed, 0, 0, beta_sched=sched, draw=core.DRAW_PLANE)
     assert np.array_equal(s, o)
     S.shaken_free(ctx)
 
@@ -250,7 +250,8 @@ def test_fused_tracking_best_energy(S):
     for k, b in enumerate(sched):
         H = np.array([o["H"] for o in core.graph_observables(cur, cur, tail, head, Jd, ld, 1.0)])
         best = np.minimum(best, H)
-        cur, _ = core.graph_run(cur, tail, head, Jd, True, ld, 1.0, b, seed, k, 1)
+        cur, _ = core.graph_run(cur, tail, head, Jd, True, ld, 1.0, b, seed, k, 1,
+                                draw=core.DRAW_PLANE)
     H = np.array([o["H"] for o in core.graph_observables(cur, cur, tail, head, Jd, ld, 1.0)])
     best = np.minimum(best, H)
     assert np.allclose(obs["best_energy"], best, rtol=1e-6, atol=1e-4)
@@ -290,7 +291,7 @@ def test_full_size_anneal_step_sampled(S):
         s = int(np.sum(np.where(J[es] > 0, 1, -1) * sr[ys].astype(np.int64)))
         h = core.field(1.0, s, q, int(sr[x]), float(lam[x]))
         T = core.threshold(h, beta)
-        uu = core.draw_direct(seed, x, r >> 5, t, half, r & 31)
+        uu = core.graph_draw(seed, x, r, t, half, core.DRAW_PLANE)
         return 1 if uu < T else -1
 
     g = np.random.default_rng(21)

@@ -59,9 +59,9 @@ def test_reversed_order_graph(S):
     o = core.graph_init(n, R, seed, 0)
     for t in range(4):
         sp = core.graph_half(o, tail, head, J.astype(np.float64), True, lam.astype(np.float64),
-                             1.0, 0.9, seed, t, 1)
+                             1.0, 0.9, seed, t, 1, draw=core.DRAW_PLANE)
         o = core.graph_half(sp, tail, head, J.astype(np.float64), True, lam.astype(np.float64),
-                            1.0, 0.9, seed, t, 0)
+                            1.0, 0.9, seed, t, 0, draw=core.DRAW_PLANE)
     assert np.array_equal(got, o)
 
 
@@ -116,7 +116,7 @@ def test_triangular_lattice_bit_exact(S):
     tail, head = core.orient(u, v, 2)
     o = core.graph_init(L * L, R, seed, 0)
     o, _ = core.graph_run(o, tail, head, J.astype(np.float64), True, 0.0, 0.6,
-                          W.beta_grid(R, 0.1, 0.6, 16), seed, 0, 5)
+                          W.beta_grid(R, 0.1, 0.6, 16), seed, 0, 5, draw=core.DRAW_PLANE)
     assert np.array_equal(got, o)
 
 
