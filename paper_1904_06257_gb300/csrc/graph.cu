@@ -35,7 +35,7 @@
 
 namespace shk {
 
-constexpr int kTableDeg = 15;  // per-vertex class tables for degree <= 15
+constexpr int kTableDeg = 31;  // per-vertex class tables for degree <= 31
 constexpr int kHubDeg = 255;   // byte counters for degree <= 255; above: one warp per word
 
 // 2^x (PTX ex2.approx: relative error below 2^-22 over the range used here).
@@ -114,6 +114,51 @@ __device__ __forceinline__ void bytes_to_planes(uint32_t (&R)[8], uint32_t (&P)[
   t44(R[4], R[5], R[6], R[7]);
 #pragma unroll
   for (int j = 0; j < 8; ++j) P[j] = R[7 - j];
+}
+
+// Threshold bytes of lanes m + 8 i (byte i) from the class table of their vertex:
+// Tm / Tp hold the top bytes for sigma = -1 / +1 and a = 0 .. 8 NW - 1 (4 per word);
+// cnt holds the lanes' counts a (bytes), sbits their sigma bits (bit 8 i).  Byte
+// permutes pick 8 entries at a time by the low three bits of a, byte masks the rest.
+template <int NW>
+__device__ __forceinline__ uint32_t lookup_bytes(const uint32_t (&Tm)[8], const uint32_t (&Tp)[8],
+                                                 uint32_t cnt, uint32_t sbits) {
+  const uint32_t x7 = cnt & 0x07070707u;
+  const uint32_t sel = __byte_perm(x7 | (x7 >> 4), 0u, 0x0020);
+  uint32_t vm = __byte_perm(Tm[0], Tm[1], sel), vp = __byte_perm(Tp[0], Tp[1], sel);
+  if (NW >= 2) {
+    const uint32_t m8 = ((cnt >> 3) & 0x01010101u) * 0xFFu;
+    vm = (__byte_perm(Tm[2], Tm[3], sel) & m8) | (vm & ~m8);
+    vp = (__byte_perm(Tp[2], Tp[3], sel) & m8) | (vp & ~m8);
+    if (NW == 4) {
+      const uint32_t m16 = ((cnt >> 4) & 0x01010101u) * 0xFFu;
+      const uint32_t hm = (__byte_perm(Tm[6], Tm[7], sel) & m8) | (__byte_perm(Tm[4], Tm[5], sel) & ~m8);
+      const uint32_t hp = (__byte_perm(Tp[6], Tp[7], sel) & m8) | (__byte_perm(Tp[4], Tp[5], sel) & ~m8);
+      vm = (hm & m16) | (vm & ~m16);
+      vp = (hp & m16) | (vp & ~m16);
+    }
+  }
+  const uint32_t ms = sbits * 0xFFu;
+  return (vp & ms) | (vm & ~ms);
+}
+
+// The same for collapsed classes (q = 1): one table T over a' = a + sigma, cnt holding
+// a' in bytes.
+template <int NW>
+__device__ __forceinline__ uint32_t lookup_bytes_c(const uint32_t (&T)[8], uint32_t cnt) {
+  const uint32_t x7 = cnt & 0x07070707u;
+  const uint32_t sel = __byte_perm(x7 | (x7 >> 4), 0u, 0x0020);
+  uint32_t v = __byte_perm(T[0], T[1], sel);
+  if (NW >= 2) {
+    const uint32_t m8 = ((cnt >> 3) & 0x01010101u) * 0xFFu;
+    v = (__byte_perm(T[2], T[3], sel) & m8) | (v & ~m8);
+    if (NW == 4) {
+      const uint32_t m16 = ((cnt >> 4) & 0x01010101u) * 0xFFu;
+      const uint32_t h = (__byte_perm(T[6], T[7], sel) & m8) | (__byte_perm(T[4], T[5], sel) & ~m8);
+      v = (h & m16) | (v & ~m16);
+    }
+  }
+  return v;
 }
 
 // Bits k of eight plane words, most significant first.
@@ -342,14 +387,14 @@ struct RoundArgs {
 };
 
 struct GraphShared {
-  __align__(16) uint32_t tb[kTile][8];  // per vertex slot: top bytes of T by class (byte
-                                        // a + 16 sigma), read as two 16-byte vectors
+  __align__(16) uint32_t tb[kTile][16];  // per vertex slot: top bytes of T by class (byte
+                                         // a + 32 sigma), read as 16-byte vectors
   GraphJob J;       // the current job's descriptor
   RoundArgs ra;     // the current job's step: input, t, update type, beta
   uint32_t* dst;    // the half step's output configuration
   float kb_u;       // -2 beta_u log2(e)
   uint32_t skip, fuse;
-  uint32_t amb[kTile];    // per vertex slot: classes whose top byte is not certain
+  unsigned long long amb[kTile];  // per vertex slot: classes whose top byte is not certain
   Pend q[kTile / 32][kQueue];
   uint32_t wp[kTile][8];  // planes 0..7 of a word with lanes waiting to be queued
   float acc[kTile / 32][32][32];  // tracking sums [warp][replica lane k][thread lane]
@@ -500,25 +545,33 @@ __global__ void __launch_bounds__(kTile, 3) graph_half_kernel(const GraphJob* __
     const float lmd = __fadd_rn(lam, -(float)d);
     const float bp = __fadd_rn(lmd, qf), bm = __fadd_rn(lmd, -qf);  // h = 2a + (lambda - d +- q)
     const float B = (float)d + fabsf(qf) + fabsf(lam) + 1.0f;
-    const bool table = INTEGER && uni && valid && d <= kTableDeg;
+    // class tables when they cost no more than per-lane thresholds: at most 32 classes
+    // per thread of the vertex (2 (d + 1) <= 32 Gj).  With q = 1 the classes collapse
+    // exactly: h(a, +1) = (2a - d + 1) + lambda = h(a + 1, -1), so one table over
+    // a' = a + sigma in 0 .. d + 1 serves both (d <= 30)
+    const bool collapse = J.q == 1.0;
+    const bool table = INTEGER && uni && valid &&
+                       (collapse ? d <= kTableDeg - 1 : (d <= kTableDeg && (uint32_t)(d + 1) <= 16u * Gj));
     const float kbu = sh.kb_u;  // in registers: the loops below store to shared memory
     const uint32_t G = J.G;
     const double* beta_g = J.beta_lane + 32u * g;
-    uint32_t vamb = 0u;  // classes of this vertex whose top byte is not certain
+    unsigned long long vamb = 0ull;  // classes of this vertex whose top byte is not certain
     if (INTEGER && uni) {
       // class tables: the Gj threads of a vertex share its 2 (d + 1) classes (one warp
-      // when Gp <= 32, else the block)
-      uint32_t mine = 0u;
+      // when Gp <= 32, else the block); byte a + 32 sigma
+      unsigned long long mine = 0ull;
       if (table) {
         const float kb = kbu, kbB = fabsf(kb) * B;
         uint8_t* tbytes = reinterpret_cast<uint8_t*>(sh.tb[vx]);
-        for (uint32_t i = go; i < 2u * (uint32_t)(d + 1); i += Gj) {
-          const uint32_t a = i >> 1, s2 = i & 1u;
+        const uint32_t ncls = collapse ? (uint32_t)(d + 2) : 2u * (uint32_t)(d + 1);
+        for (uint32_t i = go; i < ncls; i += Gj) {
+          // collapsed: class a' = i with the sigma = -1 form; else (a, sigma) = (i/2, i%2)
+          const uint32_t a = collapse ? i : i >> 1, s2 = collapse ? 0u : (i & 1u);
           float lo, hi;
           t_bounds(fmaf(2.0f, (float)a, s2 ? bp : bm), kb, kbB, lo, hi);
           const uint32_t bl = top_byte(lo), bh = top_byte(hi);
-          tbytes[a + 16u * s2] = (uint8_t)bh;
-          mine |= (uint32_t)(bl != bh) << (a + 16u * s2);
+          tbytes[a + 32u * s2] = (uint8_t)bh;
+          mine |= (unsigned long long)(bl != bh) << (a + 32u * s2);
         }
       }
       if (Gp <= 32u) {
@@ -526,17 +579,19 @@ __global__ void __launch_bounds__(kTile, 3) graph_half_kernel(const GraphJob* __
         vamb = mine;
         __syncwarp();
       } else {
-        if (go == 0u) sh.amb[vx] = 0u;
+        if (go == 0u) sh.amb[vx] = 0ull;
         __syncthreads();
-        if (mine != 0u) atomicOr(&sh.amb[vx], mine);
+        if (mine != 0ull) atomicOr(&sh.amb[vx], mine);
         __syncthreads();
         vamb = sh.amb[vx];
       }
     }
     uint32_t res = 0u;
     const bool hub = valid && d > kHubDeg;
-    // lanes of a class above 7 need the second half of the tables (warp-wide choice)
-    const bool wide = __any_sync(0xffffffffu, table && d > 7);
+    // table entries the warp's lanes need: a < 8, < 16 or < 32 (warp-wide choice)
+    // (collapsed: a' = a + sigma <= d + 1)
+    const int dn = collapse ? d + 1 : d;
+    const uint32_t nw = __reduce_max_sync(0xffffffffu, table ? (dn <= 7 ? 1u : dn <= 15 ? 2u : 4u) : 0u);
     uint32_t und = 0u;  // lanes left to the queue
     uint32_t S = 0u;
     if (valid && !hub) {
@@ -568,28 +623,47 @@ __global__ void __launch_bounds__(kTile, 3) graph_half_kernel(const GraphJob* __
         // threshold bytes R[m] (byte i: lane m + 8 i) and lanes of uncertain top byte
         uint32_t R[8], amb = 0u;
         if (table) {
-          const uint4 m0 = *reinterpret_cast<const uint4*>(&sh.tb[vx][0]);
-          const uint4 p4 = *reinterpret_cast<const uint4*>(&sh.tb[vx][4]);
-          if (vamb != 0u) {  // rare: lanes of the uncertain classes
+          if (vamb != 0ull) {  // rare: lanes of the uncertain classes
 #pragma unroll 1
             for (int k = 0; k < 32; ++k) {
-              const uint32_t a = (C[k & 7] >> (8 * (k >> 3))) & 0xFFu;
-              amb |= ((vamb >> (a + 16u * ((S >> k) & 1u))) & 1u) << k;
+              const uint32_t a = (C[k & 7] >> (8 * (k >> 3))) & 0xFFu, sk = (S >> k) & 1u;
+              const uint32_t c = collapse ? a + sk : a + 32u * sk;
+              amb |= (uint32_t)((vamb >> c) & 1ull) << k;
             }
           }
+          uint32_t Tm[8], Tp[8];
+          const uint4* tv = reinterpret_cast<const uint4*>(sh.tb[vx]);
+          const uint4 m0 = tv[0], p0v = tv[2];
+          Tm[0] = m0.x; Tm[1] = m0.y; Tm[2] = m0.z; Tm[3] = m0.w;
+          Tp[0] = p0v.x; Tp[1] = p0v.y; Tp[2] = p0v.z; Tp[3] = p0v.w;
+          if (nw == 4u) {
+            const uint4 m1 = tv[1], p1v = tv[3];
+            Tm[4] = m1.x; Tm[5] = m1.y; Tm[6] = m1.z; Tm[7] = m1.w;
+            Tp[4] = p1v.x; Tp[5] = p1v.y; Tp[6] = p1v.z; Tp[7] = p1v.w;
+          } else {
 #pragma unroll
-          for (int m = 0; m < 8; ++m) {
-            const uint32_t cnt = C[m];
-            const uint32_t x7 = cnt & 0x07070707u;
-            const uint32_t sel = __byte_perm(x7 | (x7 >> 4), 0u, 0x0020);
-            const uint32_t ms = ((S >> m) & 0x01010101u) * 0xFFu;
-            uint32_t vm = __byte_perm(m0.x, m0.y, sel), vp = __byte_perm(p4.x, p4.y, sel);
-            if (wide) {
-              const uint32_t m8 = ((cnt >> 3) & 0x01010101u) * 0xFFu;
-              vm = (__byte_perm(m0.z, m0.w, sel) & m8) | (vm & ~m8);
-              vp = (__byte_perm(p4.z, p4.w, sel) & m8) | (vp & ~m8);
+            for (int i = 4; i < 8; ++i) Tm[i] = Tp[i] = 0u;
+          }
+          if (collapse) {  // one table over a' = a + sigma (bytes: no carries, a' <= 31)
+            if (nw == 1u) {
+#pragma unroll
+              for (int m = 0; m < 8; ++m) R[m] = lookup_bytes_c<1>(Tm, C[m] + ((S >> m) & 0x01010101u));
+            } else if (nw == 2u) {
+#pragma unroll
+              for (int m = 0; m < 8; ++m) R[m] = lookup_bytes_c<2>(Tm, C[m] + ((S >> m) & 0x01010101u));
+            } else {
+#pragma unroll
+              for (int m = 0; m < 8; ++m) R[m] = lookup_bytes_c<4>(Tm, C[m] + ((S >> m) & 0x01010101u));
             }
-            R[m] = (vp & ms) | (vm & ~ms);
+          } else if (nw == 1u) {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) R[m] = lookup_bytes<1>(Tm, Tp, C[m], (S >> m) & 0x01010101u);
+          } else if (nw == 2u) {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) R[m] = lookup_bytes<2>(Tm, Tp, C[m], (S >> m) & 0x01010101u);
+          } else {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) R[m] = lookup_bytes<4>(Tm, Tp, C[m], (S >> m) & 0x01010101u);
           }
         } else {
 #pragma unroll

@@ -302,3 +302,24 @@ def test_full_size_anneal_step_sampled(S):
         for y in list(ys) + [x]:  # sigma' where the second half step reads it
             sr[y] = site(s0[r], int(y), 0, r)
         assert s1[r, x] == site(sr, x, 1, r), (x, r)
+
+
+@pytest.mark.parametrize("n,deg,R,q,beta", [(2000, 12.0, 64, 0.8, 0.7),   # classes (a, sigma)
+                                             (1500, 30.0, 32, 1.0, 0.3),   # collapsed, d <= 30
+                                             (1200, 5.0, 96, 1.0, 1.1)])   # collapsed, 3 groups
+def test_integer_graph_class_tables_bit_exact(S, n, deg, R, q, beta):
+    """One beta on every replica: the per-vertex class tables decide the lanes (class
+    (a, sigma) tables for q != 1; with q = 1 the collapsed tables over a + sigma, since
+    h(a, +1) = h(a + 1, -1) exactly), at every table width (degrees up to 7, 15, 31)
+    and above them through per-lane thresholds; bit-exact against the oracle."""
+    u, v, J, lam = er_instance(n, deg, 300 + n, lam_sd=0.2)
+    seed = 0x5348414B + 7 * n
+    ctx = S.shaken_init(graph_problem(S, n, u, v, J, R, beta, q=q, lam=lam), seed)
+    S.shaken_step(ctx, 3)
+    got = S.shaken_get_spins(ctx, R, n)
+    S.shaken_free(ctx)
+    tail, head = core.orient(u, v, 0)
+    o = core.graph_init(n, R, seed, 0)
+    o, _ = core.graph_run(o, tail, head, J.astype(np.float64), True, lam.astype(np.float64), q,
+                          beta, seed, 0, 3, draw=core.DRAW_PLANE)
+    assert np.array_equal(got, o)
