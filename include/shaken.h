@@ -300,12 +300,14 @@ shaken_status shaken_batch_set_rng_counter(shaken_batch* b, uint64_t* device_cou
 
 /* Autotuner of the lattice launch shape.  For every lattice encoding family of
  * a plan (a batch, or a context stepped on its own) the half-step kernel runs
- * with tiles of 256 lane words (one per thread) or 1024 (four per thread).
- * With autotuning on (the default) a family of at least one resident wave of
- * 1024-word tiles is timed once with both shapes -- trial launches of the
- * first half step that rewrite sigma' with the values the real step writes,
- * so no trajectory changes -- and the faster shape is cached per (encoding,
- * bit length of the lane-word count, bit length of the job count).  Off: a
+ * with tiles of 256 lane words (one per thread) or 1024 (four per thread), and
+ * with as many resident blocks per SM as fit or one fewer (each block then walks
+ * a longer range of tiles).  With autotuning on (the default) a family of at
+ * least one resident wave of 1024-word tiles is timed once in each of the four
+ * shapes -- trial launches of the first half step that rewrite sigma' with the
+ * values the real step writes, so no trajectory changes -- and the fastest shape
+ * is cached per (encoding, bit length of the lane-word count, bit length of the
+ * job count).  Off: a
  * fixed rule (four words per thread once the family fills eight waves).
  * Trajectories are bit-identical under every shape.
  * lattice_wpt returns the words per thread the plan uses for an encoding
@@ -318,6 +320,16 @@ shaken_status shaken_batch_set_autotune(shaken_batch* b, int on);
 shaken_status shaken_set_autotune(shaken_ctx* ctx, int on);
 shaken_status shaken_batch_lattice_wpt(shaken_batch* b, int encoding, int* words_per_thread);
 shaken_status shaken_lattice_wpt(shaken_ctx* ctx, int* words_per_thread);
+/* The full shape a batch plan uses for an encoding: lane words per thread and
+ * resident blocks per SM of its half-step kernel (0, 0 if it has no such family). */
+shaken_status shaken_batch_lattice_shape(shaken_batch* b, int encoding, int* words_per_thread,
+                                         int* blocks_per_sm);
+/* Pin the launch shape of a batch's family of an encoding (words per thread 1 or 4,
+ * blocks per SM from 1 to as many as fit), overriding the tuner; words_per_thread
+ * = 0 returns the family to the tuner.  Trajectories are the same in every shape.
+ * E_INVAL for other values. */
+shaken_status shaken_batch_set_lattice_shape(shaken_batch* b, int encoding, int words_per_thread,
+                                             int blocks_per_sm);
 shaken_status shaken_autotune_stats(uint64_t* trials, uint64_t* cached);
 shaken_status shaken_autotune_clear(void);
 

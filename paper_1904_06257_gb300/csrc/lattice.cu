@@ -1375,15 +1375,16 @@ cudaError_t launch_build_lattice_tables(const double* beta_lanes, int ntab, doub
 
 template <int ENC, int WPT>
 static cudaError_t launch_half_t(const LatJob* jobs, const Tile* tiles, int n_tiles, uint32_t half,
-                                 unsigned long long* rng_calls, cudaStream_t st) {
-  // one wave: every block resident, each walking a contiguous range of tiles
+                                 unsigned long long* rng_calls, int bps, cudaStream_t st) {
+  // one wave: every block resident, each walking a contiguous range of tiles;
+  // bps > 0 asks for fewer blocks per SM than fit (longer tile ranges per block)
   static int occ = 0;
   if (occ == 0) {
     int o = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lattice_half_kernel<ENC, WPT>, kTile, 0);
     occ = o > 0 ? o : 1;
   }
-  const int grid = grid_for(n_tiles, occ);
+  const int grid = grid_for(n_tiles, bps > 0 && bps < occ ? bps : occ);
   return launch_dependent(lattice_half_kernel<ENC, WPT>, dim3(grid), dim3(kTile), 0, st, jobs,
                           tiles, n_tiles, half, rng_calls);
 }
@@ -1399,20 +1400,34 @@ int lattice_resident_blocks() {
 
 cudaError_t launch_lattice_half(int enc, int wpt, const LatJob* jobs, const Tile* tiles,
                                 int n_tiles, uint32_t half, unsigned long long* rng_calls,
-                                cudaStream_t st) {
+                                cudaStream_t st, int bps) {
   if (n_tiles <= 0) return cudaSuccess;
   if (wpt == kWordsPerThread) {
     if (enc == kEncInt8)
-      return launch_half_t<kEncInt8, kWordsPerThread>(jobs, tiles, n_tiles, half, rng_calls, st);
+      return launch_half_t<kEncInt8, kWordsPerThread>(jobs, tiles, n_tiles, half, rng_calls, bps,
+                                                       st);
     if (enc == kEncPacked)
-      return launch_half_t<kEncPacked, kWordsPerThread>(jobs, tiles, n_tiles, half, rng_calls, st);
+      return launch_half_t<kEncPacked, kWordsPerThread>(jobs, tiles, n_tiles, half, rng_calls,
+                                                         bps, st);
     return launch_half_t<kEncMultispin, kWordsPerThread>(jobs, tiles, n_tiles, half, rng_calls,
-                                                         st);
+                                                         bps, st);
   }
-  if (enc == kEncInt8) return launch_half_t<kEncInt8, 1>(jobs, tiles, n_tiles, half, rng_calls, st);
+  if (enc == kEncInt8)
+    return launch_half_t<kEncInt8, 1>(jobs, tiles, n_tiles, half, rng_calls, bps, st);
   if (enc == kEncPacked)
-    return launch_half_t<kEncPacked, 1>(jobs, tiles, n_tiles, half, rng_calls, st);
-  return launch_half_t<kEncMultispin, 1>(jobs, tiles, n_tiles, half, rng_calls, st);
+    return launch_half_t<kEncPacked, 1>(jobs, tiles, n_tiles, half, rng_calls, bps, st);
+  return launch_half_t<kEncMultispin, 1>(jobs, tiles, n_tiles, half, rng_calls, bps, st);
+}
+
+int lattice_blocks_per_sm(int wpt) {
+  int o = 1;
+  if (wpt == kWordsPerThread)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &o, lattice_half_kernel<kEncMultispin, kWordsPerThread>, kTile, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lattice_half_kernel<kEncMultispin, 1>,
+                                                  kTile, 0);
+  return o > 0 ? o : 1;
 }
 
 cudaError_t launch_lattice_init(int enc, int wpt, const LatJob* jobs, const Tile* tiles,

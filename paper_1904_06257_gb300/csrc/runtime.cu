@@ -33,8 +33,9 @@
 namespace shk {
 cudaError_t launch_build_lattice_tables(const double*, int, double, double, double, LatTable*,
                                         cudaStream_t);
+int lattice_blocks_per_sm(int);
 cudaError_t launch_lattice_half(int, int, const LatJob*, const Tile*, int, uint32_t,
-                                unsigned long long*, cudaStream_t);
+                                unsigned long long*, cudaStream_t, int);
 int lattice_resident_blocks();
 cudaError_t run_microbench(int, double*, double*);
 cudaError_t launch_lattice_init(int, int, const LatJob*, const Tile*, int, int, cudaStream_t);
@@ -134,6 +135,7 @@ struct Family {
   int kind = 0;  // 0 lattice, 1 graph
   int enc = 0;   // lattice encoding; graph: 1 integer couplings, 0 real
   int wpt = 1;   // lattice: lane words per thread per tile (tile = 256 wpt words)
+  int bps = 0;   // lattice: resident blocks per SM of the half step (0: as many as fit)
   DevMem jobs, tiles;  // graph: multi-group jobs and (vertex, group) pair tiles (half steps)
   int n_tiles = 0;
   DevMem ojobs, otiles;  // graph: one job per group and vertex tiles (init, observables)
@@ -151,6 +153,7 @@ struct Plan {
   uint64_t graph_launches = 0;
   bool dirty = true;
   bool autotune = true;  // pick the lattice tile shape by timing trial launches
+  int pinned[3][2] = {{0, 0}, {0, 0}, {0, 0}};  // per lattice encoding: (wpt, bps) set by the caller
   int blocks_per_sm = 8;
   int timing = 0;           // bracket the half-step launches of every timing-th step (0: off)
   uint64_t steps_issued = 0;  // non-graph steps launched (for the timing stride)
@@ -288,7 +291,7 @@ struct TuneKey {
   }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, int> g_tune;
+std::map<TuneKey, std::pair<int, int>> g_tune;  // -> (words per thread, blocks per SM)
 std::atomic<uint64_t> g_tune_trials{0};
 
 int bit_length(uint64_t x) {
@@ -310,8 +313,8 @@ struct EventPair {
 }  // namespace
 
 // Mean device time (ms) of one position-0 half-step launch with tiles of kTile * wpt
-// lane words: 3 timed launches after one warm-up.
-static shaken_status trial_lattice(int enc, int wpt, const DevMem& jobs_dev,
+// lane words and bps blocks per SM: 3 timed launches after one warm-up.
+static shaken_status trial_lattice(int enc, int wpt, int bps, const DevMem& jobs_dev,
                                    const std::vector<LatJob>& jobs, cudaStream_t st, float* ms) {
   std::vector<Tile> tiles;
   lattice_tiles(jobs, (uint32_t)(kTile * wpt), tiles);
@@ -321,11 +324,12 @@ static shaken_status trial_lattice(int enc, int wpt, const DevMem& jobs_dev,
   CU(cudaEventCreate(&ev.a));
   CU(cudaEventCreate(&ev.b));
   const int nt = (int)tiles.size();
-  CU(shk::launch_lattice_half(enc, wpt, jobs_dev.as<LatJob>(), td.as<Tile>(), nt, 0u, nullptr, st));
+  CU(shk::launch_lattice_half(enc, wpt, jobs_dev.as<LatJob>(), td.as<Tile>(), nt, 0u, nullptr, st,
+                              bps));
   CU(cudaEventRecord(ev.a, st));
   for (int r = 0; r < 3; ++r)
     CU(shk::launch_lattice_half(enc, wpt, jobs_dev.as<LatJob>(), td.as<Tile>(), nt, 0u, nullptr,
-                                st));
+                                st, bps));
   CU(cudaEventRecord(ev.b, st));
   CU(cudaEventSynchronize(ev.b));
   float t = 0.0f;
@@ -334,18 +338,29 @@ static shaken_status trial_lattice(int enc, int wpt, const DevMem& jobs_dev,
   return SHAKEN_OK;
 }
 
-static shaken_status choose_lattice_wpt(const Plan& P, int enc, const std::vector<LatJob>& jobs,
-                                        cudaStream_t st, int* wpt) {
+// Launch shape of a lattice family: lane words per thread (1 or kWordsPerThread) and
+// resident blocks per SM of the half step (every block that fits, or one fewer, so
+// that each block walks a longer range of tiles).  A shape is {wpt, bps}, bps = 0
+// meaning as many as fit.
+struct LatShape {
+  int wpt = 1, bps = 0;
+};
+
+static shaken_status choose_lattice_shape(const Plan& P, int enc, const std::vector<LatJob>& jobs,
+                                          cudaStream_t st, LatShape* out) {
+  if (P.pinned[enc][0] != 0) {  // a shape pinned by the caller
+    out->wpt = P.pinned[enc][0];
+    out->bps = P.pinned[enc][1];
+    return SHAKEN_OK;
+  }
   uint64_t words = 0;
   for (const LatJob& J : jobs) words += J.nwords;
   const uint64_t wave = (uint64_t)shk::lattice_resident_blocks();
   const uint64_t big_tiles = words / (uint64_t)shk::kLatTile;
-  if (big_tiles < wave) {  // not one wave of large tiles: one lane word per thread
-    *wpt = 1;
-    return SHAKEN_OK;
-  }
+  *out = LatShape{};
+  if (big_tiles < wave) return SHAKEN_OK;  // not one wave of large tiles: one word per thread
   if (!P.autotune) {  // fixed rule: large tiles once the family fills 8 waves
-    *wpt = big_tiles >= 8 * wave ? shk::kWordsPerThread : 1;
+    out->wpt = big_tiles >= 8 * wave ? shk::kWordsPerThread : 1;
     return SHAKEN_OK;
   }
   const TuneKey key{enc, bit_length(words), bit_length(jobs.size())};
@@ -353,7 +368,8 @@ static shaken_status choose_lattice_wpt(const Plan& P, int enc, const std::vecto
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      *wpt = it->second;
+      out->wpt = it->second.first;
+      out->bps = it->second.second;
       return SHAKEN_OK;
     }
   }
@@ -361,21 +377,25 @@ static shaken_status choose_lattice_wpt(const Plan& P, int enc, const std::vecto
   for (LatJob& J : trial) J.sums = nullptr;
   DevMem jd;
   TRY(upload(jd, trial.data(), trial.size() * sizeof(LatJob), st));
-  const int cands[2] = {1, shk::kWordsPerThread};
   float best = 0.0f;
-  int pick = 1;
-  for (int i = 0; i < 2; ++i) {
-    float ms = 0.0f;
-    TRY(trial_lattice(enc, cands[i], jd, trial, st, &ms));
-    if (i == 0 || ms < best) {
-      best = ms;
-      pick = cands[i];
+  bool first = true;
+  for (int wpt : {1, shk::kWordsPerThread}) {
+    const int occ = shk::lattice_blocks_per_sm(wpt);
+    for (int bps : {0, occ - 1}) {
+      if (bps < 0 || (bps == occ - 1 && occ <= 1)) continue;
+      float ms = 0.0f;
+      TRY(trial_lattice(enc, wpt, bps, jd, trial, st, &ms));
+      if (first || ms < best) {
+        best = ms;
+        out->wpt = wpt;
+        out->bps = bps;
+        first = false;
+      }
     }
   }
   g_tune_trials.fetch_add(1);
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[key] = pick;
-  *wpt = pick;
+  g_tune[key] = {out->wpt, out->bps};
   return SHAKEN_OK;
 }
 
@@ -473,18 +493,19 @@ static shaken_status build_plan(Plan& P, cudaStream_t st) {
       }
     }
   }
-  int lat_wpt[3] = {1, 1, 1};
+  LatShape lat_shape[3];
   for (int e = 0; e < 3; ++e) {
     if (ljobs[e].empty()) continue;
-    TRY(choose_lattice_wpt(P, e, ljobs[e], st, &lat_wpt[e]));
-    lattice_tiles(ljobs[e], (uint32_t)(kTile * lat_wpt[e]), tiles[e]);
+    TRY(choose_lattice_shape(P, e, ljobs[e], st, &lat_shape[e]));
+    lattice_tiles(ljobs[e], (uint32_t)(kTile * lat_shape[e].wpt), tiles[e]);
   }
   for (int e = 0; e < 3; ++e) {
     if (ljobs[e].empty()) continue;
     auto F = std::make_unique<Family>();
     F->kind = 0;
     F->enc = e;
-    F->wpt = lat_wpt[e];
+    F->wpt = lat_shape[e].wpt;
+    F->bps = lat_shape[e].bps;
     TRY(upload(F->jobs, ljobs[e].data(), ljobs[e].size() * sizeof(LatJob), st));
     TRY(upload(F->tiles, tiles[e].data(), tiles[e].size() * sizeof(Tile), st));
     F->n_tiles = (int)tiles[e].size();
@@ -547,7 +568,7 @@ static shaken_status plan_step_launch(Plan& P, cudaStream_t st, uint64_t* nl,
       }
       if (F->kind == 0)
         CU(shk::launch_lattice_half(F->enc, F->wpt, F->jobs.as<LatJob>(), F->tiles.as<Tile>(),
-                                    F->n_tiles, half, P.rng_counter, st));
+                                    F->n_tiles, half, P.rng_counter, st, F->bps));
       else
         CU(shk::launch_graph_half(F->enc != 0, F->jobs.as<GraphJob>(), F->tiles.as<Tile>(),
                                   F->n_tiles, half, ex, P.blocks_per_sm, st));
@@ -1664,6 +1685,24 @@ shaken_status shaken_batch_set_autotune(shaken_batch* b, int on) {
   return SHAKEN_OK;
 }
 
+shaken_status shaken_batch_set_lattice_shape(shaken_batch* b, int encoding, int words_per_thread,
+                                             int blocks_per_sm) {
+  if (!b || encoding < 0 || encoding > 2) return fail(SHAKEN_E_INVAL, "bad batch or encoding");
+  if (words_per_thread == 0) {  // back to the tuner
+    b->plan.pinned[encoding][0] = b->plan.pinned[encoding][1] = 0;
+  } else {
+    if (words_per_thread != 1 && words_per_thread != shk::kWordsPerThread)
+      return fail(SHAKEN_E_INVAL, "words per thread must be 1 or 4");
+    const int occ = shk::lattice_blocks_per_sm(words_per_thread);
+    if (blocks_per_sm < 1 || blocks_per_sm > occ)
+      return fail(SHAKEN_E_INVAL, "blocks per SM must be in [1, " + std::to_string(occ) + "]");
+    b->plan.pinned[encoding][0] = words_per_thread;
+    b->plan.pinned[encoding][1] = blocks_per_sm == occ ? 0 : blocks_per_sm;
+  }
+  b->plan.invalidate();
+  return SHAKEN_OK;
+}
+
 shaken_status shaken_set_autotune(shaken_ctx* ctx, int on) {
   if (!ctx) return fail(SHAKEN_E_INVAL, "NULL context");
   ctx->solo.autotune = on != 0;
@@ -1690,6 +1729,25 @@ shaken_status shaken_lattice_wpt(shaken_ctx* ctx, int* words_per_thread) {
   if (ctx->kind != SHAKEN_LATTICE) return fail(SHAKEN_E_INVAL, "not a lattice context");
   if (ctx->owner) return fail(SHAKEN_E_STATE, "context belongs to a batch");
   return plan_lattice_wpt(ctx->solo, ctx->stream, ctx->enc, words_per_thread);
+}
+
+static shaken_status plan_lattice_shape(Plan& P, cudaStream_t st, int enc, int* wpt, int* bps) {
+  if (!wpt || !bps || enc < 0 || enc > 2) return fail(SHAKEN_E_INVAL, "bad encoding or NULL output");
+  if (P.dirty) TRY(build_plan(P, st));
+  *wpt = 0;
+  *bps = 0;
+  for (auto& F : P.fams)
+    if (F->kind == 0 && F->enc == enc) {
+      *wpt = F->wpt;
+      *bps = F->bps > 0 ? F->bps : shk::lattice_blocks_per_sm(F->wpt);
+    }
+  return SHAKEN_OK;
+}
+
+shaken_status shaken_batch_lattice_shape(shaken_batch* b, int encoding, int* words_per_thread,
+                                         int* blocks_per_sm) {
+  if (!b) return fail(SHAKEN_E_INVAL, "NULL batch");
+  return plan_lattice_shape(b->plan, b->stream, encoding, words_per_thread, blocks_per_sm);
 }
 
 shaken_status shaken_autotune_stats(uint64_t* trials, uint64_t* cached) {

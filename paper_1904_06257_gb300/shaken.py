@@ -97,6 +97,9 @@ def _load():
         "shaken_batch_set_autotune": [vp, ctypes.c_int],
         "shaken_set_autotune": [vp, ctypes.c_int],
         "shaken_batch_lattice_wpt": [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+        "shaken_batch_lattice_shape": [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int)],
+        "shaken_batch_set_lattice_shape": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int],
         "shaken_lattice_wpt": [vp, ctypes.POINTER(ctypes.c_int)],
         "shaken_autotune_stats": [ctypes.POINTER(u64), ctypes.POINTER(u64)],
         "shaken_autotune_clear": [],
@@ -342,6 +345,17 @@ def shaken_batch_set_autotune(batch, on: bool):
 
 def shaken_set_autotune(ctx, on: bool):
     _check(_lib.shaken_set_autotune(ctx, int(bool(on))))
+
+
+def shaken_batch_set_lattice_shape(b, encoding: int, words_per_thread: int, blocks_per_sm: int):
+    _check(_lib.shaken_batch_set_lattice_shape(b, int(encoding), int(words_per_thread),
+                                               int(blocks_per_sm)))
+
+
+def shaken_batch_lattice_shape(b, encoding: int):
+    w, p = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.shaken_batch_lattice_shape(b, int(encoding), ctypes.byref(w), ctypes.byref(p)))
+    return w.value, p.value
 
 
 def shaken_batch_lattice_wpt(batch, encoding: int) -> int:

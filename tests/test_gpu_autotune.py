@@ -75,6 +75,39 @@ def test_trials_leave_no_trace_and_results_are_cached(S):
     free_batch(S, b, ctxs)
 
 
+def test_every_launch_shape_gives_the_same_trajectory(S):
+    """The tuner's two knobs -- lane words per thread (1, 4) and resident blocks per SM
+    (every block that fits, or fewer) -- change only how tiles are spread over blocks:
+    pinned in each shape, a batch of uneven groups follows the same trajectory, equal to
+    the oracle's at sampled groups; the tuner's own choice is one of these shapes."""
+    Ls = [512, 256, 512, 64]
+    betas = W.beta_grid(32 * len(Ls), 0.3, 0.6, 64)
+    seeds = [W.BASE_SEED + 50 + g for g in range(len(Ls))]
+    b, ctxs = batch_of(S, Ls, betas, seeds, True)
+    wpt, bps = S.shaken_batch_lattice_shape(b, S.MULTISPIN)
+    assert wpt in (1, 4) and bps >= 1
+    free_batch(S, b, ctxs)
+    results = []
+    for w in (1, 4):
+        for p in (1, 2):
+            b, ctxs = batch_of(S, Ls, betas, seeds, True)
+            S.shaken_batch_set_lattice_shape(b, S.MULTISPIN, w, p)
+            assert S.shaken_batch_lattice_shape(b, S.MULTISPIN) == (w, p)
+            S.shaken_batch_step(b, 4, False)
+            S.shaken_batch_sync(b)
+            results.append([S.shaken_get_spins(c, 32, int(L) * int(L)) for c, L in zip(ctxs, Ls)])
+            with pytest.raises(S.ShakenError):
+                S.shaken_batch_set_lattice_shape(b, S.MULTISPIN, 2, 1)
+            free_batch(S, b, ctxs)
+    for r in results[1:]:
+        for a, ref in zip(r, results[0]):
+            assert np.array_equal(a, ref)
+    L = Ls[3]
+    o = core.lattice_init(L, 32, seeds[3], core.MODE_MULTISPIN, 0)
+    o, _ = core.lattice_run(o, 1.0, 1.0, 0.0, betas[96:128], seeds[3], 0, 4, core.MODE_MULTISPIN)
+    assert np.array_equal(results[0][3].reshape(32, L, L), o)
+
+
 def test_small_family_is_not_tuned(S):
     t0, _ = S.shaken_autotune_stats()
     ctx = S.shaken_init(lattice_problem(S, S.MULTISPIN, 64, 32, W.beta_grid(32)), 5)

@@ -64,3 +64,54 @@ def test_two_rank_sharding_gloo():
     s1, _ = core.lattice_run(s0, 1.0, 1.0, 0.0, betas[32 * g1:32 * g1 + 32], seeds[g1], 0, 2,
                              core.MODE_MULTISPIN)
     assert int(s1.sum()) == sum1
+
+
+def _agg_worker(rank, world, port, q, planted):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    Ls, _, seeds = bench.workload(rank)
+    steps = 20
+    ms = 10.0 * (rank + 1)  # a fake per-rank duration: rank 1 is the slow one
+    upd = bench.updates_per_step(Ls) * steps
+    if planted:  # a plausible mistake: every rank also counts the others' updates
+        upd *= world
+    value, ms_max = bench.aggregate(upd, ms, world)
+    q.put((rank, len(seeds), value, ms_max))
+    dist.destroy_process_group()
+
+
+def _run_agg(planted):
+    ctx = tmp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_agg_worker, args=(r, 2, port, q, planted)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=300) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    return res
+
+
+def _check_agg(res):
+    import bench
+    # the job: every rank's own groups (weak scaling), summed, over the slowest rank
+    expected = sum(bench.updates_per_step(bench.workload(r)[0]) * 20 for r in range(2)) / 0.020
+    for rank, ngroups, value, ms_max in res:
+        assert ngroups == bench.GROUPS
+        assert ms_max == 20.0
+        assert abs(value - expected) <= 1e-9 * expected, (value, expected)
+
+
+def test_bench_rank_aggregation_gloo():
+    """bench.py's rank path (bench.aggregate over gloo, world size 2) with fake per-rank
+    times: value = the updates of both ranks' groups over the slower rank's time, the
+    same on every rank; a planted double count of the updates is rejected."""
+    pytest.importorskip("torch.distributed")
+    _check_agg(_run_agg(False))
+    with pytest.raises(AssertionError):
+        _check_agg(_run_agg(True))
