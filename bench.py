@@ -996,7 +996,7 @@ def main():
                     help="steps per job = U[1000, 20000] x this factor")
     ap.add_argument("--serve-pool", type=int, default=12, help="pre-generated graphs")
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
-    ap.add_argument("--serve-work-cap", type=float, default=1.5e9,
+    ap.add_argument("--serve-work-cap", type=float, default=3e8,
                     help="site updates per step of the server's running set")
     ap.add_argument("--serve-timeout", type=float, default=120.0)
     args = ap.parse_args()

@@ -365,7 +365,8 @@ shaken_status shaken_server_submit(shaken_server* s, const shaken_problem* p, ui
 /* Admission policy (no counterpart in the paper; serving is this library's own
  * use of the anneal).  Besides the memory budget, a queued job is admitted only
  * while the running jobs' work per full step -- the sum of 2 n R site updates --
- * stays at or below max_step_updates (default 1.5e9); a job larger than the cap
+ * stays at or below max_step_updates (default 3e8, about a millisecond of GPU work per
+ * step); a job larger than the cap
  * runs when nothing else does.  Bounding the work in flight keeps the GPU's rate
  * on the running jobs, so under overload jobs keep completing while the queue
  * grows.  order 0 (default): arrival order, first fit -- a job that does not fit

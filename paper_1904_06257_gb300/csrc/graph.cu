@@ -68,6 +68,15 @@ __device__ __forceinline__ void t_bounds(float hf, float kb, float kbB, float& l
   hi = fminf(T + D, 4294967296.0f);
 }
 
+// A field of exactly 0 gives T = 2^31 exactly (p = 1/2), on a byte boundary where the
+// fp32 bounds cannot fix the top byte: with integer couplings and lambda = 0 (or q
+// canceling lambda) it is a whole class of lanes.  When the fp32 field is 0, the fp64
+// field (the rounding order of the threshold's definition) decides whether T is
+// exactly 2^31.
+__device__ __noinline__ bool field_is_zero(int s, int sig, double q, float lam) {
+  return field_h(1.0, s, q, sig ? 1 : -1, (double)lam) == 0.0;
+}
+
 // Top byte of a value in [0, 2^32] (2^32, i.e. T that always accepts, maps to 255: a
 // lane whose draw has top byte 255 is then left to the per-lane decision).
 __device__ __forceinline__ uint32_t top_byte(float v) {
@@ -180,7 +189,9 @@ __device__ __noinline__ bool decide_lane(uint32_t key0, uint32_t key1, uint32_t 
                                          float kb, float kbB, double beta, bool force_exact) {
   float lo = 0.0f, hi = 4294967296.0f;
   if (!force_exact) {
-    t_bounds(fmaf(2.0f, (float)a, sig ? bp : bm), kb, kbB, lo, hi);
+    const float hf = fmaf(2.0f, (float)a, sig ? bp : bm);
+    t_bounds(hf, kb, kbB, lo, hi);
+    if (hf == 0.0f && field_is_zero(2 * a - d, sig, q, lam)) lo = hi = 2147483648.0f;  // T = 2^31
     if ((float)(u8 + 1u) * 16777216.0f <= lo) return true;  // u < (u8 + 1) 2^24 <= T
     if ((float)u8 * 16777216.0f >= hi) return false;        // u >= u8 2^24 >= T
   }
@@ -209,7 +220,7 @@ __device__ __noinline__ bool decide_lane(uint32_t key0, uint32_t key1, uint32_t 
 // lanes whose top byte is not certain (bit k).
 __device__ __noinline__ uint2 lane_bytes(uint32_t cnt, uint32_t S, int m, float bp, float bm,
                                          float B, const double* __restrict__ beta_lane,
-                                         float kb_uni, bool uni) {
+                                         float kb_uni, bool uni, int d, double q, float lam) {
   float kbl[4];
   if (uni) {  // (kept out of the lane loop: an fp64 product per lane is slow here)
 #pragma unroll
@@ -223,9 +234,12 @@ __device__ __noinline__ uint2 lane_bytes(uint32_t cnt, uint32_t S, int m, float 
   for (int i = 0; i < 4; ++i) {
     const int k = m + 8 * i;
     const int a = (int)((cnt >> (8 * i)) & 0xFFu);
+    const int sig = (int)((S >> k) & 1u);
+    const float hf = fmaf(2.0f, (float)a, sig ? bp : bm);
     float lo, hi;
-    t_bounds(fmaf(2.0f, (float)a, ((S >> k) & 1u) ? bp : bm), kbl[i], fabsf(kbl[i]) * B, lo, hi);
-    const uint32_t bl = top_byte(lo), bh = top_byte(hi);
+    t_bounds(hf, kbl[i], fabsf(kbl[i]) * B, lo, hi);
+    uint32_t bl = top_byte(lo), bh = top_byte(hi);
+    if (hf == 0.0f && field_is_zero(2 * a - d, sig, q, lam)) bl = bh = 0x80u;  // T = 2^31
     r |= bh << (8 * i);
     am |= (uint32_t)(bl != bh) << k;
   }
@@ -567,9 +581,11 @@ __global__ void __launch_bounds__(kTile, 3) graph_half_kernel(const GraphJob* __
         for (uint32_t i = go; i < ncls; i += Gj) {
           // collapsed: class a' = i with the sigma = -1 form; else (a, sigma) = (i/2, i%2)
           const uint32_t a = collapse ? i : i >> 1, s2 = collapse ? 0u : (i & 1u);
+          const float hf = fmaf(2.0f, (float)a, s2 ? bp : bm);
           float lo, hi;
-          t_bounds(fmaf(2.0f, (float)a, s2 ? bp : bm), kb, kbB, lo, hi);
-          const uint32_t bl = top_byte(lo), bh = top_byte(hi);
+          t_bounds(hf, kb, kbB, lo, hi);
+          uint32_t bl = top_byte(lo), bh = top_byte(hi);
+          if (hf == 0.0f && field_is_zero(2 * (int)a - d, (int)s2, J.q, lam)) bl = bh = 0x80u;
           tbytes[a + 32u * s2] = (uint8_t)bh;
           mine |= (unsigned long long)(bl != bh) << (a + 32u * s2);
         }
@@ -668,7 +684,7 @@ __global__ void __launch_bounds__(kTile, 3) graph_half_kernel(const GraphJob* __
         } else {
 #pragma unroll
           for (int m = 0; m < 8; ++m) {
-            const uint2 rb = lane_bytes(C[m], S, m, bp, bm, B, beta_g, kbu, uni);
+            const uint2 rb = lane_bytes(C[m], S, m, bp, bm, B, beta_g, kbu, uni, d, J.q, lam);
             R[m] = rb.x;
             amb |= rb.y;
           }

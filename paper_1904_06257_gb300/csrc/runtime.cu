@@ -1873,7 +1873,7 @@ static constexpr int kServerMaxSkips = 8;
 
 struct shaken_server {
   size_t budget = 0, used = 0;
-  double work_cap = 1.5e9;  // site updates per step of the running set
+  double work_cap = 3e8;    // site updates per step of the running set
   double work = 0.0;        // of the running jobs
   int order = 0;            // 0 arrival order (first fit, aging), 1 shortest total work first
   bool keep_states = false;

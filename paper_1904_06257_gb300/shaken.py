@@ -471,7 +471,7 @@ def shaken_server_poll(server, job_id: int) -> int:
     return st.value
 
 
-def shaken_server_set_policy(server, max_step_updates: float = 1.5e9, order: int = 0,
+def shaken_server_set_policy(server, max_step_updates: float = 3e8, order: int = 0,
                              keep_states: bool = False):
     _check(_lib.shaken_server_set_policy(server, float(max_step_updates), int(order),
                                          int(bool(keep_states))))
