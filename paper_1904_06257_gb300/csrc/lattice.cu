@@ -1060,7 +1060,9 @@ __global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* _
 // (halo rows; the lattice wraps).  After each half step every block publishes the
 // first and the last row it computed to a global exchange area (two sets by
 // half-step parity, so a row is not overwritten while a neighbour may still read
-// it), passes a grid barrier and copies its neighbours' rows into its halo rows.
+// it), raises its published-half-step count, and before the next half step waits
+// for the counts of its two neighbours only and copies their rows into its halo
+// rows; one grid barrier at the end of the run decides whether it is committed.
 // The draws, thresholds and decisions are those of lattice_half_kernel (head of
 // four words per thread, eight planes, a per-warp queue for the words still
 // undecided), so the trajectory is the same.
@@ -1116,6 +1118,50 @@ __device__ __forceinline__ uint32_t band_wait(BandSync* bs, uint32_t& gen, uint3
     *s_flag = f;
   }
   gen += 1u;
+  __syncthreads();
+  return *s_flag;
+}
+
+// Neighbour exchange between half steps: flags[b] counts the half steps whose first
+// and last rows block b has published (release after a fence, like band_arrive);
+// before reading its halo rows for half step h a block waits until both neighbours'
+// counts reach h + 1 (acquire).  A block cannot publish half step h + 2 into the
+// exchange set of h before both neighbours published h + 1, i.e. after they read h,
+// so two sets suffice.  The waits end on the same deadline and error flag as the
+// grid barrier; a block giving up aborts the run (commit 0 -> 2).
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void band_publish(uint32_t* flags, uint32_t b, uint32_t count) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flags + b),
+                                     "r"(count) : "memory");
+}
+
+// Returns 0 to go on, 1 to return without writing (the run is aborted).
+__device__ __forceinline__ uint32_t band_wait_nbrs(BandSync* bs, const uint32_t* flags,
+                                                   uint32_t up, uint32_t dn, uint32_t count,
+                                                   uint32_t* s_flag) {
+  if (threadIdx.x == 0) {
+    const uint64_t t0 = global_ns();
+    uint32_t polls = 0, f = 0u;
+    while (ld_acquire_u32(flags + up) < count || ld_acquire_u32(flags + dn) < count) {
+      if (atomicAdd(&bs->err, 0u) != 0u || global_ns() - t0 > kBandWaitNs ||
+          ++polls > kBandPollLimit) {
+        atomicExch(&bs->err, 1u);
+        atomicCAS(&bs->commit, 0u, 2u);
+        f = 1u;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+    *s_flag = f;
+  }
   __syncthreads();
   return *s_flag;
 }
@@ -1270,8 +1316,8 @@ __device__ __forceinline__ void band_decide(const LatJob& J, const LatTable& tab
 // xch: exchange area, [2 parities][G blocks][first row, last row][wpr words].
 template <int ENC>
 __global__ void __launch_bounds__(kTile, kBandMinBlocks) lattice_band_kernel(
-    const LatJob* __restrict__ jobs, uint32_t* __restrict__ xch, BandSync* __restrict__ bs,
-    uint32_t t0, uint32_t n_steps) {
+    const LatJob* __restrict__ jobs, uint32_t* __restrict__ xch, uint32_t* __restrict__ flags,
+    BandSync* __restrict__ bs, uint32_t t0, uint32_t n_steps) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ LatTable stab;
   __shared__ LatJob sJ;  // the job descriptor, read from shared memory
@@ -1325,14 +1371,11 @@ __global__ void __launch_bounds__(kTile, kBandMinBlocks) lattice_band_kernel(
         __stcg(mine + c, out[wpr + c]);
         __stcg(mine + wpr + c, out[nr * wpr + c]);
       }
-      band_arrive(bs, gen);
+      const uint32_t count = 2u * st + pos + 1u;  // half steps published so far
+      band_publish(flags, b, count);
       band_decide(J, stab, in, out, Ri, w_first, wpr, typ, K, P, q, calls);
-      const uint32_t w = band_wait(bs, gen, &s_flag, st + 1u == n_steps && pos == 1u);
-      if (w == 1u) return;
-      if (w == 2u) {
-        write_back = true;
-        break;
-      }
+      if (band_wait_nbrs(bs, flags, (b + G - 1u) % G, (b + 1u) % G, count, &s_flag) != 0u)
+        return;
       const uint32_t* above = xch + ((size_t)pos * G + (b + G - 1u) % G) * 2u * wpr + wpr;
       const uint32_t* below = xch + ((size_t)pos * G + (b + 1u) % G) * 2u * wpr;
       for (uint32_t c = threadIdx.x; c < wpr; c += blockDim.x) {
@@ -1341,8 +1384,12 @@ __global__ void __launch_bounds__(kTile, kBandMinBlocks) lattice_band_kernel(
       }
       __syncthreads();
     }
-    if (write_back) break;
   }
+  // one grid barrier for the whole chunk: every block has finished its last half step
+  band_arrive(bs, gen);
+  const uint32_t w = band_wait(bs, gen, &s_flag, true);
+  if (w == 1u) return;
+  write_back = w == 2u;
   if (!write_back) {
     // every block passed the last barrier: commit (0 -> 1) unless a block that gave
     // up has already aborted the run (2); the chunk is written back only if committed
@@ -1504,10 +1551,11 @@ bool lattice_band_shape(int enc, uint32_t L, uint32_t wpr, int* grid, size_t* sm
 // n steps of the one job in `jobs` by the banded kernel (cooperative launch; the
 // grid and shared memory from lattice_band_shape; bs zeroed by the caller).
 cudaError_t launch_lattice_band(int enc, const LatJob* jobs, int grid, size_t smem,
-                                uint32_t* xch, BandSync* bs, uint32_t t0, uint32_t n_steps,
-                                cudaStream_t st) {
+                                uint32_t* xch, uint32_t* flags, BandSync* bs, uint32_t t0,
+                                uint32_t n_steps, cudaStream_t st) {
   if (n_steps == 0) return cudaSuccess;
-  void* args[] = {(void*)&jobs, (void*)&xch, (void*)&bs, (void*)&t0, (void*)&n_steps};
+  void* args[] = {(void*)&jobs, (void*)&xch, (void*)&flags, (void*)&bs, (void*)&t0,
+                  (void*)&n_steps};
   const void* k = enc == kEncInt8 ? (const void*)lattice_band_kernel<kEncInt8>
                                   : (const void*)lattice_band_kernel<kEncPacked>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
