@@ -393,6 +393,9 @@ def run_ours(args, rank, world, local_rank):
                         "comparison stops drawing once all 32 lanes of a word are decided",
                 "calls_per_launch": calls_per_launch,
                 "frac_of_measured_philox": done / rates["philox_calls"],
+                # the calls plus the plane comparisons they feed, one pipe after the other
+                "calls_plus_planes": calls_plus_planes(calls_per_launch, avg_kernel_s, rates,
+                                                       sms),
                 "peak_source": f"derived: {sms} SMs x {sm_max_mhz():.0f} MHz x "
                                f"{WIDE_MUL_PER_CLK_PER_SM} wide multiplies/clk/SM / "
                                f"{WIDE_MUL_PER_CALL} per call",
@@ -469,6 +472,7 @@ MICROBENCH_KINDS = ("philox_calls", "lop3", "imad", "lop3_imad_mix", "mad_wide",
 ALG_CALLS_PER_UPDATE = 0.25   # one 32-bit uniform per site update = 1/4 Philox-4x32-10 call
 WIDE_MUL_PER_CLK_PER_SM = 32  # 32 x 32 -> 64-bit multiplies: 8 lanes/clk on each of 4 SMSPs
 WIDE_MUL_PER_CALL = 20        # 10 rounds x 2
+LOP3_PER_CLK_PER_SM = 64      # 32-bit logic operations: 16 lanes/clk on each of 4 SMSPs
 SM_MAX_MHZ_FALLBACK = 2070.0
 
 
@@ -478,6 +482,28 @@ def sm_max_mhz() -> float:
             return float(json.load(f)["sm_max_mhz"])
     except (OSError, KeyError, ValueError):
         return SM_MAX_MHZ_FALLBACK
+
+
+PLANE_OPS_PER_CALL = 16        # 4 planes x (select, complement, borrow, equality): mirror tables
+LOP3_PER_CALL = 20             # 10 rounds x one three-input XOR for each of the two new words
+
+
+def calls_plus_planes(calls: float, launch_s: float, rates: dict, sms: int) -> dict:
+    """Launch-time bound of the multispin half step from the work it performs: the
+    Philox calls it makes and the four logic operations per plane it compares for
+    each call, the two kinds of work taken one after the other (no overlap).  Once
+    with the measured rates of the microbenchmarks (Philox calls/s, LOP3/s), once
+    with the rates the units allow (wide multiplies and LOP3 lanes per clock)."""
+    meas = calls / rates["philox_calls"] + calls * PLANE_OPS_PER_CALL / rates["lop3"]
+    clk = sms * sm_max_mhz() * 1e6
+    unit = (calls * WIDE_MUL_PER_CALL / (WIDE_MUL_PER_CLK_PER_SM * clk)
+            + calls * (LOP3_PER_CALL + PLANE_OPS_PER_CALL) / (LOP3_PER_CLK_PER_SM * clk))
+    return {"plane_ops_per_call": PLANE_OPS_PER_CALL,
+            "bound_ms_measured_rates": meas * 1e3, "frac_measured_rates": meas / launch_s,
+            "bound_ms_unit_rates": unit * 1e3, "frac_unit_rates": unit / launch_s,
+            "note": "bound = calls / Philox rate + 16 x calls / LOP3 rate (measured), or "
+                    "20 wide multiplies per call at 32 lanes/clk/SM plus 36 logic operations "
+                    "per call at 64 lanes/clk/SM (units); frac = bound / launch time"}
 
 
 def philox_peak_derived(sms: int) -> float:

@@ -1057,12 +1057,13 @@ __global__ void __launch_bounds__(kTile) lattice_resident_kernel(const LatJob* _
 // block holds): a cooperative grid keeps the lattice in shared memory, in the
 // packed layout, as bands of rows for a whole run of n steps.  Block b owns rows
 // [b L / G, (b+1) L / G) and also holds the row above and the row below its band
-// (halo rows; the lattice wraps).  After each half step every block publishes the
-// first and the last row it computed to a global exchange area (two sets by
-// half-step parity, so a row is not overwritten while a neighbour may still read
-// it), raises its published-half-step count, and before the next half step waits
-// for the counts of its two neighbours only and copies their rows into its halo
-// rows; one grid barrier at the end of the run decides whether it is committed.
+// (halo rows; the lattice wraps).  A half step of type dl reads the row above each
+// row, one of type ur the row below, so between two half steps one row crosses each
+// band boundary, in one direction: in every half step a block first decides the
+// own row its neighbour will read next and publishes it word by word to a global
+// exchange area (two sets by half-step parity), then decides its other rows, then
+// takes the one halo row it needs next from the neighbour on that side.  One grid
+// barrier at the end of the run decides whether it is committed.
 // The draws, thresholds and decisions are those of lattice_half_kernel (head of
 // four words per thread, eight planes, a per-warp queue for the words still
 // undecided), so the trajectory is the same.
@@ -1078,9 +1079,10 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // Grid barrier of a cooperative launch in two phases, so a block can compute
-// between announcing its rows and needing its neighbours'.  band_arrive: every
-// thread fences its global writes (the published rows), then thread 0 counts the
-// block in; the last block resets the count and advances the generation.
+// between announcing its rows and needing its neighbours'.  band_arrive: after a
+// block barrier thread 0 fences (the fence orders the writes of every thread of
+// the block that the barrier ordered before it) and counts the block in; the last
+// block resets the count and advances the generation.
 // band_wait: thread 0 polls the generation until a deadline of kBandWaitNs on the
 // global timer (and at most kBandPollLimit polls); a wait that runs out, or that
 // sees another block's error, sets the error flag and then settles the run's
@@ -1089,9 +1091,9 @@ __device__ __forceinline__ uint64_t global_ns() {
 // which case this block still writes its band back.  Returns 0 to go on, 1 to
 // return without writing, 2 to write back (only possible at the last barrier).
 __device__ __forceinline__ void band_arrive(BandSync* bs, uint32_t gen) {
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     if (atomicAdd(&bs->count, 1u) == gridDim.x - 1u) {
       atomicExch(&bs->count, 0u);
       __threadfence();
@@ -1122,48 +1124,47 @@ __device__ __forceinline__ uint32_t band_wait(BandSync* bs, uint32_t& gen, uint3
   return *s_flag;
 }
 
-// Neighbour exchange between half steps: flags[b] counts the half steps whose first
-// and last rows block b has published (release after a fence, like band_arrive);
-// before reading its halo rows for half step h a block waits until both neighbours'
-// counts reach h + 1 (acquire).  A block cannot publish half step h + 2 into the
-// exchange set of h before both neighbours published h + 1, i.e. after they read h,
-// so two sets suffice.  The waits end on the same deadline and error flag as the
-// grid barrier; a block giving up aborts the run (commit 0 -> 2).
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+// Neighbour exchange between half steps: every published row word is one 64-bit
+// store of (half-step count << 32 | word), the count being the number of half
+// steps of the launch done (1, 2, ...; the area is zeroed before each launch).
+// A reader polls each halo word until its count is the one it needs: the word and
+// its count are read together (single-copy atomic), so no fence or flag orders the
+// exchange.  Two sets by half-step parity: a block overwrites the set of half step
+// h at h + 2 only after it has read its neighbours' rows of h + 1, which they wrote
+// after reading those of h.  A count other than the expected one is never taken;
+// a wait gives up on the same deadline and error flag as the grid barrier.
+__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 
-__device__ __forceinline__ void band_publish(uint32_t* flags, uint32_t b, uint32_t count) {
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flags + b),
-                                     "r"(count) : "memory");
-}
-
-// Returns 0 to go on, 1 to return without writing (the run is aborted).
-__device__ __forceinline__ uint32_t band_wait_nbrs(BandSync* bs, const uint32_t* flags,
-                                                   uint32_t up, uint32_t dn, uint32_t count,
-                                                   uint32_t* s_flag) {
-  if (threadIdx.x == 0) {
+// The word of half step `count` at p; false when the wait gave up (error flag set,
+// run aborted unless already committed, which cannot happen before the last barrier).
+__device__ __forceinline__ bool band_fetch(const uint64_t* p, uint32_t count, BandSync* bs,
+                                           uint32_t& v) {
+  uint64_t x = ld_relaxed_u64(p);
+  if ((uint32_t)(x >> 32) != count) {
     const uint64_t t0 = global_ns();
-    uint32_t polls = 0, f = 0u;
-    while (ld_acquire_u32(flags + up) < count || ld_acquire_u32(flags + dn) < count) {
-      if (atomicAdd(&bs->err, 0u) != 0u || global_ns() - t0 > kBandWaitNs ||
-          ++polls > kBandPollLimit) {
+    uint32_t polls = 0;
+    do {
+      // the error flag by a plain load every 16 polls: many threads poll at once
+      if (((++polls & 15u) == 0u && *reinterpret_cast<volatile const uint32_t*>(&bs->err) != 0u) ||
+          global_ns() - t0 > kBandWaitNs || polls > kBandPollLimit) {
         atomicExch(&bs->err, 1u);
         atomicCAS(&bs->commit, 0u, 2u);
-        f = 1u;
-        break;
+        return false;
       }
       __nanosleep(32);
-    }
-    __threadfence();
-    *s_flag = f;
+      x = ld_relaxed_u64(p);
+    } while ((uint32_t)(x >> 32) != count);
   }
-  __syncthreads();
-  return *s_flag;
+  v = (uint32_t)x;
+  return true;
 }
 
 // S, V, H of local word l (column c) of a band buffer (packed rows of wpr words;
@@ -1234,10 +1235,10 @@ __device__ __forceinline__ void band_round(const LatTable& tab, const uint32_t* 
 // 31..24 of every word; words with undecided lanes go to the warp's queue, which
 // runs a round whenever it holds 32 of them.
 // Own words are addressed through an index: word idx of a range is own word
-// idx + (idx < split ? off_lo : off_hi), so the first and the last own row can be
-// one range of 2 wpr indices.
+// idx + (idx < s1 ? o0 : idx < s2 ? o1 : o2), so the first own row, the last own
+// row and a run of interior rows can be one range.
 struct BandRange {
-  uint32_t n, split, off_lo, off_hi;
+  uint32_t n, s1, s2, o0, o1, o2;
 };
 
 template <bool COLL, bool MIR, int W>
@@ -1254,7 +1255,7 @@ __device__ __forceinline__ void band_pass(const LatJob& J, const LatTable& tab,
   for (int k = 0; k < W; ++k) {
     const uint32_t idx = i0 + threadIdx.x + (uint32_t)k * kTile;
     act[k] = idx < R.n;
-    const uint32_t oo = act[k] ? idx + (idx < R.split ? R.off_lo : R.off_hi) : 0u;
+    const uint32_t oo = act[k] ? idx + (idx < R.s1 ? R.o0 : idx < R.s2 ? R.o1 : R.o2) : 0u;
     const uint32_t c = pow2 ? (oo & (wpr - 1u)) : oo % wpr;
     a[k] = w_first + oo;  // global lane word: the Philox counter and the frozen mask
     uint32_t S, V, H;
@@ -1293,7 +1294,15 @@ __device__ __forceinline__ void band_range(const LatJob& J, const LatTable& tab,
   for (; i0 + (uint32_t)kLatTile <= R.n; i0 += kLatTile)
     band_pass<COLL, MIR, kWordsPerThread>(J, tab, in, out, i0, R, w_first, wpr, pow2, typ, K, P,
                                           q, qn, calls);
-  for (; i0 < R.n; i0 += kTile)
+  // the rest in one pass of as many words per thread as it needs
+  const uint32_t rest = R.n - i0;
+  if (rest > 3u * kTile)
+    band_pass<COLL, MIR, 4>(J, tab, in, out, i0, R, w_first, wpr, pow2, typ, K, P, q, qn, calls);
+  else if (rest > 2u * kTile)
+    band_pass<COLL, MIR, 3>(J, tab, in, out, i0, R, w_first, wpr, pow2, typ, K, P, q, qn, calls);
+  else if (rest > (uint32_t)kTile)
+    band_pass<COLL, MIR, 2>(J, tab, in, out, i0, R, w_first, wpr, pow2, typ, K, P, q, qn, calls);
+  else if (rest > 0u)
     band_pass<COLL, MIR, 1>(J, tab, in, out, i0, R, w_first, wpr, pow2, typ, K, P, q, qn, calls);
   while (qn != 0u) band_round<COLL>(tab, in, out, q, qn, w_first, wpr, pow2, typ, K, P, calls);
 }
@@ -1313,11 +1322,34 @@ __device__ __forceinline__ void band_decide(const LatJob& J, const LatTable& tab
     band_range<false, false>(J, tab, in, out, R, w_first, wpr, typ, K, P, q, calls);
 }
 
-// xch: exchange area, [2 parities][G blocks][first row, last row][wpr words].
+// The own row `orow` that a neighbour reads in the next half step: one word per
+// thread, decided by three unconditional calls (twelve planes) and the rare later
+// ones, without the warp queue, and published word by word (no block barrier).
+template <bool COLL>
+__device__ __forceinline__ void band_edge(const LatJob& J, const LatTable& tab,
+                                          const uint32_t* in, uint32_t* out, uint32_t orow,
+                                          uint32_t w_first, uint32_t wpr, uint32_t typ,
+                                          const PhKey& K, const PhShared& P, uint64_t* pub,
+                                          uint64_t tag, uint32_t& calls) {
+  for (uint32_t c = threadIdx.x; c < wpr; c += blockDim.x) {
+    const uint32_t oo = orow * wpr + c, a = w_first + oo;
+    uint32_t S, V, H;
+    band_words(in, wpr + oo, c, wpr, typ, S, V, H);
+    const uint32_t F = J.frozen != nullptr ? J.frozen[a] : 0u;
+    LaneWord L = classify<COLL>(S, V, H, F, tab);
+    decide_head3<COLL>(L, tab, K, P, a, typ, calls);
+    if (L.U != 0u) decide_tail<COLL>(L, tab, K, P, a, typ, 3u, calls);
+    out[wpr + oo] = L.res;
+    st_relaxed_u64(pub + c, tag | L.res);
+  }
+}
+
+// xch: exchange area, [2 parities][G blocks][wpr words] of (count << 32 | word),
+// zeroed before the launch.
 template <int ENC>
 __global__ void __launch_bounds__(kTile, kBandMinBlocks) lattice_band_kernel(
-    const LatJob* __restrict__ jobs, uint32_t* __restrict__ xch, uint32_t* __restrict__ flags,
-    BandSync* __restrict__ bs, uint32_t t0, uint32_t n_steps) {
+    const LatJob* __restrict__ jobs, uint64_t* __restrict__ xch, BandSync* __restrict__ bs,
+    uint32_t t0, uint32_t n_steps) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ LatTable stab;
   __shared__ LatJob sJ;  // the job descriptor, read from shared memory
@@ -1359,30 +1391,34 @@ __global__ void __launch_bounds__(kTile, kBandMinBlocks) lattice_band_kernel(
       const uint32_t typ = pos ^ order;  // update type of this position
       const uint32_t* in = buf[pos];
       uint32_t* out = buf[pos ^ 1u];
-      // the first and last own rows (what the neighbours need) first, then publish
-      // them and announce; the interior rows overlap the other blocks' arrival
-      const BandRange Rb = nr == 1u ? BandRange{wpr, wpr, 0u, 0u}
-                                    : BandRange{2u * wpr, wpr, 0u, (nr - 2u) * wpr};
-      const BandRange Ri = {nr >= 3u ? (nr - 2u) * wpr : 0u, 0xffffffffu, wpr, 0u};
-      band_decide(J, stab, in, out, Rb, w_first, wpr, typ, K, P, q, calls);
-      __syncthreads();
-      uint32_t* mine = xch + ((size_t)pos * G + b) * 2u * wpr;
-      for (uint32_t c = threadIdx.x; c < wpr; c += blockDim.x) {
-        __stcg(mine + c, out[wpr + c]);
-        __stcg(mine + wpr + c, out[nr * wpr + c]);
+      // In the next half step (type typ ^ 1) a band reads one neighbouring row: the
+      // one above it (type 0, dl) or below it (type 1, ur).  So this block publishes
+      // one own row -- its last row for the block below, or its first row for the
+      // block above -- first, then decides its other rows, then fetches the one halo
+      // row it needs next, published by the neighbour on that side.
+      const uint32_t nxt = typ ^ 1u;
+      const uint32_t prow = nxt == 0u ? nr - 1u : 0u;
+      const uint32_t count = 2u * st + pos + 1u;  // half steps of this launch done
+      const uint64_t tag = (uint64_t)count << 32;
+      if (stab.collapsed)
+        band_edge<true>(J, stab, in, out, prow, w_first, wpr, typ, K, P,
+                        xch + ((size_t)pos * G + b) * wpr, tag, calls);
+      else
+        band_edge<false>(J, stab, in, out, prow, w_first, wpr, typ, K, P,
+                         xch + ((size_t)pos * G + b) * wpr, tag, calls);
+      const BandRange R = {n_own - wpr, 0xffffffffu, 0xffffffffu, prow == 0u ? wpr : 0u, 0u,
+                           0u};
+      band_decide(J, stab, in, out, R, w_first, wpr, typ, K, P, q, calls);
+      const uint32_t nbr = nxt == 0u ? (b + G - 1u) % G : (b + 1u) % G;
+      const uint64_t* src = xch + ((size_t)pos * G + nbr) * wpr;
+      uint32_t* halo = out + (nxt == 0u ? 0u : (nr + 1u) * wpr);
+      bool ok = true;
+      for (uint32_t c = threadIdx.x; c < wpr && ok; c += blockDim.x) {
+        uint32_t v = 0u;
+        ok = band_fetch(src + c, count, bs, v);
+        halo[c] = v;
       }
-      const uint32_t count = 2u * st + pos + 1u;  // half steps published so far
-      band_publish(flags, b, count);
-      band_decide(J, stab, in, out, Ri, w_first, wpr, typ, K, P, q, calls);
-      if (band_wait_nbrs(bs, flags, (b + G - 1u) % G, (b + 1u) % G, count, &s_flag) != 0u)
-        return;
-      const uint32_t* above = xch + ((size_t)pos * G + (b + G - 1u) % G) * 2u * wpr + wpr;
-      const uint32_t* below = xch + ((size_t)pos * G + (b + 1u) % G) * 2u * wpr;
-      for (uint32_t c = threadIdx.x; c < wpr; c += blockDim.x) {
-        out[c] = __ldcg(above + c);
-        out[(nr + 1u) * wpr + c] = __ldcg(below + c);
-      }
-      __syncthreads();
+      if (__syncthreads_or(!ok)) return;  // the run is aborted: nothing is written
     }
   }
   // one grid barrier for the whole chunk: every block has finished its last half step
@@ -1551,11 +1587,10 @@ bool lattice_band_shape(int enc, uint32_t L, uint32_t wpr, int* grid, size_t* sm
 // n steps of the one job in `jobs` by the banded kernel (cooperative launch; the
 // grid and shared memory from lattice_band_shape; bs zeroed by the caller).
 cudaError_t launch_lattice_band(int enc, const LatJob* jobs, int grid, size_t smem,
-                                uint32_t* xch, uint32_t* flags, BandSync* bs, uint32_t t0,
-                                uint32_t n_steps, cudaStream_t st) {
+                                uint64_t* xch, BandSync* bs, uint32_t t0, uint32_t n_steps,
+                                cudaStream_t st) {
   if (n_steps == 0) return cudaSuccess;
-  void* args[] = {(void*)&jobs, (void*)&xch, (void*)&flags, (void*)&bs, (void*)&t0,
-                  (void*)&n_steps};
+  void* args[] = {(void*)&jobs, (void*)&xch, (void*)&bs, (void*)&t0, (void*)&n_steps};
   const void* k = enc == kEncInt8 ? (const void*)lattice_band_kernel<kEncInt8>
                                   : (const void*)lattice_band_kernel<kEncPacked>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

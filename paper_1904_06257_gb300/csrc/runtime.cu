@@ -50,8 +50,8 @@ cudaError_t launch_epilogue(CtxDev* const*, int, cudaStream_t);
 cudaError_t launch_member_copy(int, const shk::MemberDev*, int, void*, unsigned long long,
                                cudaStream_t);
 bool lattice_band_shape(int, uint32_t, uint32_t, int*, size_t*);
-cudaError_t launch_lattice_band(int, const LatJob*, int, size_t, uint32_t*, uint32_t*, BandSync*,
-                                uint32_t, uint32_t, cudaStream_t);
+cudaError_t launch_lattice_band(int, const LatJob*, int, size_t, uint64_t*, BandSync*, uint32_t,
+                                uint32_t, cudaStream_t);
 cudaError_t launch_lattice_resident(int, const LatJob*, int, uint32_t, uint32_t, uint32_t,
                                     cudaStream_t);
 cudaError_t launch_philox(uint64_t, const uint32_t*, uint32_t*, int64_t, cudaStream_t);
@@ -1075,11 +1075,9 @@ static shaken_status run_band(shaken_ctx* c, uint64_t n_steps, int grid, size_t 
   if (c->solo.dirty) TRY(build_plan(c->solo, st));
   const Family& F = *c->solo.fams[0];
   const uint32_t wpr = (uint32_t)(c->L / 32);
-  // exchange rows [2 parities][grid][2][wpr], then one published-half-step count per block
-  const size_t xwords = (size_t)2 * grid * 2 * wpr;
-  const size_t xbytes = (xwords + (size_t)grid) * sizeof(uint32_t);
+  // exchange rows [2 parities][grid][wpr] of (half-step count << 32 | word)
+  const size_t xbytes = (size_t)2 * grid * wpr * sizeof(uint64_t);
   if (c->band_xch.p == nullptr || c->band_xch.bytes < xbytes) TRY(c->band_xch.alloc(xbytes));
-  uint32_t* flags = c->band_xch.as<uint32_t>() + xwords;
   if (c->band_sync.p == nullptr) TRY(c->band_sync.alloc(sizeof(shk::BandSync)));
   uint64_t done = 0;
   while (done < n_steps) {
@@ -1090,11 +1088,10 @@ static shaken_status run_band(shaken_ctx* c, uint64_t n_steps, int grid, size_t 
     c->band_stall = false;
     c->band_hurry = -1;
     CU(cudaMemcpyAsync(c->band_sync.p, &h0, sizeof(h0), cudaMemcpyHostToDevice, st));
-    CU(cudaMemsetAsync(flags, 0, (size_t)grid * sizeof(uint32_t), st));
+    CU(cudaMemsetAsync(c->band_xch.p, 0, xbytes, st));  // no count is valid yet
     CU(shk::launch_lattice_band(F.enc, F.jobs.as<LatJob>(), grid, smem,
-                                c->band_xch.as<uint32_t>(), flags,
-                                c->band_sync.as<shk::BandSync>(), (uint32_t)c->host_step,
-                                (uint32_t)chunk, st));
+                                c->band_xch.as<uint64_t>(), c->band_sync.as<shk::BandSync>(),
+                                (uint32_t)c->host_step, (uint32_t)chunk, st));
     c->launches++;
     shk::BandSync h{};
     CU(cudaMemcpyAsync(&h, c->band_sync.p, sizeof(h), cudaMemcpyDeviceToHost, st));
