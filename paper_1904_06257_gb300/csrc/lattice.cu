@@ -1325,13 +1325,15 @@ __device__ __forceinline__ void band_decide(const LatJob& J, const LatTable& tab
 // The own row `orow` that a neighbour reads in the next half step: one word per
 // thread, decided by three unconditional calls (twelve planes) and the rare later
 // ones, without the warp queue, and published word by word (no block barrier).
+// Word c goes to thread blockDim - 1 - c: the passes over the other rows give
+// their extra words to the first threads.
 template <bool COLL>
 __device__ __forceinline__ void band_edge(const LatJob& J, const LatTable& tab,
                                           const uint32_t* in, uint32_t* out, uint32_t orow,
                                           uint32_t w_first, uint32_t wpr, uint32_t typ,
                                           const PhKey& K, const PhShared& P, uint64_t* pub,
                                           uint64_t tag, uint32_t& calls) {
-  for (uint32_t c = threadIdx.x; c < wpr; c += blockDim.x) {
+  for (uint32_t c = blockDim.x - 1u - threadIdx.x; c < wpr; c += blockDim.x) {
     const uint32_t oo = orow * wpr + c, a = w_first + oo;
     uint32_t S, V, H;
     band_words(in, wpr + oo, c, wpr, typ, S, V, H);
