@@ -139,21 +139,37 @@ def oracle_pool(n_groups):
     return pool, workers
 
 
-def oracle_sample(pool, workers, Ls, betas, seeds, steps_per_group=1, max_groups=None):
-    """Run the CPU oracle, as it stands, on the smallest groups of the workload
-    (L = 32 and 64), one task per group on the pool, and return
-    (updates/s over the wall time, cores used, description, updates, wall)."""
-    idx = [g for g in range(len(Ls)) if Ls[g] <= 64]
-    if max_groups:
-        idx = idx[:max_groups]
-    workers = min(workers, len(idx))
-    jobs = [(int(Ls[g]), betas[32 * g:32 * g + 32], seeds[g], steps_per_group) for g in idx]
+def oracle_sample_plan(Ls, per_size):
+    """(L, group, full steps) of the oracle sample: the first `per_size` groups of each
+    lattice size, each for round(L_max^2 / L^2) steps (about equal updates per group)."""
+    sizes = sorted(set(int(x) for x in Ls))
+    top = max(sizes) ** 2
+    plan = []
+    for L in sizes:
+        steps = max(1, round(top / (L * L)))
+        plan += [(L, g, steps) for g in range(len(Ls)) if int(Ls[g]) == L][:per_size]
+    return plan
+
+
+def oracle_sample(pool, workers, Ls, betas, seeds, per_size=3):
+    """Run the CPU oracle, as it stands, on the first `per_size` groups of every
+    lattice size of the workload (32 replicas each), one task per group on the pool,
+    each group for as many full steps as the largest size's one step is worth in
+    updates (so the tasks take about the same time), and return (updates/s over the
+    wall time, cores used, description, updates, wall)."""
+    sizes = sorted(set(int(x) for x in Ls))
+    top = max(sizes) ** 2
+    jobs = [(L, betas[32 * g:32 * g + 32], seeds[g], steps)
+            for L, g, steps in oracle_sample_plan(Ls, per_size)]
+    workers = min(workers, len(jobs))
     t0 = time.perf_counter()
-    res = pool.map(_oracle_group, jobs)
+    res = pool.map(_oracle_group, jobs, chunksize=1)
     wall = time.perf_counter() - t0
     upd = sum(r[0] for r in res)
-    desc = (f"{len(jobs)} groups of the workload with L in {{32, 64}} (32 replicas each), "
-            f"{steps_per_group} full step(s) each, one spawned process per group")
+    per = ", ".join(f"L={L}: {max(1, round(top / (L * L)))}" for L in sizes)
+    desc = (f"{len(jobs)} groups of the workload, {per_size} at each L (32 replicas each), "
+            f"full steps per group {per} (about equal work per group), one spawned process "
+            f"per group")
     return upd / wall, workers, desc, upd, wall
 
 
@@ -428,8 +444,7 @@ def run_ours(args, rank, world, local_rank):
         cpu = None
         if world == 1:
             pool, workers = oracle_pool(GROUPS)
-            v, cores, desc, upd, wall = oracle_sample(pool, workers, Ls, betas, seeds,
-                                                      steps_per_group=8)
+            v, cores, desc, upd, wall = oracle_sample(pool, workers, Ls, betas, seeds, 3)
             pool.close()
             pool.join()
             cpu = {"value": v, "unit": "updates/s", "cores": cores, "kind": "oracle",
@@ -971,8 +986,7 @@ def run_reference(args, rank, world):
     tot_upd, tot_wall, cores, desc = 0.0, 0.0, 1, ""
     pool, workers = oracle_pool(16)
     for k in range(args.warmup + args.steps):
-        v, cores, desc, upd, wall = oracle_sample(pool, workers, Ls, betas, seeds, 1,
-                                                  max_groups=16)
+        v, cores, desc, upd, wall = oracle_sample(pool, workers, Ls, betas, seeds, 1)
         if k >= args.warmup:
             tot_upd += upd
             tot_wall += wall

@@ -24,3 +24,18 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "updates/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_oracle_sample_covers_every_size_with_equal_work():
+    sys.path.insert(0, ROOT)
+    import bench
+    Ls, _, _ = bench.workload(0)
+    plan = bench.oracle_sample_plan(Ls, 3)
+    sizes = sorted(set(int(x) for x in Ls))
+    assert sorted(set(L for L, _, _ in plan)) == sizes
+    for L in sizes:
+        groups = [g for LL, g, _ in plan if LL == L]
+        assert len(groups) == min(3, sum(1 for x in Ls if int(x) == L))
+        assert all(int(Ls[g]) == L for g in groups) and len(set(groups)) == len(groups)
+    work = [L * L * steps for L, _, steps in plan]
+    assert max(work) == min(work) == max(sizes) ** 2
