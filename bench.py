@@ -823,6 +823,29 @@ def run_graphs(S, stream, torch, args):
     dt = _timed(torch, stream, lambda: S.shaken_step(c, k))
     S.shaken_free(c)
     out["reg3_pm1_step"] = {"updates_per_s": 2.0 * n * R * k / dt, "steps": k}
+    # +-1 on a hub-heavy power-law graph (Chung-Lu, exponent 2.1, mean degree 8): the
+    # vertices of degree above 255 take the warp-per-word path
+    up, vp = W.power_law(n, 8.0, 2.1, W.BASE_SEED + 15)
+    Jp = W.couplings_pm1(up.size, W.BASE_SEED + 16)
+    deg = np.bincount(np.concatenate([up, vp]), minlength=n)
+    indeg = np.bincount(vp, minlength=n)  # min -> max orientation: the larger id is the head
+    outdeg = np.bincount(up, minlength=n)
+    p = S.Problem(S.GRAPH, S.MULTISPIN, R, 1.0, 1.0, n=n, u=up, v=vp, J_edge=Jp,
+                  J_is_integer=True, lambda_=lam)
+    c = S.shaken_init(p, W.BASE_SEED + 15, stream)
+    S.shaken_step(c, 2)
+    S.shaken_sync(c)
+    kp = 20
+    dt = _timed(torch, stream, lambda: S.shaken_step(c, kp))
+    S.shaken_free(c)
+    out["powerlaw_pm1_step"] = {
+        "n": n, "m": int(up.size), "exponent": 2.1, "replicas": R, "steps": kp,
+        "updates_per_s": 2.0 * n * R * kp / dt,
+        "max_degree": int(deg.max()), "max_in_degree": int(indeg.max()),
+        "max_out_degree": int(outdeg.max()),
+        "hubs_in": int((indeg > 255).sum()), "hubs_out": int((outdeg > 255).sum()),
+        "note": "vertices of degree above 255 in a half step's direction: one warp per "
+                "32-replica word"}
     # the optimisation use of Sec. 6 on a synthetic 2D Edwards-Anderson +-1 instance:
     # L x L torus, couplings +-1 i.i.d., lambda = 0, q = 2.5 (> 2: the regime where the
     # minimisers of the pair Hamiltonian carry over, Sec. 6), 256 replicas, linear anneal

@@ -36,7 +36,7 @@
 namespace shk {
 
 constexpr int kTableDeg = 31;  // per-vertex class tables for degree <= 31
-constexpr int kHubDeg = 255;   // byte counters for degree <= 255; above: one warp per word
+// byte counters for degree <= kHubDeg (shaken_internal.cuh); above: graph_hub_kernel
 
 // 2^x (PTX ex2.approx: relative error below 2^-22 over the range used here).
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -292,96 +292,133 @@ __device__ __forceinline__ V warp_transpose_sum(V (&v)[32], int lane) {
   return v[0];
 }
 
-struct HubArgs {
-  uint32_t x, g, t, typ;
-  bool fuse, uni;
-  double beta_u;
-};
-
-// One word (x, g) of a vertex of degree above kHubDeg, done by the whole warp: lane l
-// takes the edges p0 + l, p0 + l + 32, ...; the per-replica counts (integer) or fields
-// (real) are combined across the warp so that lane k holds replica k's, and lane k
-// decides replica k (integer: T in fp64 and the plane-assembled draw; real: the fp32
-// test of the direct draw).  Returns the word (every lane).
+// Sum over the chunk's edges [e0, e1) of word (., g), lane l taking edges e0 + l,
+// e0 + l + 32, ...; returns lane k's value for replica k: the number of neighbours
+// with J_xy s_y = +1 (integer couplings; byte counters, at most kHubChunk / 32 = 64
+// edges per lane) or the float sum of J_xy s_y (real couplings, as its bits).
 template <bool INTEGER>
-__device__ __noinline__ uint32_t hub_word(const GraphJob& J, HubArgs A, uint32_t half,
-                                          int lane) {
+__device__ __forceinline__ uint32_t hub_chunk_sum(const uint32_t* src, const uint32_t* col,
+                                                  const float* Jr, uint32_t e0, uint32_t e1,
+                                                  uint32_t G, uint32_t g, int lane) {
+  if (INTEGER) {
+    uint32_t C[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) C[m] = 0u;
+    for (uint32_t e = e0 + (uint32_t)lane; e < e1; e += 32u) {
+      const uint32_t cv = __ldg(col + e);
+      const uint32_t w = __ldg(src + (size_t)(cv & 0x7fffffffu) * G + g) ^ (0u - (cv >> 31));
+#pragma unroll
+      for (int m = 0; m < 8; ++m) C[m] += (w >> m) & 0x01010101u;
+    }
+    uint32_t v[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = (C[k & 7] >> (8 * (k >> 3))) & 0xFFu;
+    return warp_transpose_sum(v, lane);
+  }
+  float v[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = 0.0f;
+  for (uint32_t e = e0 + (uint32_t)lane; e < e1; e += 32u) {
+    const uint32_t y = __ldg(col + e) & 0x7fffffffu;
+    const float Jv = __ldg(Jr + e);
+    const uint32_t wy = __ldg(src + (size_t)y * G + g);
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] += ((wy >> k) & 1u) ? Jv : -Jv;
+  }
+  return __float_as_uint(warp_transpose_sum(v, lane));
+}
+
+// Words of the vertices of degree above kHubDeg in the half step's direction, one
+// warp per (chunk of kHubChunk edges, group): the warp sums its chunk into a partial
+// row, and the warp that finishes a word's last chunk adds the rows in chunk order
+// (the same sum whichever warp comes last), resets the word's counter and decides
+// the 32 replicas, lane k replica k (integer: T in fp64 and the plane-assembled
+// draw; real: the fp32 test of the direct draw).  Runs after the half-step kernel,
+// which leaves these words alone.
+template <bool INTEGER>
+__global__ void __launch_bounds__(kTile) graph_hub_kernel(const GraphJob* __restrict__ jobs,
+                                                          const HubItem* __restrict__ items,
+                                                          const uint32_t* __restrict__ unit_item,
+                                                          int n_units, uint32_t half,
+                                                          uint32_t* __restrict__ partial,
+                                                          uint32_t* __restrict__ done) {
+  const int lane = threadIdx.x & 31;
+  const int u = blockIdx.x * (kTile / 32) + (threadIdx.x >> 5);
+  if (u >= n_units) return;  // the whole warp
+  const HubItem it = items[unit_item[u]];
+  const GraphJob& J = jobs[it.job];
+  const CtxDev* cd = J.cd;
+  const uint32_t t = cd->step;
+  if (t >= cd->t_end) return;
+  const uint32_t typ = half ^ cd->order;
+  if (it.dir != typ) return;  // the other direction's vertices
+  const uint32_t go = (uint32_t)u - it.ubase, g = J.g0 + go, G = J.G;
   const uint32_t* src = half == 0u ? J.A : J.B;
-  const int32_t* ptr = A.typ == 0u ? J.in_ptr : J.out_ptr;
-  const uint32_t* col = A.typ == 0u ? J.in_col : J.out_col;
-  const float* Jr = A.typ == 0u ? J.in_J : J.out_J;
-  const int32_t p0 = ptr[A.x], p1 = ptr[A.x + 1];
-  const int d = p1 - p0;
-  const uint32_t G = J.G;
-  const uint32_t S = src[(size_t)A.x * G + A.g];
-  const uint32_t F = J.frozen != nullptr ? J.frozen[A.x] : 0u;
-  const float lam = J.lambda != nullptr ? J.lambda[A.x] : J.lambda_c;
-  const double beta = A.uni ? A.beta_u : J.beta_lane[32u * A.g + (uint32_t)lane];
+  uint32_t* dst = half == 0u ? J.B : J.A;
+  const uint32_t* col = typ == 0u ? J.in_col : J.out_col;
+  const float* Jr = typ == 0u ? J.in_J : J.out_J;
+  const uint32_t v = hub_chunk_sum<INTEGER>(src, col, Jr, it.e0, it.e1, G, g, lane);
+  uint32_t* rows = partial + (size_t)(it.pbase + go * it.nchunks) * 32u;
+  rows[it.chunk * 32u + (uint32_t)lane] = v;
+  __threadfence();
+  __syncwarp();
+  uint32_t last = 0u;
+  if (lane == 0) last = atomicAdd(done + it.dbase + go, 1u) == it.nchunks - 1u ? 1u : 0u;
+  if (__shfl_sync(0xffffffffu, last, 0) == 0u) return;
+  __threadfence();
+  if (lane == 0) done[it.dbase + go] = 0u;  // ready for the next half step
+  const uint32_t x = it.x;
+  const int32_t* ptr = typ == 0u ? J.in_ptr : J.out_ptr;
+  const int d = ptr[x + 1] - ptr[x];
+  const uint32_t S = src[(size_t)x * G + g];
+  const uint32_t F = J.frozen != nullptr ? J.frozen[x] : 0u;
+  const float lam = J.lambda != nullptr ? J.lambda[x] : J.lambda_c;
+  double beta;
+  if (J.beta_sched != nullptr && cd->anneal_len != 0u) {
+    uint32_t k = t - cd->anneal_t0;
+    if (k >= cd->anneal_len) k = cd->anneal_len - 1u;
+    beta = J.beta_sched[k];
+  } else {
+    beta = J.beta_lane[32u * g + (uint32_t)lane];
+  }
+  const bool fuse = half == 0u && cd->tracking && !cd->record && J.sums != nullptr;
   const int sig = (int)((S >> lane) & 1u);
   const PhKey K = ph_key(J.key0, J.key1);
   bool tau;
   float contrib;
   if (INTEGER) {
-    uint32_t v[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) v[k] = 0u;
-    // 16-bit counters (lanes m and m + 16), widened every 65535 edges of this lane
-    for (int e0 = p0; e0 < p1; e0 += 32 * 65535) {
-      const int e1 = min(p1, e0 + 32 * 65535);
-      uint32_t c16[16];
-#pragma unroll
-      for (int m = 0; m < 16; ++m) c16[m] = 0u;
-      for (int e = e0 + lane; e < e1; e += 32) {
-        const uint32_t cv = __ldg(col + e);
-        const uint32_t w = __ldg(src + (size_t)(cv & 0x7fffffffu) * G + A.g) ^ (0u - (cv >> 31));
-#pragma unroll
-        for (int m = 0; m < 16; ++m) c16[m] += (w >> m) & 0x00010001u;
-      }
-#pragma unroll
-      for (int m = 0; m < 16; ++m) {
-        v[m] += c16[m] & 0xFFFFu;
-        v[m + 16] += c16[m] >> 16;
-      }
-    }
-    const int a = (int)warp_transpose_sum(v, lane);
+    int a = 0;
+    for (uint32_t c = 0; c < it.nchunks; ++c) a += (int)__ldcg(rows + c * 32u + (uint32_t)lane);
     // planes: lane c < 8 makes call c, then lane k gathers bit k of each plane
-    const uint4 w = ph_call(K, A.x, A.g, A.t, A.typ + 2u * (uint32_t)(lane & 7));
-    uint32_t u = 0u;
+    const uint4 w = ph_call(K, x, g, t, typ + 2u * (uint32_t)(lane & 7));
+    uint32_t uu = 0u;
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       const uint32_t c = (j & 3) == 0 ? w.x : (j & 3) == 1 ? w.y : (j & 3) == 2 ? w.z : w.w;
-      u |= ((__shfl_sync(0xffffffffu, c, j >> 2) >> lane) & 1u) << (31 - j);
+      uu |= ((__shfl_sync(0xffffffffu, c, j >> 2) >> lane) & 1u) << (31 - j);
     }
     const double h = field_h(1.0, 2 * a - d, J.q, sig ? 1 : -1, (double)lam);
-    tau = (unsigned long long)u < threshold_T(h, beta);
+    tau = (unsigned long long)uu < threshold_T(h, beta);
     contrib = (float)(2 * a - d) + 2.0f * lam;
   } else {
-    float v[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) v[k] = 0.0f;
-    for (int e = p0 + lane; e < p1; e += 32) {
-      const uint32_t y = __ldg(col + e) & 0x7fffffffu;
-      const float Jv = __ldg(Jr + e);
-      const uint32_t wy = __ldg(src + (size_t)y * G + A.g);
-#pragma unroll
-      for (int k = 0; k < 32; ++k) v[k] += ((wy >> k) & 1u) ? Jv : -Jv;
-    }
-    const float hs = warp_transpose_sum(v, lane);
-    const uint4 w = ph_call(K, A.x, A.g, A.t, A.typ + 2u * (uint32_t)(lane >> 2));
-    const uint32_t u = (lane & 3) == 0 ? w.x : (lane & 3) == 1 ? w.y : (lane & 3) == 2 ? w.z : w.w;
+    float hs = 0.0f;
+    for (uint32_t c = 0; c < it.nchunks; ++c)
+      hs += __uint_as_float(__ldcg(rows + c * 32u + (uint32_t)lane));
+    const uint4 w = ph_call(K, x, g, t, typ + 2u * (uint32_t)(lane >> 2));
+    const uint32_t uu = (lane & 3) == 0 ? w.x : (lane & 3) == 1 ? w.y : (lane & 3) == 2 ? w.z : w.w;
     const float qf = (float)J.q;
     const float hk = __fadd_rn(__fadd_rn(hs, sig ? qf : -qf), lam);
     const float onep = 1.0f + ex2_approx((float)(-2.0 * beta * 1.4426950408889634) * hk);
-    tau = __uint2float_rn(u) * 2.3283064365386963e-10f * onep < 1.0f;
+    tau = __uint2float_rn(uu) * 2.3283064365386963e-10f * onep < 1.0f;
     contrib = hs + 2.0f * lam;
   }
   const uint32_t res = __ballot_sync(0xffffffffu, tau) | F;
-  if (A.fuse) {  // -H(sigma_t) share of replica (g, lane): sigma (field sum + 2 lambda)
+  if (fuse) {  // -H(sigma_t) share of replica (g, lane): sigma (field sum + 2 lambda)
     const float c = sig ? contrib : -contrib;
     if (c != 0.0f)
-      atomicAdd(J.sums + (size_t)(32u * A.g + (uint32_t)lane) * kNumSums + kSumE, (double)c);
+      atomicAdd(J.sums + (size_t)(32u * g + (uint32_t)lane) * kNumSums + kSumE, (double)c);
   }
-  return res;
+  if (lane == 0) dst[(size_t)x * G + g] = res;
 }
 
 // A lane left undecided by the head of its word, waiting in its warp's queue.
@@ -603,7 +640,7 @@ __global__ void __launch_bounds__(kTile, 3) graph_half_kernel(const GraphJob* __
       }
     }
     uint32_t res = 0u;
-    const bool hub = valid && d > kHubDeg;
+    const bool hub = valid && (uint32_t)d > kHubDeg;  // left to graph_hub_kernel
     // table entries the warp's lanes need: a < 8, < 16 or < 32 (warp-wide choice)
     // (collapsed: a' = a + sigma <= d + 1)
     const int dn = collapse ? d + 1 : d;
@@ -755,22 +792,6 @@ __global__ void __launch_bounds__(kTile, 3) graph_half_kernel(const GraphJob* __
           __syncwarp();
         }
       }
-    }
-    // vertices of degree above kHubDeg: one warp per word
-    unsigned hubs = __ballot_sync(0xffffffffu, hub);
-    while (hubs != 0u) {
-      const int srcl = __ffs(hubs) - 1;
-      hubs &= hubs - 1u;
-      HubArgs A;
-      A.x = __shfl_sync(0xffffffffu, x, srcl);
-      A.g = __shfl_sync(0xffffffffu, g, srcl);
-      A.t = t;
-      A.typ = typ;
-      A.fuse = fuse;
-      A.uni = uni;
-      A.beta_u = sh.ra.beta_u;
-      const uint32_t wres = hub_word<INTEGER>(J, A, half, lane);
-      if (lane == 0) dst[(size_t)A.x * J.G + A.g] = wres;
     }
   }
   if (cur_job >= 0) {
@@ -960,6 +981,21 @@ cudaError_t launch_graph_half(bool integer, const GraphJob* jobs, const Tile* ti
     graph_half_kernel<true><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, half, exact_always);
   else
     graph_half_kernel<false><<<grid, kTile, 0, st>>>(jobs, tiles, n_tiles, half, exact_always);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_graph_hub(bool integer, const GraphJob* jobs, const HubItem* items,
+                             const uint32_t* unit_item, int n_units, uint32_t half,
+                             uint32_t* partial, uint32_t* done, cudaStream_t st) {
+  if (n_units <= 0) return cudaSuccess;
+  constexpr int per = kTile / 32;
+  const int grid = (n_units + per - 1) / per;
+  if (integer)
+    graph_hub_kernel<true><<<grid, kTile, 0, st>>>(jobs, items, unit_item, n_units, half, partial,
+                                                   done);
+  else
+    graph_hub_kernel<false><<<grid, kTile, 0, st>>>(jobs, items, unit_item, n_units, half,
+                                                    partial, done);
   return cudaGetLastError();
 }
 

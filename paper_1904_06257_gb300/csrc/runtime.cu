@@ -42,6 +42,8 @@ cudaError_t launch_lattice_init(int, int, const LatJob*, const Tile*, int, int, 
 cudaError_t launch_lattice_obs(int, int, const LatJob*, const Tile*, int, int, int, cudaStream_t);
 cudaError_t launch_graph_half(bool, const GraphJob*, const Tile*, int, uint32_t, int, int,
                               cudaStream_t);
+cudaError_t launch_graph_hub(bool, const GraphJob*, const HubItem*, const uint32_t*, int, uint32_t,
+                             uint32_t*, uint32_t*, cudaStream_t);
 cudaError_t launch_graph_init(const GraphJob*, const Tile*, int, int, cudaStream_t);
 cudaError_t launch_graph_obs(const GraphJob*, const Tile*, int, int, int, cudaStream_t);
 cudaError_t launch_graph_fields(const GraphJob*, const Tile*, int, uint32_t, float*,
@@ -60,6 +62,7 @@ cudaError_t launch_threshold(const double*, const double*, uint64_t*, int64_t, c
 
 using shk::CtxDev;
 using shk::GraphJob;
+using shk::HubItem;
 using shk::LatJob;
 using shk::LatTable;
 using shk::Tile;
@@ -140,6 +143,10 @@ struct Family {
   int n_tiles = 0;
   DevMem ojobs, otiles;  // graph: one job per group and vertex tiles (init, observables)
   int n_otiles = 0;
+  // graph: chunks of the edge lists of vertices of degree above kHubDeg, one warp per
+  // (chunk, group) unit; partial rows and finished-chunk counters of their words
+  DevMem hub_items, hub_units, hub_partial, hub_done;
+  int n_hub_units = 0;
 };
 
 struct Plan {
@@ -236,6 +243,8 @@ struct shaken_ctx {
   DevMem series_m, series_H;
   DevMem in_ptr, in_col, in_J, out_ptr, out_col, out_J, lam_dev;
   DevMem in_perm, out_perm;  // vertices by increasing in- / out-degree (half-step order)
+  std::vector<uint32_t> hubs[2];  // graph: (x, first edge, end edge) of the vertices of degree
+                                  // above kHubDeg, in-CSR [0] and out-CSR [1]
   DevMem band_xch, band_sync;  // banded runs: row exchange area and grid barrier
   bool band_stall = false;     // diagnostics: the next banded run's barrier never completes
   int band_hurry = -1;         // diagnostics: block that gives up the next run's last wait at once
@@ -262,6 +271,30 @@ static cudaStream_t ctx_stream(const shaken_ctx* c) {
 
 static void add_tiles(std::vector<Tile>& tiles, uint32_t job, uint64_t count, uint32_t size) {
   for (uint64_t w = 0; w < count; w += size) tiles.push_back(Tile{job, (uint32_t)w});
+}
+
+// Graph half-step tiles of one job, vertices in degree order: the tiles are listed in
+// the order k -> (k * s) mod N with s coprime to N near N (sqrt 5 - 1) / 2, so the
+// heavy tiles (the highest degrees, at the end of the order) spread evenly over the
+// contiguous tile ranges the blocks take instead of all falling to the last blocks.
+static void add_graph_tiles(std::vector<Tile>& tiles, uint32_t job, uint64_t count,
+                            uint32_t size) {
+  const uint64_t N = (count + size - 1) / size;
+  if (N == 0) return;
+  uint64_t st = (uint64_t)((double)N * 0.6180339887498949);
+  if (st == 0) st = 1;
+  auto gcd = [](uint64_t a, uint64_t b) {
+    while (b != 0) {
+      const uint64_t t = a % b;
+      a = b;
+      b = t;
+    }
+    return a;
+  };
+  while (gcd(st, N) != 1) ++st;
+  uint64_t pos = 0;
+  for (uint64_t k = 0; k < N; ++k, pos = (pos + st) % N)
+    tiles.push_back(Tile{job, (uint32_t)(pos * size)});
 }
 
 static void lattice_tiles(const std::vector<LatJob>& jobs, uint32_t size,
@@ -407,6 +440,9 @@ static shaken_status build_plan(Plan& P, cudaStream_t st) {
   std::vector<std::vector<GraphJob>> ojobs(2);  // per-group jobs
   std::vector<std::vector<Tile>> otiles(2);
   std::vector<std::vector<Tile>> tiles(5);
+  std::vector<std::vector<HubItem>> hitems(2);    // per graph family: hub chunks
+  std::vector<std::vector<uint32_t>> hunits(2);   // unit -> item
+  std::vector<uint32_t> hrows(2, 0u), hdone(2, 0u);
   std::vector<CtxDev*> cds;
   for (shaken_ctx* c : P.members) {
     CtxDev* cdp = c->cd.as<CtxDev>();
@@ -479,8 +515,33 @@ static shaken_status build_plan(Plan& P, cudaStream_t st) {
         H.Gj = std::min<uint32_t>((uint32_t)kTile, ng - g0);
         H.Gp = 1;
         while (H.Gp < H.Gj) H.Gp <<= 1;
-        add_tiles(tiles[3 + fi], (uint32_t)gjobs[fi].size(), (uint64_t)c->n,
-                  (uint32_t)kTile / H.Gp);
+        add_graph_tiles(tiles[3 + fi], (uint32_t)gjobs[fi].size(), (uint64_t)c->n,
+                        (uint32_t)kTile / H.Gp);
+        for (uint32_t dir = 0; dir < 2; ++dir) {
+          const std::vector<uint32_t>& hv = c->hubs[dir];
+          for (size_t k = 0; k + 2 < hv.size(); k += 3) {
+            const uint32_t e0 = hv[k + 1], e1 = hv[k + 2];
+            const uint32_t nch = (e1 - e0 + shk::kHubChunk - 1u) / shk::kHubChunk;
+            for (uint32_t ch = 0; ch < nch; ++ch) {
+              HubItem it{};
+              it.job = (uint32_t)gjobs[fi].size();
+              it.x = hv[k];
+              it.e0 = e0 + ch * shk::kHubChunk;
+              it.e1 = std::min(e1, it.e0 + shk::kHubChunk);
+              it.chunk = ch;
+              it.nchunks = nch;
+              it.pbase = hrows[fi];
+              it.dbase = hdone[fi];
+              it.dir = dir;
+              it.ubase = (uint32_t)hunits[fi].size();
+              for (uint32_t go = 0; go < H.Gj; ++go)
+                hunits[fi].push_back((uint32_t)hitems[fi].size());
+              hitems[fi].push_back(it);
+            }
+            hrows[fi] += nch * H.Gj;
+            hdone[fi] += H.Gj;
+          }
+        }
         gjobs[fi].push_back(H);
       }
       // init, observables, fields: one job per group, tiles of kTile vertices
@@ -522,6 +583,14 @@ static shaken_status build_plan(Plan& P, cudaStream_t st) {
     TRY(upload(F->ojobs, ojobs[fi].data(), ojobs[fi].size() * sizeof(GraphJob), st));
     TRY(upload(F->otiles, otiles[fi].data(), otiles[fi].size() * sizeof(Tile), st));
     F->n_otiles = (int)otiles[fi].size();
+    if (!hunits[fi].empty()) {
+      TRY(upload(F->hub_items, hitems[fi].data(), hitems[fi].size() * sizeof(HubItem), st));
+      TRY(upload(F->hub_units, hunits[fi].data(), hunits[fi].size() * 4, st));
+      TRY(F->hub_partial.alloc((size_t)hrows[fi] * 32u * 4u));
+      TRY(F->hub_done.alloc((size_t)hdone[fi] * 4u));
+      CU(cudaMemsetAsync(F->hub_done.p, 0, (size_t)hdone[fi] * 4u, st));
+      F->n_hub_units = (int)hunits[fi].size();
+    }
     P.fams.push_back(std::move(F));
   }
   TRY(upload(P.ctxlist, cds.data(), cds.size() * sizeof(CtxDev*), st));
@@ -573,6 +642,12 @@ static shaken_status plan_step_launch(Plan& P, cudaStream_t st, uint64_t* nl,
         CU(shk::launch_graph_half(F->enc != 0, F->jobs.as<GraphJob>(), F->tiles.as<Tile>(),
                                   F->n_tiles, half, ex, P.blocks_per_sm, st));
       ++count;
+      if (F->kind == 1 && F->n_hub_units > 0) {
+        CU(shk::launch_graph_hub(F->enc != 0, F->jobs.as<GraphJob>(), F->hub_items.as<HubItem>(),
+                                 F->hub_units.as<uint32_t>(), F->n_hub_units, half,
+                                 F->hub_partial.as<uint32_t>(), F->hub_done.as<uint32_t>(), st));
+        ++count;
+      }
       if (timed) {
         CU(cudaEventRecord(e1, st));
         P.ev_pending.emplace_back(e0, e1);
@@ -784,6 +859,7 @@ static shaken_status validate(const shaken_problem* p) {
 struct HostPrep {
   std::vector<int32_t> iptr, optr;
   std::vector<uint32_t> iperm, operm;  // vertices by increasing in- / out-degree
+  std::vector<uint32_t> hubs[2];       // (x, first edge, end edge) above kHubDeg: in, out
   std::vector<uint32_t> icol, ocol;
   std::vector<float> iJ, oJ;
   std::vector<uint32_t> frozen_lanes;
@@ -835,11 +911,24 @@ static void build_graph_host(shaken_ctx* c, const shaken_problem* p, HostPrep& h
   };
   by_degree(hp.iptr, hp.iperm);
   by_degree(hp.optr, hp.operm);
+  auto hubs = [&](const std::vector<int32_t>& ptr, std::vector<uint32_t>& out) {
+    out.clear();
+    for (int64_t x = 0; x < n; ++x)
+      if ((uint32_t)(ptr[x + 1] - ptr[x]) > shk::kHubDeg) {
+        out.push_back((uint32_t)x);
+        out.push_back((uint32_t)ptr[x]);
+        out.push_back((uint32_t)ptr[x + 1]);
+      }
+  };
+  hubs(hp.iptr, hp.hubs[0]);
+  hubs(hp.optr, hp.hubs[1]);
   c->sumJ = 0.0;
   for (int64_t e = 0; e < m; ++e) c->sumJ += (double)p->J_edge[e];
 }
 
 static shaken_status upload_graph(shaken_ctx* c, const HostPrep& hp, cudaStream_t st) {
+  c->hubs[0] = hp.hubs[0];
+  c->hubs[1] = hp.hubs[1];
   TRY(upload(c->in_ptr, hp.iptr.data(), hp.iptr.size() * 4, st));
   TRY(upload(c->in_perm, hp.iperm.data(), hp.iperm.size() * 4, st));
   TRY(upload(c->out_perm, hp.operm.data(), hp.operm.size() * 4, st));

@@ -334,4 +334,23 @@ struct Tile {
   uint32_t w0;
 };
 
+// Vertices of degree above kHubDeg in a half step's direction are not decided by the
+// half-step kernel: their edge lists are cut into chunks of kHubChunk edges, one warp
+// per (chunk, group) sums the chunk's 32 per-replica fields, and the warp that
+// finishes a vertex word last adds the chunk sums in chunk order and decides it.
+constexpr uint32_t kHubDeg = 255;
+constexpr uint32_t kHubChunk = 2048;
+
+struct HubItem {
+  uint32_t job;      // half-step job (index in the family's jobs)
+  uint32_t x;        // the vertex
+  uint32_t e0, e1;   // the chunk's edges [e0, e1) in the direction's CSR
+  uint32_t chunk;    // index of the chunk among the vertex's
+  uint32_t nchunks;  // chunks of the vertex
+  uint32_t pbase;    // partial rows of the vertex: pbase + go * nchunks + chunk (32 words each)
+  uint32_t dbase;    // finished-chunk counters of the vertex: dbase + go
+  uint32_t dir;      // 0: in-edges (update type 0), 1: out-edges (type 1)
+  uint32_t ubase;    // its warps (units) ubase + go for the job's groups go < Gj
+};
+
 }  // namespace shk
