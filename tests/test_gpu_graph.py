@@ -110,7 +110,8 @@ def _field_band(h, beta, scale):
     ex2.approx (relative 2^-22) and the rounding of its exponent (relative 2^-24 of
     2 beta h log2 e), the draw converted to fp32 and the product (2 x 2^-24 of 2^32 p),
     plus one unit for the floor."""
-    p = 1.0 / (1.0 + np.exp(-2.0 * beta * h))
+    with np.errstate(over="ignore"):  # p -> 0 for strongly negative fields
+        p = 1.0 / (1.0 + np.exp(-2.0 * beta * h))
     dp = p * (1.0 - p)
     return (2.0 ** 32 * dp * (2.0 * beta * 1e-6 * scale + 2.0 ** -22
                               + np.abs(2.0 * beta * h) * 2.0 ** -23)
@@ -159,6 +160,63 @@ def test_real_coupling_decisions_outside_field_band(S, reversed_):
         total_in_band += int((~outside).sum())
     # the band is a few parts in 10^6 of the draw range: a handful of lanes at most
     assert total_in_band <= 2e-4 * 2 * n * R, total_in_band
+
+
+def _real_band_check(S, n, u, v, J, lam, R, beta, q, seed, orientation):
+    """One full step of the real-coupling product kernel from a given orientation;
+    returns the number of (vertex, replica) lanes inside the field band after
+    asserting every lane outside it equals the oracle's fp64 decision."""
+    ctx = S.shaken_init(graph_problem(S, n, u, v, J, R, beta, q=q, lam=lam, integer=False,
+                                      orientation=orientation), seed)
+    S.shaken_step(ctx, 1)
+    sig0 = S.shaken_get_spins(ctx, R, n)
+    S.shaken_step(ctx, 1)
+    sigp = S.shaken_get_spins_prime(ctx, R, n)
+    sig1 = S.shaken_get_spins(ctx, R, n)
+    S.shaken_free(ctx)
+    tail, head = core.orient(u, v, orientation)
+    Jd, ld = J.astype(np.float64), lam.astype(np.float64)
+    in_band = 0
+    for typ, src, out in ((0, sig0, sigp), (1, sigp, sig1)):
+        h = core.graph_fields(src, tail, head, Jd, False, ld, q, typ)
+        ref = core.graph_half(src, tail, head, Jd, False, ld, q, beta, seed, 1, typ)
+        draws = core.graph_draws(seed, n, R, 1, typ, core.DRAW_DIRECT).astype(np.float64)
+        ends = head if typ == 0 else tail
+        scale = (np.bincount(ends, weights=np.abs(Jd), minlength=n) + q + np.abs(ld))[None, :]
+        band, bound = _field_band(h, beta[:, None], scale)
+        outside = np.abs(draws - bound) > band
+        bad = outside & (out != ref)
+        assert not bad.any(), (orientation, typ, np.argwhere(bad)[:5])
+        in_band += int((~outside).sum())
+    return in_band
+
+
+def test_real_coupling_hub_decisions_outside_field_band(S):
+    """Vertices of degree above 255 with real couplings (the chunked hub kernel: per
+    chunk fp32 sums, added in chunk order): a star with 10^4 leaves (its centre's
+    edges in five chunks) with the centre on the in- and then the out-side, and a
+    power-law graph (n = 20000, exponent 2.5, a dozen hubs) in both orientations.
+    Every (vertex, replica) decision of both half steps equals the oracle's fp64
+    decision outside the field band (Sec. 2, fields below Eq. (ham21))."""
+    R, q = 64, 1.0
+    leaves = 10_000
+    n = leaves + 1
+    src = np.arange(1, n, dtype=np.int32)
+    hub = np.zeros(leaves, np.int32)
+    J = W.couplings_normal(leaves, 21)
+    lam = W.fields_normal(n, 0.1, 22)
+    beta = W.beta_grid(R, 0.001, 0.02, 23)  # the centre's field is ~N(0, 10^4)
+    in_band = 0
+    for k, (uu, vv) in enumerate(((src, hub), (hub, src))):
+        in_band += _real_band_check(S, n, uu, vv, J, lam, R, beta, q, 31 + k, 2)
+    n = 20000
+    u, v = W.power_law(n, 6.0, 2.5, 3)
+    J = W.couplings_normal(u.size, 24)
+    lam = W.fields_normal(n, 0.1, 25)
+    beta = W.beta_grid(R, 0.05, 1.0, 26)
+    for k, (uu, vv) in enumerate(((u, v), (v, u))):
+        in_band += _real_band_check(S, n, uu, vv, J, lam, R, beta, q, 41 + k, 2)
+    assert in_band <= 2e-4 * 2 * R * (leaves + 1 + n) * 2, in_band
 
 
 def test_real_coupling_decisions_full_size_sampled(S):
