@@ -835,9 +835,28 @@ __global__ void __launch_bounds__(kTile) lattice_obs_single_kernel(
   }
 }
 
-// MULTISPIN: per-lane (= per replica) sums.  Each warp covers 32 consecutive
-// sites at a time; for every mask the warp ballots bit k and lane k adds the
-// popcount.
+// Column counts of the warp's 32 words: lane k gets the number of lanes whose word
+// has bit k set.  Five butterfly exchanges transpose the 32 x 32 bit block (at the
+// exchange of distance j, the lanes with bit j clear take the partner's low-column
+// half into their high columns and the others the reverse), so lane k then holds
+// column k, and a popcount finishes.
+__device__ __forceinline__ int warp_column_count(uint32_t x, int lane) {
+  const uint32_t Hm[5] = {0xFFFF0000u, 0xFF00FF00u, 0xF0F0F0F0u, 0xCCCCCCCCu, 0xAAAAAAAAu};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int j = 16 >> i;
+    const uint32_t p = __shfl_xor_sync(0xffffffffu, x, j);
+    const bool hi = (lane & j) != 0;
+    const uint32_t t = hi ? (p >> j) : (p << j);
+    const uint32_t M = hi ? ~Hm[i] : Hm[i];
+    x = (x & ~M) | (t & M);
+  }
+  return __popc(x);
+}
+
+// MULTISPIN: per-lane (= per replica) sums.  Each warp covers 32 consecutive sites at
+// a time; for every mask the warp's 32 words are transposed so that lane k counts
+// replica k's bits (warp_column_count).
 __global__ void __launch_bounds__(kTile) lattice_obs_multispin_kernel(
     const LatJob* __restrict__ jobs, const Tile* __restrict__ tiles, int n_tiles, int which,
     int full, int wpt) {
@@ -857,31 +876,19 @@ __global__ void __launch_bounds__(kTile) lattice_obs_multispin_kernel(
         if (full) load_lane_words<kEncMultispin>(J, J.B, w, 1u, S2, U2, R2);
       }
       const uint32_t act_m = act ? 0xffffffffu : 0u;
-      const uint32_t m_plus = S & act_m;
-      const uint32_t ag_v = ~(S ^ V) & act_m, ag_h = ~(S ^ H) & act_m;
-      const uint32_t ag_u = ~(S ^ U2) & act_m, ag_r = ~(S ^ R2) & act_m;
-      const uint32_t ag_s = ~(S ^ S2) & act_m, p2 = S2 & act_m;
       const int nact = __popc(__ballot_sync(0xffffffffu, act));
-#pragma unroll 4
-      for (int k = 0; k < 32; ++k) {
-        const int c0 = __popc(__ballot_sync(0xffffffffu, (m_plus >> k) & 1u));
-        const int c1 = __popc(__ballot_sync(0xffffffffu, (ag_v >> k) & 1u)) +
-                       __popc(__ballot_sync(0xffffffffu, (ag_h >> k) & 1u));
-        int c2 = 0, c3 = 0, c4 = 0;
-        if (full) {
-          c2 = __popc(__ballot_sync(0xffffffffu, (ag_u >> k) & 1u)) +
-               __popc(__ballot_sync(0xffffffffu, (ag_r >> k) & 1u));
-          c3 = __popc(__ballot_sync(0xffffffffu, (ag_s >> k) & 1u));
-          c4 = __popc(__ballot_sync(0xffffffffu, (p2 >> k) & 1u));
-        }
-        if (lane == k) {
-          cnt[0] += 2 * c0 - nact;      // sum sigma
-          cnt[1] += 2 * c1 - 2 * nact;  // in-edge products
-          cnt[2] += 2 * c2 - 2 * nact;  // P1
-          cnt[3] += 2 * c3 - nact;      // P2
-          cnt[4] += 2 * c4 - nact;      // M2
-          cnt[5] += 2 * nact - c1;      // cut = disagreements
-        }
+      const int c0 = warp_column_count(S & act_m, lane);
+      const int c1 = warp_column_count(~(S ^ V) & act_m, lane) +
+                     warp_column_count(~(S ^ H) & act_m, lane);
+      cnt[0] += 2 * c0 - nact;      // sum sigma
+      cnt[1] += 2 * c1 - 2 * nact;  // in-edge products
+      cnt[5] += 2 * nact - c1;      // cut = disagreements
+      if (full) {
+        const int c2 = warp_column_count(~(S ^ U2) & act_m, lane) +
+                       warp_column_count(~(S ^ R2) & act_m, lane);
+        cnt[2] += 2 * c2 - 2 * nact;                                  // P1
+        cnt[3] += 2 * warp_column_count(~(S ^ S2) & act_m, lane) - nact;  // P2
+        cnt[4] += 2 * warp_column_count(S2 & act_m, lane) - nact;         // M2
       }
     }
 #pragma unroll

@@ -95,6 +95,15 @@ __global__ void __launch_bounds__(256) pack_obs_kernel(const MemberDev* __restri
   }
 }
 
+// Every member's observables sums set to zero (before the observables kernels add
+// into them): one launch for the whole batch.
+__global__ void __launch_bounds__(256) zero_obs_kernel(const MemberDev* __restrict__ m) {
+  const MemberDev M = m[blockIdx.y];
+  const uint32_t ns = M.R * (uint32_t)kNumSums;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += gridDim.x * blockDim.x)
+    M.obs[i] = 0.0;
+}
+
 __global__ void __launch_bounds__(256) unpack_best_kernel(const MemberDev* __restrict__ m,
                                                           const double* __restrict__ src) {
   const MemberDev M = m[blockIdx.y];
@@ -106,7 +115,8 @@ __global__ void __launch_bounds__(256) unpack_best_kernel(const MemberDev* __res
   }
 }
 
-// what: 0 pack states, 1 unpack states, 2 pack observables, 3 unpack best energies
+// what: 0 pack states, 1 unpack states, 2 pack observables, 3 unpack best energies,
+// 4 zero the observables sums (buf unused)
 cudaError_t launch_member_copy(int what, const MemberDev* m, int n, void* buf,
                                unsigned long long max_words, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
@@ -121,8 +131,10 @@ cudaError_t launch_member_copy(int what, const MemberDev* m, int n, void* buf,
     unpack_states_kernel<<<grid, 256, 0, st>>>(m, static_cast<const uint32_t*>(buf));
   else if (what == 2)
     pack_obs_kernel<<<grid, 256, 0, st>>>(m, static_cast<double*>(buf));
-  else
+  else if (what == 3)
     unpack_best_kernel<<<grid, 256, 0, st>>>(m, static_cast<const double*>(buf));
+  else
+    zero_obs_kernel<<<grid, 256, 0, st>>>(m);
   return cudaGetLastError();
 }
 

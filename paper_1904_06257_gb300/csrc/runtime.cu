@@ -1446,9 +1446,10 @@ shaken_status shaken_batch_observables(shaken_batch* b, shaken_obs* out) {
   if (P.dirty) TRY(build_plan(P, st));
   TRY(member_table(P, st));
   TRY(stage(P.stage_obs, P.obs_doubles * sizeof(double)));
-  for (shaken_ctx* c : P.members)
-    CU(cudaMemsetAsync(c->obs_sums.p, 0, c->obs_sums.bytes, st));
-  uint64_t nl = 0;
+  // every member's sums zeroed by one launch (not one memset per member)
+  CU(shk::launch_member_copy(4, P.mtab.as<shk::MemberDev>(), (int)P.members.size(), nullptr,
+                             P.max_obs, st));
+  uint64_t nl = 1;
   TRY(obs_launch(P, st, &nl));
   const int n = (int)P.members.size();
   CU(shk::launch_member_copy(2, P.mtab.as<shk::MemberDev>(), n, P.stage_obs.p, P.max_obs, st));

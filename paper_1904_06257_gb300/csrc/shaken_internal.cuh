@@ -250,7 +250,7 @@ struct BandSync {
 struct MemberDev {
   uint32_t* A;                   // sigma
   uint32_t* B;                   // sigma'
-  const double* obs;             // [R][kNumSums] observables sums
+  double* obs;                   // [R][kNumSums] observables sums
   double* best;                  // [R]
   long long* best_step;          // [R]
   unsigned long long state_off;  // first 32-bit word of its state in the packed states
