@@ -59,6 +59,66 @@ def test_batch_equals_alone(S, use_graph):
     S.shaken_batch_free(b)
 
 
+def test_batch_of_hub_graphs_equals_alone_and_oracle(S):
+    """Graph contexts whose vertices of degree above 255 go to the chunked hub kernel,
+    batched together (one family: the hub chunks of several jobs, different group
+    counts, one context in reversed step order so its half steps take the other
+    direction's hubs first): every member equals its run alone and the oracle."""
+    n1 = 3001  # star: centre 0 with 3000 leaves (two chunks of 2048 edges)
+    u1 = np.zeros(n1 - 1, np.int32)
+    v1 = np.arange(1, n1, dtype=np.int32)
+    J1 = W.couplings_pm1(n1 - 1, 51)
+    lam1 = W.fields_normal(n1, 0.2, 52)
+    n2 = 20000
+    u2, v2 = W.power_law(n2, 6.0, 2.5, 53)
+    J2 = W.couplings_pm1(u2.size, 54)
+    lam2 = W.fields_normal(n2, 0.1, 55)
+    members = [  # (problem args, seed, R, reversed)
+        ((n1, u1, v1, J1, 64, W.beta_grid(64, 0.01, 0.05, 64), 0.5, lam1), 61, 64, False),
+        ((n2, u2, v2, J2, 32, 0.7, 1.0, lam2), 62, 32, False),
+        ((n2, u2, v2, J2, 96, W.beta_grid(96, 0.3, 1.2, 57), 1.0, lam2), 63, 96, True),
+    ]
+    steps = 6
+
+    def make(args, seed, rev):
+        n, u, v, J, R, beta, q, lam = args
+        c = S.shaken_init(graph_problem(S, n, u, v, J, R, beta, q=q, lam=lam), seed)
+        if rev:
+            S.shaken_set_order(c, True)
+        return c
+
+    alone = []
+    for args, seed, R, rev in members:
+        c = make(args, seed, rev)
+        S.shaken_step(c, steps)
+        alone.append(S.shaken_get_spins(c, R, args[0]))
+        S.shaken_free(c)
+    b = S.shaken_batch_create()
+    ctxs = []
+    for args, seed, R, rev in members:
+        c = make(args, seed, rev)
+        S.shaken_batch_add(b, c)
+        ctxs.append(c)
+    S.shaken_batch_step(b, steps, False)
+    S.shaken_batch_sync(b)
+    for c, ref, (args, seed, R, rev) in zip(ctxs, alone, members):
+        got = S.shaken_get_spins(c, R, args[0])
+        assert np.array_equal(got, ref), seed
+        n, u, v, J, R_, beta, q, lam = args
+        tail, head = core.orient(u, v, 0)
+        o = core.graph_init(n, R, seed, 0)
+        for t in range(steps):
+            for typ in ((1, 0) if rev else (0, 1)):
+                o = core.graph_half(o, tail, head, J.astype(np.float64), True,
+                                    lam.astype(np.float64), q, beta, seed, t, typ,
+                                    draw=core.DRAW_PLANE)
+        assert np.array_equal(got, o), seed
+    for c in ctxs:
+        S.shaken_batch_remove(b, c)
+        S.shaken_free(c)
+    S.shaken_batch_free(b)
+
+
 def test_batch_observables_and_async_state_equal_per_context_calls(S):
     """shaken_batch_observables (one launch per family for all members) gives each
     member's records exactly as shaken_observables on the same states, in member
