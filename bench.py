@@ -139,10 +139,11 @@ def oracle_pool(n_groups):
     return pool, workers
 
 
-def oracle_sample_plan(Ls, per_size):
+def oracle_sample_plan(Ls, per_size, max_L=None):
     """(L, group, full steps) of the oracle sample: the first `per_size` groups of each
-    lattice size, each for round(L_max^2 / L^2) steps (about equal updates per group)."""
-    sizes = sorted(set(int(x) for x in Ls))
+    lattice size up to max_L (all sizes when None), each for round(top^2 / L^2) steps,
+    top the largest size taken (about equal updates per group)."""
+    sizes = sorted(set(int(x) for x in Ls if max_L is None or int(x) <= max_L))
     top = max(sizes) ** 2
     plan = []
     for L in sizes:
@@ -151,26 +152,34 @@ def oracle_sample_plan(Ls, per_size):
     return plan
 
 
-def oracle_sample(pool, workers, Ls, betas, seeds, per_size=3):
+def oracle_sample(pool, workers, Ls, betas, seeds, per_size=3, max_L=None):
     """Run the CPU oracle, as it stands, on the first `per_size` groups of every
-    lattice size of the workload (32 replicas each), one task per group on the pool,
-    each group for as many full steps as the largest size's one step is worth in
-    updates (so the tasks take about the same time), and return (updates/s over the
-    wall time, cores used, description, updates, wall)."""
-    sizes = sorted(set(int(x) for x in Ls))
-    top = max(sizes) ** 2
-    jobs = [(L, betas[32 * g:32 * g + 32], seeds[g], steps)
-            for L, g, steps in oracle_sample_plan(Ls, per_size)]
+    lattice size of the workload up to max_L (32 replicas each), one task per group on
+    the pool, each group for as many full steps as the largest size's one step is
+    worth in updates (so the tasks take about the same time), and return (updates/s
+    over the wall time, cores used, description, updates, wall)."""
+    plan = oracle_sample_plan(Ls, per_size, max_L)
+    top = max(L for L, _, _ in plan) ** 2
+    jobs = [(L, betas[32 * g:32 * g + 32], seeds[g], steps) for L, g, steps in plan]
     workers = min(workers, len(jobs))
     t0 = time.perf_counter()
     res = pool.map(_oracle_group, jobs, chunksize=1)
     wall = time.perf_counter() - t0
     upd = sum(r[0] for r in res)
-    per = ", ".join(f"L={L}: {max(1, round(top / (L * L)))}" for L in sizes)
-    desc = (f"{len(jobs)} groups of the workload, {per_size} at each L (32 replicas each), "
-            f"full steps per group {per} (about equal work per group), one spawned process "
-            f"per group")
+    per = ", ".join(f"L={L}: {st}" for L, st in sorted(set((L, st) for L, _, st in plan)))
+    desc = (f"{len(jobs)} groups of the workload, {per_size} at each L "
+            f"{'' if max_L is None else f'<= {max_L} '}(32 replicas each), full steps per "
+            f"group {per} (about equal work per group), one spawned process per group")
     return upd / wall, workers, desc, upd, wall
+
+
+def reference_max_L(n_samples: int):
+    """Largest lattice size in the reference arm's per-step sample, so that n_samples
+    samples end within a few minutes: a group's step at L = 512 takes ~7 s of one Grace
+    core, at 256 ~1.7 s, at 128 ~0.4 s (the oracle's rate does not depend on L)."""
+    if n_samples <= 30:
+        return None
+    return 256 if n_samples <= 100 else 128
 
 
 def _oracle_config(task):
@@ -1009,7 +1018,8 @@ def run_reference(args, rank, world):
     tot_upd, tot_wall, cores, desc = 0.0, 0.0, 1, ""
     pool, workers = oracle_pool(16)
     for k in range(args.warmup + args.steps):
-        v, cores, desc, upd, wall = oracle_sample(pool, workers, Ls, betas, seeds, 1)
+        v, cores, desc, upd, wall = oracle_sample(pool, workers, Ls, betas, seeds, 1,
+                                                  reference_max_L(args.warmup + args.steps))
         if k >= args.warmup:
             tot_upd += upd
             tot_wall += wall

@@ -39,3 +39,16 @@ def test_oracle_sample_covers_every_size_with_equal_work():
         assert all(int(Ls[g]) == L for g in groups) and len(set(groups)) == len(groups)
     work = [L * L * steps for L, _, steps in plan]
     assert max(work) == min(work) == max(sizes) ** 2
+
+
+def test_reference_sample_is_bounded_for_long_runs():
+    sys.path.insert(0, ROOT)
+    import bench
+    Ls, _, _ = bench.workload(0)
+    assert bench.reference_max_L(25) is None
+    for n, cap in ((100, 256), (205, 128)):
+        assert bench.reference_max_L(n) == cap
+        plan = bench.oracle_sample_plan(Ls, 1, cap)
+        assert max(L for L, _, _ in plan) == cap
+        assert sorted(set(L for L, _, _ in plan)) == [L for L in (32, 64, 128, 256) if L <= cap]
+        assert len(set(L * L * st for L, _, st in plan)) == 1
