@@ -875,8 +875,88 @@ __global__ void __launch_bounds__(kTile) graph_init_kernel(const GraphJob* __res
   }
 }
 
-// Observables: each warp walks 32 vertices of its tile; lane k accumulates the
-// sums of replica 32g+k, then the block combines its warps and adds once.
+// Adds one bit per lane (x) to the bit-sliced counter p (planes 0 .. B - 1).
+__device__ __forceinline__ void bs_add(uint32_t (&p)[8], uint32_t x, int B) {
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    if (b < B) {
+      const uint32_t c = p[b] & x;
+      p[b] ^= x;
+      x = c;
+    }
+  }
+}
+
+// Sums over the CSR edges (x -> y) of the warp's 32 vertices (thread t: vertex x of
+// lane t), for lane k's replica: esum = sum of J_xy s_x s_y with s_y from Y, and (if
+// want_cut) cut = the number of those edges with s_x != s_y.  Integer couplings: per
+// thread, bit-sliced counters of the agreeing products (chunks of 255 edges), whose
+// planes are transposed across the warp; real couplings: per-replica float sums,
+// transposed once.  A thread's edges are read four at a time, the loads of the four
+// independent of one another.
+template <bool INTEGER>
+__device__ __forceinline__ void obs_edges(const int32_t* ptr, const uint32_t* col,
+                                          const float* Jr, const uint32_t* Y, uint32_t x,
+                                          bool act, uint32_t S, uint32_t G, uint32_t g,
+                                          bool want_cut, int lane, double& esum, double& cut) {
+  const int e0 = act ? ptr[x] : 0;
+  const int d = act ? ptr[x + 1] - e0 : 0;
+  const int dmax = __reduce_max_sync(0xffffffffu, d);
+  const int dsum = __reduce_add_sync(0xffffffffu, d);
+  long long cj = 0, ca = 0;
+  float fv[INTEGER ? 1 : 32];
+#pragma unroll
+  for (int k = 0; k < (INTEGER ? 1 : 32); ++k) fv[k] = 0.0f;
+  for (int base = 0; base < dmax; base += 252) {
+    const int B = 32 - __clz(min(dmax - base, 255));  // planes for counts up to the chunk
+    uint32_t pj[8], pa[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) pj[b] = pa[b] = 0u;
+    const int hi = min(d, base + 252);
+    for (int e = base; e < hi; e += 4) {
+      uint32_t cv[4], w[4];
+      float Jv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) cv[i] = e + i < hi ? __ldg(col + e0 + e + i) : 0u;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        w[i] = e + i < hi ? __ldg(Y + (size_t)(cv[i] & 0x7fffffffu) * G + g) : 0u;
+        if (!INTEGER) Jv[i] = e + i < hi ? __ldg(Jr + e0 + e + i) : 0.0f;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (e + i < hi) {
+          const uint32_t agree = ~(S ^ w[i]);
+          if constexpr (INTEGER) {
+            bs_add(pj, agree ^ (0u - (cv[i] >> 31)), B);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) fv[k] += ((agree >> k) & 1u) ? Jv[i] : -Jv[i];
+          }
+          if (want_cut) bs_add(pa, agree, B);
+        }
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      if (b < B) {
+        if (INTEGER) cj += (long long)warp_column_count(pj[b], lane) << b;
+        if (want_cut) ca += (long long)warp_column_count(pa[b], lane) << b;
+      }
+    }
+  }
+  if constexpr (INTEGER)
+    esum = (double)(2 * cj - dsum);
+  else
+    esum = (double)warp_transpose_sum(fv, lane);
+  cut = want_cut ? (double)(dsum - ca) : 0.0;
+}
+
+// Observables of one group (per-group jobs, Gj = 1): thread t of a tile takes vertex
+// w0 + t; the sums over the warp's 32 vertices reach lane k (replica 32 g + k) by bit
+// transposes of the sigma words and of bit-sliced edge counters (integer sums) or by
+// transposing butterflies (float sums), and the block adds its warps once per tile.
+template <bool INTEGER>
 __global__ void __launch_bounds__(kTile) graph_obs_kernel(const GraphJob* __restrict__ jobs,
                                                           const Tile* __restrict__ tiles,
                                                           int n_tiles, int which, int full) {
@@ -887,52 +967,35 @@ __global__ void __launch_bounds__(kTile) graph_obs_kernel(const GraphJob* __rest
     const Tile tl = tiles[ti];
     const GraphJob& J = jobs[tl.job];
     const uint32_t G = J.G, g = J.g0;
+    const uint32_t x = tl.w0 + (uint32_t)threadIdx.x;
+    const bool act = x < J.n;
+    const uint32_t am = act ? 0xffffffffu : 0u;
+    const uint32_t S = act ? J.A[(size_t)x * G + g] : 0u;
+    const uint32_t S2 = (act && full) ? J.B[(size_t)x * G + g] : 0u;
+    const float lam = act ? (J.lambda != nullptr ? J.lambda[x] : J.lambda_c) : 0.0f;
+    const int nact = __popc(__ballot_sync(0xffffffffu, act));
     double acc[kNumSums];
 #pragma unroll
     for (int q = 0; q < kNumSums; ++q) acc[q] = 0.0;
-    long long im = 0, iE = 0, iP1 = 0, iP2 = 0, icut = 0;
-    const uint32_t xb = tl.w0 + 32u * warp;
-    for (uint32_t xi = 0; xi < 32u; ++xi) {
-      const uint32_t x = xb + xi;
-      if (x >= J.n) break;
-      const int sx = ((J.A[(size_t)x * G + g] >> lane) & 1u) ? 1 : -1;
-      const float lam = J.lambda != nullptr ? J.lambda[x] : J.lambda_c;
-      im += sx;
-      acc[kSumLS] += (double)(lam * (float)sx);
-      float eacc = 0.0f;
-      for (int e = J.in_ptr[x]; e < J.in_ptr[x + 1]; ++e) {
-        const uint32_t cv = J.in_col[e];
-        const int sy = ((J.A[(size_t)(cv & 0x7fffffffu) * G + g] >> lane) & 1u) ? 1 : -1;
-        icut += (sx != sy);
-        if (J.integer) {
-          iE += (cv >> 31) ? -sx * sy : sx * sy;
-        } else {
-          eacc += J.in_J[e] * (float)(sx * sy);
-        }
-      }
-      acc[kSumE] += (double)eacc;
-      if (full) {
-        const int s2 = ((J.B[(size_t)x * G + g] >> lane) & 1u) ? 1 : -1;
-        iP2 += sx * s2;
-        acc[kSumLS2] += (double)(lam * (float)s2);
-        float pacc = 0.0f;
-        for (int e = J.out_ptr[x]; e < J.out_ptr[x + 1]; ++e) {
-          const uint32_t cv = J.out_col[e];
-          const int sy = ((J.B[(size_t)(cv & 0x7fffffffu) * G + g] >> lane) & 1u) ? 1 : -1;
-          if (J.integer) {
-            iP1 += (cv >> 31) ? -sx * sy : sx * sy;
-          } else {
-            pacc += J.out_J[e] * (float)(sx * sy);
-          }
-        }
-        acc[kSumP1] += (double)pacc;
-      }
+    acc[kSumM] = (double)(2 * warp_column_count(S & am, lane) - nact);
+    {
+      float v[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] = ((S >> k) & 1u) ? lam : -lam;
+      acc[kSumLS] = (double)warp_transpose_sum(v, lane);
     }
-    acc[kSumM] = (double)im;
-    acc[kSumE] += (double)iE;
-    acc[kSumP1] += (double)iP1;
-    acc[kSumP2] = (double)iP2;
-    acc[kSumCut] = (double)icut;
+    obs_edges<INTEGER>(J.in_ptr, J.in_col, J.in_J, J.A, x, act, S, G, g, true, lane,
+                       acc[kSumE], acc[kSumCut]);
+    if (full) {
+      acc[kSumP2] = (double)(2 * warp_column_count(~(S ^ S2) & am, lane) - nact);
+      float v[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] = ((S2 >> k) & 1u) ? lam : -lam;
+      acc[kSumLS2] = (double)warp_transpose_sum(v, lane);
+      double unused;
+      obs_edges<INTEGER>(J.out_ptr, J.out_col, J.out_J, J.B, x, act, S, G, g, false, lane,
+                         acc[kSumP1], unused);
+    }
 #pragma unroll
     for (int q = 0; q < kNumSums; ++q) red[warp][lane][q] = acc[q];
     __syncthreads();
@@ -1006,11 +1069,15 @@ cudaError_t launch_graph_init(const GraphJob* jobs, const Tile* tiles, int n_til
   return cudaGetLastError();
 }
 
-cudaError_t launch_graph_obs(const GraphJob* jobs, const Tile* tiles, int n_tiles, int which,
-                             int full, cudaStream_t st) {
+cudaError_t launch_graph_obs(bool integer, const GraphJob* jobs, const Tile* tiles, int n_tiles,
+                             int which, int full, cudaStream_t st) {
   if (n_tiles <= 0) return cudaSuccess;
-  return launch_dependent(graph_obs_kernel, dim3(grid_for(n_tiles, 4)), dim3(kTile), 0, st, jobs,
-                          tiles, n_tiles, which, full);
+  const dim3 grid(grid_for(n_tiles, 4));
+  if (integer)
+    return launch_dependent(graph_obs_kernel<true>, grid, dim3(kTile), 0, st, jobs, tiles,
+                            n_tiles, which, full);
+  return launch_dependent(graph_obs_kernel<false>, grid, dim3(kTile), 0, st, jobs, tiles,
+                          n_tiles, which, full);
 }
 
 cudaError_t launch_graph_fields(const GraphJob* jobs, const Tile* tiles, int n_tiles, uint32_t half,

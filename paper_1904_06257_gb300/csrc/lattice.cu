@@ -835,25 +835,6 @@ __global__ void __launch_bounds__(kTile) lattice_obs_single_kernel(
   }
 }
 
-// Column counts of the warp's 32 words: lane k gets the number of lanes whose word
-// has bit k set.  Five butterfly exchanges transpose the 32 x 32 bit block (at the
-// exchange of distance j, the lanes with bit j clear take the partner's low-column
-// half into their high columns and the others the reverse), so lane k then holds
-// column k, and a popcount finishes.
-__device__ __forceinline__ int warp_column_count(uint32_t x, int lane) {
-  const uint32_t Hm[5] = {0xFFFF0000u, 0xFF00FF00u, 0xF0F0F0F0u, 0xCCCCCCCCu, 0xAAAAAAAAu};
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const int j = 16 >> i;
-    const uint32_t p = __shfl_xor_sync(0xffffffffu, x, j);
-    const bool hi = (lane & j) != 0;
-    const uint32_t t = hi ? (p >> j) : (p << j);
-    const uint32_t M = hi ? ~Hm[i] : Hm[i];
-    x = (x & ~M) | (t & M);
-  }
-  return __popc(x);
-}
-
 // MULTISPIN: per-lane (= per replica) sums.  Each warp covers 32 consecutive sites at
 // a time; for every mask the warp's 32 words are transposed so that lane k counts
 // replica k's bits (warp_column_count).

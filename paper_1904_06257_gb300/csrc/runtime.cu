@@ -45,7 +45,7 @@ cudaError_t launch_graph_half(bool, const GraphJob*, const Tile*, int, uint32_t,
 cudaError_t launch_graph_hub(bool, const GraphJob*, const HubItem*, const uint32_t*, int, uint32_t,
                              uint32_t*, uint32_t*, cudaStream_t);
 cudaError_t launch_graph_init(const GraphJob*, const Tile*, int, int, cudaStream_t);
-cudaError_t launch_graph_obs(const GraphJob*, const Tile*, int, int, int, cudaStream_t);
+cudaError_t launch_graph_obs(bool, const GraphJob*, const Tile*, int, int, int, cudaStream_t);
 cudaError_t launch_graph_fields(const GraphJob*, const Tile*, int, uint32_t, float*,
                                 cudaStream_t);
 cudaError_t launch_epilogue(CtxDev* const*, int, cudaStream_t);
@@ -621,8 +621,8 @@ static shaken_status plan_step_launch(Plan& P, cudaStream_t st, uint64_t* nl,
                                    F->n_tiles, 0, 0, st));
         ++count;
       } else if (F->kind == 1) {
-        CU(shk::launch_graph_obs(F->ojobs.as<GraphJob>(), F->otiles.as<Tile>(), F->n_otiles, 0, 0,
-                                 st));
+        CU(shk::launch_graph_obs(F->enc != 0, F->ojobs.as<GraphJob>(), F->otiles.as<Tile>(),
+                                 F->n_otiles, 0, 0, st));
         ++count;
       }
     }
@@ -1371,8 +1371,8 @@ static shaken_status obs_launch(Plan& P, cudaStream_t st, uint64_t* launches) {
       CU(shk::launch_lattice_obs(F->enc, F->wpt, F->jobs.as<LatJob>(), F->tiles.as<Tile>(),
                                  F->n_tiles, 1, 1, st));
     else
-      CU(shk::launch_graph_obs(F->ojobs.as<GraphJob>(), F->otiles.as<Tile>(), F->n_otiles, 1, 1,
-                               st));
+      CU(shk::launch_graph_obs(F->enc != 0, F->ojobs.as<GraphJob>(), F->otiles.as<Tile>(),
+                               F->n_otiles, 1, 1, st));
     ++*launches;
   }
   return SHAKEN_OK;
