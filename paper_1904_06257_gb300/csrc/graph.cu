@@ -586,11 +586,12 @@ __global__ void __launch_bounds__(kTile, 3) graph_half_kernel(const GraphJob* __
     int32_t p0 = 0;
     int d = 0;
     float lam = 0.0f;
-    if (valid) {
-      x = __ldg((typ == 0u ? J.in_perm : J.out_perm) + slot);
-      p0 = __ldg(ptr + x);
-      d = __ldg(ptr + x + 1) - p0;
-      lam = J.lambda != nullptr ? __ldg(J.lambda + x) : J.lambda_c;
+    if (valid) {  // one 16-byte read: the vertex, its edge range and lambda_x
+      const uint4 vi = __ldg((typ == 0u ? J.in_visit : J.out_visit) + slot);
+      x = vi.x;
+      p0 = (int32_t)vi.y;
+      d = (int)vi.z;
+      lam = __uint_as_float(vi.w);
     }
     const float qf = (float)J.q;
     const float lmd = __fadd_rn(lam, -(float)d);

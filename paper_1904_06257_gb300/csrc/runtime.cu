@@ -242,7 +242,7 @@ struct shaken_ctx {
   DevMem step_sums, obs_sums, best, best_step;
   DevMem series_m, series_H;
   DevMem in_ptr, in_col, in_J, out_ptr, out_col, out_J, lam_dev;
-  DevMem in_perm, out_perm;  // vertices by increasing in- / out-degree (half-step order)
+  DevMem in_visit, out_visit;  // half-step visiting order: (x, first edge, degree, lambda_x)
   std::vector<uint32_t> hubs[2];  // graph: (x, first edge, end edge) of the vertices of degree
                                   // above kHubDeg, in-CSR [0] and out-CSR [1]
   DevMem band_xch, band_sync;  // banded runs: row exchange area and grid barrier
@@ -491,8 +491,8 @@ static shaken_status build_plan(Plan& P, cudaStream_t st) {
       J.out_ptr = c->out_ptr.as<int32_t>();
       J.out_col = c->out_col.as<uint32_t>();
       J.out_J = c->integer ? nullptr : c->out_J.as<float>();
-      J.in_perm = c->in_perm.as<uint32_t>();
-      J.out_perm = c->out_perm.as<uint32_t>();
+      J.in_visit = c->in_visit.as<uint4>();
+      J.out_visit = c->out_visit.as<uint4>();
       J.lambda = c->has_lambda ? c->lam_dev.as<float>() : nullptr;
       J.frozen = c->frozen_lanes.p ? c->frozen_lanes.as<uint32_t>() : nullptr;
       J.beta_lane = c->beta_lanes.as<double>();
@@ -858,7 +858,8 @@ static shaken_status validate(const shaken_problem* p) {
 // set-up so that the server can prepare jobs on the submitting thread.
 struct HostPrep {
   std::vector<int32_t> iptr, optr;
-  std::vector<uint32_t> iperm, operm;  // vertices by increasing in- / out-degree
+  std::vector<uint32_t> ivisit, ovisit;  // per slot of the degree order: x, first edge,
+                                         // degree, lambda_x bits (in- / out-CSR)
   std::vector<uint32_t> hubs[2];       // (x, first edge, end edge) above kHubDeg: in, out
   std::vector<uint32_t> icol, ocol;
   std::vector<float> iJ, oJ;
@@ -900,17 +901,26 @@ static void build_graph_host(shaken_ctx* c, const shaken_problem* p, HostPrep& h
   csr(tail, head, hp.optr, hp.ocol, hp.oJ);
   // visiting order of each half step: vertices by increasing degree (counting sort,
   // stable), so a warp's words have nearly equal edge loops and take the same path
-  auto by_degree = [&](const std::vector<int32_t>& ptr, std::vector<uint32_t>& perm) {
+  auto by_degree = [&](const std::vector<int32_t>& ptr, std::vector<uint32_t>& visit) {
     int32_t dmax = 0;
     for (int64_t x = 0; x < n; ++x) dmax = std::max(dmax, ptr[x + 1] - ptr[x]);
     std::vector<int64_t> start((size_t)dmax + 2, 0);
     for (int64_t x = 0; x < n; ++x) start[(size_t)(ptr[x + 1] - ptr[x]) + 1]++;
     for (size_t k = 1; k < start.size(); ++k) start[k] += start[k - 1];
-    perm.assign((size_t)n, 0u);
-    for (int64_t x = 0; x < n; ++x) perm[(size_t)start[(size_t)(ptr[x + 1] - ptr[x])]++] = (uint32_t)x;
+    visit.assign((size_t)n * 4, 0u);
+    for (int64_t x = 0; x < n; ++x) {
+      const size_t sl = (size_t)start[(size_t)(ptr[x + 1] - ptr[x])]++;
+      const float lam = p->lambda != nullptr ? p->lambda[x] : p->lambda_const;
+      uint32_t lb;
+      std::memcpy(&lb, &lam, 4);
+      visit[4 * sl] = (uint32_t)x;
+      visit[4 * sl + 1] = (uint32_t)ptr[x];
+      visit[4 * sl + 2] = (uint32_t)(ptr[x + 1] - ptr[x]);
+      visit[4 * sl + 3] = lb;
+    }
   };
-  by_degree(hp.iptr, hp.iperm);
-  by_degree(hp.optr, hp.operm);
+  by_degree(hp.iptr, hp.ivisit);
+  by_degree(hp.optr, hp.ovisit);
   auto hubs = [&](const std::vector<int32_t>& ptr, std::vector<uint32_t>& out) {
     out.clear();
     for (int64_t x = 0; x < n; ++x)
@@ -930,8 +940,8 @@ static shaken_status upload_graph(shaken_ctx* c, const HostPrep& hp, cudaStream_
   c->hubs[0] = hp.hubs[0];
   c->hubs[1] = hp.hubs[1];
   TRY(upload(c->in_ptr, hp.iptr.data(), hp.iptr.size() * 4, st));
-  TRY(upload(c->in_perm, hp.iperm.data(), hp.iperm.size() * 4, st));
-  TRY(upload(c->out_perm, hp.operm.data(), hp.operm.size() * 4, st));
+  TRY(upload(c->in_visit, hp.ivisit.data(), hp.ivisit.size() * 4, st));
+  TRY(upload(c->out_visit, hp.ovisit.data(), hp.ovisit.size() * 4, st));
   TRY(upload(c->out_ptr, hp.optr.data(), hp.optr.size() * 4, st));
   TRY(upload(c->in_col, hp.icol.data(), hp.icol.size() * 4, st));
   TRY(upload(c->out_col, hp.ocol.data(), hp.ocol.size() * 4, st));
@@ -1993,6 +2003,7 @@ static size_t job_bytes(const shaken_problem* p) {
   size_t b = 2 * (size_t)(p->replicas / 32) * N * 4;  // A, B
   if (p->kind == SHAKEN_GRAPH) {
     b += 2 * (size_t)(N + 1) * 4 + 2 * (size_t)p->m * 4;  // CSR
+    b += 2 * (size_t)N * 16;                                // visiting orders
     if (!p->J_is_integer) b += 2 * (size_t)p->m * 4;
     if (p->lambda) b += (size_t)N * 4;
     if (p->frozen_mask) b += (size_t)N * 4;

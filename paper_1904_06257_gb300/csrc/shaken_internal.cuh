@@ -309,8 +309,9 @@ struct GraphJob {
   const int32_t* out_ptr;  // out-CSR (heads y of (x -> y))
   const uint32_t* out_col;
   const float* out_J;
-  const uint32_t* in_perm;  // vertices by increasing in-degree (half-step order, h^{1->2})
-  const uint32_t* out_perm; // vertices by increasing out-degree (h^{2->1})
+  const uint4* in_visit;   // half-step order h^{1->2} (vertices by increasing in-degree):
+                           // (x, first in-edge, in-degree, lambda_x bits) per slot
+  const uint4* out_visit;  // the same for h^{2->1} (out-edges, out-degree)
   const float* lambda;     // [n] or null (lambda_c)
   const uint32_t* frozen;  // [n] lane masks or null
   const double* beta_lane; // [R] betas of the context

@@ -309,7 +309,7 @@ def test_server_budget_serialises_jobs(S):
     u, v = W.erdos_renyi(n, 6.0, 7)
     J = W.couplings_pm1(u.size, 8)
     p = graph_problem(S, n, u, v, J, 64, 1.0)
-    srv = S.shaken_server_create(150_000, 8)  # one ~110 kB job fits at a time
+    srv = S.shaken_server_create(250_000, 8)  # one ~175 kB job fits at a time
     sched = W.linear_schedule(0.2, 2.0, 30)
     ids = [S.shaken_server_submit(srv, p, s, sched) for s in range(4)]
     S.shaken_server_drain(srv, 120.0)
@@ -354,7 +354,7 @@ def test_server_free_cancels_queued_and_running_jobs(S):
     u, v = W.erdos_renyi(n, 6.0, 17)
     J = W.couplings_pm1(u.size, 18)
     p = graph_problem(S, n, u, v, J, 64, 1.0)
-    srv = S.shaken_server_create(300_000, 8)  # one ~206 kB job fits at a time
+    srv = S.shaken_server_create(500_000, 8)  # one ~335 kB job fits at a time
     sched = W.linear_schedule(0.2, 2.0, 2_000_000)
     a = S.shaken_server_submit(srv, p, 1, sched)
     b = S.shaken_server_submit(srv, p, 2, sched)
