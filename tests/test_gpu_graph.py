@@ -381,3 +381,32 @@ def test_integer_graph_class_tables_bit_exact(S, n, deg, R, q, beta):
     o, _ = core.graph_run(o, tail, head, J.astype(np.float64), True, lam.astype(np.float64), q,
                           beta, seed, 0, 3, draw=core.DRAW_PLANE)
     assert np.array_equal(got, o)
+
+
+@pytest.mark.parametrize("integer", [True, False])
+def test_graph_step_record_series(S, integer):
+    """The per-step series of a graph context (shaken_step_record: m and H(sigma_t) of
+    every replica at every step, from the graph observables kernel) against the
+    oracle's observables of the oracle's trajectory: m exactly, H within 1e-6 of its
+    scale sum |J| + 2 sum |lambda| (the scale of the fp32 sums, as for the fields).  Real
+    couplings: only the first step is compared (the trajectories agree outside the
+    field band, not bit for bit)."""
+    n, R, steps = 600, 64, 6 if integer else 1
+    u, v, J, lam = er_instance(n, 6.0, 91, integer=integer)
+    beta = W.beta_grid(R, 0.3, 1.5, 64)
+    seed = 93
+    ctx = S.shaken_init(graph_problem(S, n, u, v, J, R, beta, q=1.0, lam=lam,
+                                      integer=integer), seed)
+    mag, en = S.shaken_step_record(ctx, steps, R)
+    S.shaken_free(ctx)
+    tail, head = core.orient(u, v, 0)
+    Jd, ld = J.astype(np.float64), lam.astype(np.float64)
+    cur = core.graph_init(n, R, seed, 0)
+    scale = np.abs(Jd).sum() + 2.0 * np.abs(ld).sum()
+    for k in range(steps):
+        ref = core.graph_observables(cur, cur, tail, head, Jd, ld, 1.0)
+        for r in range(R):
+            assert abs(mag[k, r] - ref[r]["m"]) < 1e-12, (k, r)
+            assert abs(en[k, r] - ref[r]["H"]) < 1e-6 * (abs(ref[r]["H"]) + scale), (k, r)
+        cur, _ = core.graph_run(cur, tail, head, Jd, integer, ld, 1.0, beta, seed, k, 1,
+                                draw=core.DRAW_PLANE if integer else core.DRAW_DIRECT)
