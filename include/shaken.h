@@ -138,9 +138,11 @@ void shaken_free(shaken_ctx* ctx);
  * call: small lattices (<= 4096 lane words per replica, n >= 4) run in one
  * launch per 65536 steps with the state in shared memory; one mid-size
  * INT8/PACKED lattice (one replica, n >= 8, no tracking or anneal) runs in one
- * cooperative launch per 65536 steps holding row bands in shared memory, and
- * returns E_TIMEOUT if a grid-barrier wait ran out (the chunk is then not
- * applied: sigma, sigma' and the step counter stay as before it).  Every path
+ * cooperative launch per 65536 steps holding row bands in shared memory
+ * (neighbouring bands pass one boundary row per half step), and returns
+ * E_TIMEOUT if a wait for a neighbour's row or at the final grid barrier ran
+ * out (the chunk is then not applied: sigma, sigma' and the step counter stay
+ * as before it).  Every path
  * gives the same trajectory.  E_STATE if the context is owned by a batch. */
 shaken_status shaken_step(shaken_ctx* ctx, uint64_t n_steps);
 
@@ -222,9 +224,10 @@ shaken_status shaken_debug_exact_always(shaken_ctx* ctx, int on);
 
 /* Diagnostics for the failure path of banded runs (one mid-size INT8/PACKED
  * lattice, chunks of >= 8 steps without tracking, held in shared memory by a
- * cooperative grid with a grid barrier per half step): the next banded chunk
- * starts with its barrier's arrival count preset so that no block is ever the
- * last to arrive.  Every block's wait then runs out after its bounded spin
+ * cooperative grid: neighbouring blocks pass one boundary row per half step and
+ * all blocks meet at one grid barrier at the end of the chunk): the next banded
+ * chunk starts with that barrier's arrival count preset so that no block is ever
+ * the last to arrive.  Every block's wait then runs out after its bounded spin
  * (one second on the GPU's global timer), the blocks return without writing the
  * chunk back, and the stepping call returns SHAKEN_E_TIMEOUT with sigma, sigma'
  * and the step counter as before the chunk; the context stays usable.
