@@ -27,8 +27,11 @@
 // planes against the fp32 bounds on T, and T in fp64 where even they do not decide.
 // Real couplings (fp32 sums): direct draws u_k = W_k and tau_k = +1 iff
 // u_k (1 + e~) / 2^32 < 1 (statistical parity).
-// Vertices of degree above 255 are done by a whole warp (edge list split over the
-// lanes, per-replica counts or fields combined by a butterfly of shuffles).
+// Vertices of degree above 255 are left to graph_hub_kernel: their edge lists are cut
+// into chunks of 2048 edges, one warp per (chunk, group) combines its lanes' counts or
+// fields by a butterfly of shuffles, and the warp finishing a word's last chunk adds
+// the chunk sums in chunk order and decides the word.  A job's tiles are listed so
+// that the high-degree end of the visiting order spreads over the blocks.
 #include <cstdint>
 
 #include "shaken_internal.cuh"
