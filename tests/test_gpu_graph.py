@@ -290,11 +290,24 @@ def test_real_graph_statistics_match_oracle(S):
         assert abs(ga.mean() - oa.mean()) < 4 * se + 1e-12
 
 
-def test_fused_tracking_best_energy(S):
-    # the best energy tracked inside half 0 equals the minimum over steps of the
-    # oracle's H(sigma_t) along the same (bit-exact) trajectory
-    n, R = 500, 32
-    u, v, J, lam = er_instance(n, 6.0, 91)
+def _hub_instance(n, seed):
+    # Erdos-Renyi plus an in-hub: vertex n - 1 joined to every other vertex (under
+    # min -> max orientation its n - 1 edges all enter it: two chunks of the hub kernel)
+    u, v = W.erdos_renyi(n, 4.0, seed)
+    a = np.concatenate([u, np.arange(n - 1)]).astype(np.int64)
+    b = np.concatenate([v, np.full(n - 1, n - 1)]).astype(np.int64)
+    keys = np.unique(np.minimum(a, b) * n + np.maximum(a, b))
+    u, v = (keys // n).astype(np.int32), (keys % n).astype(np.int32)
+    return u, v, W.couplings_pm1(u.size, seed + 1), W.fields_normal(n, 0.1, seed + 2)
+
+
+@pytest.mark.parametrize("kind", ["er", "hub"])
+def test_fused_tracking_best_energy(S, kind):
+    # the best energy tracked inside half 0 (the hub kernel adds the words of vertices
+    # of degree above 255) equals the minimum over steps of the oracle's H(sigma_t)
+    # along the same (bit-exact) trajectory
+    n, R = (500, 32) if kind == "er" else (3001, 64)
+    u, v, J, lam = er_instance(n, 6.0, 91) if kind == "er" else _hub_instance(n, 95)
     sched = W.linear_schedule(0.2, 2.5, 15)
     seed = 4711
     ctx = S.shaken_init(graph_problem(S, n, u, v, J, R, 0.5, q=1.0, lam=lam), seed)
