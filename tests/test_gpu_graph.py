@@ -423,3 +423,34 @@ def test_graph_step_record_series(S, integer):
             assert abs(en[k, r] - ref[r]["H"]) < 1e-6 * (abs(ref[r]["H"]) + scale), (k, r)
         cur, _ = core.graph_run(cur, tail, head, Jd, integer, ld, 1.0, beta, seed, k, 1,
                                 draw=core.DRAW_PLANE if integer else core.DRAW_DIRECT)
+
+
+@pytest.mark.parametrize("reverse", [False, True])
+def test_graph_observables_with_hubs(S, reverse):
+    """Observables of a graph with a vertex of degree 3000 (the observables kernel
+    counts its edges in chunks of 252 per thread) against the oracle's, in both
+    orientations of the hub's edges: m and cut exactly, H and the pair energy within
+    1e-6 rel (integer couplings, fp32 lambda sums)."""
+    n, R = 3001, 64
+    u, v, J, lam = _hub_instance(n, 97)
+    orientation = 0
+    if reverse:  # the hub's edges leave it: given orientation, hub as the tail
+        u, v = np.where(v == n - 1, v, u), np.where(v == n - 1, u, v)
+        orientation = 2
+    beta = W.beta_grid(R, 0.2, 1.5, 64)
+    seed = 99
+    ctx = S.shaken_init(graph_problem(S, n, u, v, J, R, beta, q=1.0, lam=lam,
+                                      orientation=orientation), seed)
+    S.shaken_step(ctx, 3)
+    s1 = S.shaken_get_spins(ctx, R, n)
+    sp = S.shaken_get_spins_prime(ctx, R, n)
+    obs = S.shaken_observables(ctx, R)
+    S.shaken_free(ctx)
+    tail, head = core.orient(u, v, orientation)
+    ref = core.graph_observables(s1, sp, tail, head, J.astype(np.float64),
+                                 lam.astype(np.float64), 1.0)
+    for r in range(R):
+        assert abs(obs["magnetization"][r] - ref[r]["m"]) < 1e-12
+        assert abs(obs["energy"][r] - ref[r]["H"]) < 1e-6 * (1 + abs(ref[r]["H"]))
+        assert abs(obs["pair_energy"][r] - ref[r]["pair"]) < 1e-6 * (1 + abs(ref[r]["pair"]))
+        assert obs["cut_edges"][r] == ref[r]["cut"]
