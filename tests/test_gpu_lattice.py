@@ -30,6 +30,7 @@ CASES = [
     ("PACKED", 64, 2, -1.0, 1.0, 0.2, True),
     ("MULTISPIN", 32, 64, 1.0, 1.0, 0.0, False),
     ("MULTISPIN", 96, 32, 1.0, 0.5, 0.01, True),  # 9216 sites: 36 tiles
+    ("MULTISPIN", 160, 64, 0.8, 0.7, 0.05, True),  # 25600 sites x 2 groups, frozen frame
 ]
 
 
