@@ -52,3 +52,25 @@ def test_reference_sample_is_bounded_for_long_runs():
         assert max(L for L, _, _ in plan) == cap
         assert sorted(set(L for L, _, _ in plan)) == [L for L in (32, 64, 128, 256) if L <= cap]
         assert len(set(L * L * st for L, _, st in plan)) == 1
+
+
+def test_roofline_calls_plus_planes_arithmetic():
+    """The multispin roofline's bound: calls at the measured Philox rate plus 16 logic
+    operations per call at the measured LOP3 rate, one after the other; and at the
+    unit rates (20 wide products per call at 32 lanes/clk/SM, 36 logic operations per
+    call at 64 lanes/clk/SM)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    sms, mhz = 152, bench.sm_max_mhz()
+    clk = sms * mhz * 1e6
+    rates = {"philox_calls": 1.0e11, "lop3": 4.0e12}
+    calls, launch_s = 1.0e7, 2.0e-4
+    r = bench.calls_plus_planes(calls, launch_s, rates, sms)
+    meas = calls / 1.0e11 + 16 * calls / 4.0e12
+    assert abs(r["bound_ms_measured_rates"] - meas * 1e3) < 1e-12
+    assert abs(r["frac_measured_rates"] - meas / launch_s) < 1e-12
+    unit = calls * 20 / (32 * clk) + calls * 36 / (64 * clk)
+    assert abs(r["bound_ms_unit_rates"] - unit * 1e3) < 1e-12
+    # the line's peak in calls/s is the same bound expressed as a rate
+    peak = 1.0 / (1.0 / rates["philox_calls"] + bench.PLANE_OPS_PER_CALL / rates["lop3"])
+    assert abs(calls / peak - meas) < 1e-15
