@@ -785,13 +785,34 @@ def _timed(torch, stream, fn):
 def run_graphs(S, stream, torch, args):
     """Sparse-graph workloads: Erdos-Renyi (mean degree 8) with +-1 couplings -- the
     full linear anneal beta 0.1 -> 3.0 over 5000 steps, best energy and cut -- and
-    throughput of the real-coupling path and of a random 3-regular graph."""
+    throughput of the real-coupling path, of a random 3-regular graph and of a
+    hub-heavy power-law graph, and the 2D Edwards-Anderson anneal.  args.graph_cases
+    (comma-separated: anneal, real, reg3, powerlaw, ea2d) selects some of them."""
+    cases = (set(args.graph_cases.split(",")) if getattr(args, "graph_cases", None)
+             else {"anneal", "real", "reg3", "powerlaw", "ea2d"})
     out = {}
     n, R = GRAPH_N, GRAPH_R
     lam = W.fields_normal(n, 0.1, W.BASE_SEED + 3)
-    u, v = W.erdos_renyi(n, 8.0, W.BASE_SEED + 1)
-    Jpm = W.couplings_pm1(u.size, W.BASE_SEED + 2)
     steps = args.graph_anneal_steps
+    k = 50
+    if cases & {"anneal", "real"}:
+        u, v = W.erdos_renyi(n, 8.0, W.BASE_SEED + 1)
+    if "anneal" in cases:
+        out["er_pm1_anneal"] = _graph_anneal(S, stream, torch, n, R, u, v, lam, steps)
+    if "real" in cases:
+        out["er_real_step"] = _graph_real(S, stream, torch, n, R, u, v, lam, k)
+    if "reg3" in cases:
+        out["reg3_pm1_step"] = _graph_reg3(S, stream, torch, n, R, lam, k)
+    if "powerlaw" in cases:
+        out["powerlaw_pm1_step"] = _graph_powerlaw(S, stream, torch, n, R, lam)
+    if "ea2d" in cases:
+        out["ea2d_pm1_anneal"] = _graph_ea2d(S, stream, torch, steps)
+    return out
+
+
+def _graph_anneal(S, stream, torch, n, R, u, v, lam, steps):
+    """ER +-1 anneal beta 0.1 -> 3.0 with per-step best-energy tracking."""
+    Jpm = W.couplings_pm1(u.size, W.BASE_SEED + 2)
     sched = W.linear_schedule(0.1, 3.0, steps)
     p = S.Problem(S.GRAPH, S.MULTISPIN, R, 0.1, 1.0, n=n, u=u, v=v, J_edge=Jpm,
                   J_is_integer=True, lambda_=lam)
@@ -801,7 +822,7 @@ def run_graphs(S, stream, torch, args):
     dt = _timed(torch, stream, lambda: S.shaken_anneal(c, sched))
     obs = S.shaken_observables(c, R)
     S.shaken_free(c)
-    out["er_pm1_anneal"] = {
+    return {
         "n": n, "m": int(u.size), "replicas": R, "steps": steps,
         "updates_per_s": 2.0 * n * R * steps / dt, "seconds": dt,
         "best_energy_min": float(obs["best_energy"].min()),
@@ -810,18 +831,23 @@ def run_graphs(S, stream, torch, args):
         "cut_weight_best_replica": float(obs["cut_weight"][int(np.argmin(obs["energy"]))]),
         "cut_edges_best_replica": int(obs["cut_edges"][int(np.argmin(obs["energy"]))]),
         "note": "anneal with per-step best-energy tracking (fused into half 0)"}
-    # real couplings N(0,1), fixed beta, throughput without tracking
+
+
+def _graph_real(S, stream, torch, n, R, u, v, lam, k):
+    """Real couplings N(0,1), fixed beta, throughput without tracking."""
     Jr = W.couplings_normal(u.size, W.BASE_SEED + 4)
     p = S.Problem(S.GRAPH, S.MULTISPIN, R, 1.0, 1.0, n=n, u=u, v=v, J_edge=Jr,
                   J_is_integer=False, lambda_=lam)
     c = S.shaken_init(p, W.BASE_SEED + 12, stream)
     S.shaken_step(c, 2)
     S.shaken_sync(c)
-    k = 50
     dt = _timed(torch, stream, lambda: S.shaken_step(c, k))
     S.shaken_free(c)
-    out["er_real_step"] = {"updates_per_s": 2.0 * n * R * k / dt, "steps": k}
-    # +-1 on a random 3-regular graph, fixed beta
+    return {"updates_per_s": 2.0 * n * R * k / dt, "steps": k}
+
+
+def _graph_reg3(S, stream, torch, n, R, lam, k):
+    """+-1 on a random 3-regular graph, fixed beta."""
     u3, v3 = W.random_regular3(n, W.BASE_SEED + 5)
     J3 = W.couplings_pm1(u3.size, W.BASE_SEED + 6)
     p = S.Problem(S.GRAPH, S.MULTISPIN, R, 1.0, 1.0, n=n, u=u3, v=v3, J_edge=J3,
@@ -831,9 +857,12 @@ def run_graphs(S, stream, torch, args):
     S.shaken_sync(c)
     dt = _timed(torch, stream, lambda: S.shaken_step(c, k))
     S.shaken_free(c)
-    out["reg3_pm1_step"] = {"updates_per_s": 2.0 * n * R * k / dt, "steps": k}
-    # +-1 on a hub-heavy power-law graph (Chung-Lu, exponent 2.1, mean degree 8): the
-    # vertices of degree above 255 take the warp-per-word path
+    return {"updates_per_s": 2.0 * n * R * k / dt, "steps": k}
+
+
+def _graph_powerlaw(S, stream, torch, n, R, lam):
+    """+-1 on a hub-heavy power-law graph (Chung-Lu, exponent 2.1, mean degree 8): the
+    vertices of degree above 255 go to the chunked hub kernel."""
     up, vp = W.power_law(n, 8.0, 2.1, W.BASE_SEED + 15)
     Jp = W.couplings_pm1(up.size, W.BASE_SEED + 16)
     deg = np.bincount(np.concatenate([up, vp]), minlength=n)
@@ -847,17 +876,20 @@ def run_graphs(S, stream, torch, args):
     kp = 20
     dt = _timed(torch, stream, lambda: S.shaken_step(c, kp))
     S.shaken_free(c)
-    out["powerlaw_pm1_step"] = {
+    return {
         "n": n, "m": int(up.size), "exponent": 2.1, "replicas": R, "steps": kp,
         "updates_per_s": 2.0 * n * R * kp / dt,
         "max_degree": int(deg.max()), "max_in_degree": int(indeg.max()),
         "max_out_degree": int(outdeg.max()),
         "hubs_in": int((indeg > 255).sum()), "hubs_out": int((outdeg > 255).sum()),
-        "note": "vertices of degree above 255 in a half step's direction: one warp per "
-                "32-replica word"}
-    # the optimisation use of Sec. 6 on a synthetic 2D Edwards-Anderson +-1 instance:
-    # L x L torus, couplings +-1 i.i.d., lambda = 0, q = 2.5 (> 2: the regime where the
-    # minimisers of the pair Hamiltonian carry over, Sec. 6), 256 replicas, linear anneal
+        "note": "vertices of degree above 255 in a half step's direction: the chunked hub "
+                "kernel (one warp per 2048-edge chunk and group)"}
+
+
+def _graph_ea2d(S, stream, torch, steps):
+    """The optimisation use of Sec. 6 on a synthetic 2D Edwards-Anderson +-1 instance:
+    L x L torus, couplings +-1 i.i.d., lambda = 0, q = 2.5 (> 2: the regime where the
+    minimisers of the pair Hamiltonian carry over, Sec. 6), 256 replicas, linear anneal."""
     Le, Re, qe = 256, 256, 2.5
     ue, ve = W.lattice_as_graph(Le)
     Je = W.couplings_pm1(ue.size, W.BASE_SEED + 8)
@@ -870,14 +902,13 @@ def run_graphs(S, stream, torch, args):
     dt = _timed(torch, stream, lambda: S.shaken_anneal(c, sched))
     obs = S.shaken_observables(c, Re)
     S.shaken_free(c)
-    out["ea2d_pm1_anneal"] = {
+    return {
         "L": Le, "q": qe, "replicas": Re, "steps": steps,
         "updates_per_s": 2.0 * Le * Le * Re * steps / dt, "seconds": dt,
         "best_energy_per_site_min": float(obs["best_energy"].min()) / (Le * Le),
         "best_energy_per_site_mean": float(obs["best_energy"].mean()) / (Le * Le),
         "note": "synthetic instance (the paper's EA instances are not published); energies "
                 "per site of H(sigma) = -sum J s s over the best full-step configurations"}
-    return out
 
 
 # ------------------------------------------------------------------------ serving
@@ -1065,6 +1096,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="fixed lattice launch-shape rule instead of timed trials (profiling)")
     ap.add_argument("--graph-anneal-steps", type=int, default=5000)
+    ap.add_argument("--graph-cases", default=None,
+                    help="graph section: comma-separated subset of anneal, real, reg3, "
+                         "powerlaw, ea2d (default: all)")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--serve-horizon", type=float, default=8.0,
                     help="seconds of arrivals of each load-sweep stream")
